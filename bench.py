@@ -1,0 +1,336 @@
+"""Benchmark of the modified-Ehrenfest MD step on one or more GB300s.
+
+Workload: the 96^3 precision workload -- 64 Si-like pseudo-atoms, 128 doubly
+occupied orbitals, 0.25 bohr spacing, 8th-order stencil, mu = 10,
+dt = 0.05 sqrt(10) -- with complex64 orbitals and FP64 density, energies,
+forces and ions (the headline line), plus the same workload in FP64 (extra
+key).  A "step" is one full MD step: velocity-Verlet positions, ionic tables
+and potential, 8 Horner stages of AETRS with Taylor-4 halves, density,
+Hartree + LDA, forces, velocity-Verlet velocities.
+
+Metric: orbital grid-point H*psi updates/s = 8 * n_orb * N^3 * steps / time
+(8 applications of H per orbital and point per step).
+
+Multi-GPU: the path is run as independent replicas, one per GPU (the method
+does shard by orbitals with one density/force reduction per step, which this
+build does not implement); value = all ranks' updates / max-over-ranks time.
+
+--impl reference: times the FP64 CPU oracle (the restated method, plain
+numpy) on the same workload: each step is one AETRS step (8 H applications)
+of a bounded orbital subset, scaled per orbital-point update.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "orbital grid-point H*psi updates/s"
+UNIT = "updates/s"
+# Algorithmic bytes of one Horner-stage update (read u_in, read psi0, write
+# u_out); the potential and projector lists are shared across an orbital
+# block and not counted.
+BYTES_PER_UPDATE = {"f32": 24, "f64": 48}
+# dram__bytes_read.sum + dram__bytes_write.sum of one Horner-stage launch
+# (profiles/horner_stage_c96.md), per precision, for the kernel as built;
+# None until a capture exists for it.
+TRAFFIC_PER_LAUNCH = {"f32": None, "f64": None}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._th = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"],
+                                     capture_output=True, text=True, timeout=5).stdout
+                for line in out.strip().splitlines():
+                    f = [x.strip() for x in line.split(",")]
+                    if len(f) >= 9:
+                        self.samples.append(f)
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._th = threading.Thread(target=self._run, daemon=True)
+        self._th.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._th:
+            self._th.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if s[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_oracle_rate(sysin, n_orb_sample: int, reps: int = 1):
+    """Oracle AETRS step (two Taylor-4 exponentials = 8 H applications) on
+    n_orb_sample orbitals of the workload, with the full potential of the
+    workload's density.  Returns (updates/s, seconds, threads)."""
+    import numpy as np
+    from oracle import emd_oracle as O
+    s = sysin
+    tables = O.atom_tables(s.R, s.species, s.n, s.h)
+    g = O.ion_charge(tables, s.species, s.n)
+    v_loc = O.poisson(-g, s.h)
+    rho = O.density(s.psi, s.occ)
+    v_h = O.poisson(rho, s.h)
+    _, vxc = O.lda_pz81(rho)
+    H = O.Hamiltonian(v_loc + v_h + vxc, tables, s.species, s.h, s.fd_order)
+    psi = np.ascontiguousarray(s.psi[:n_orb_sample])
+    tau = 0.5 * (s.dt / s.mu)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        out = O.taylor4(O.taylor4(psi, tau, H), tau, H)
+    dt = time.perf_counter() - t0
+    upd = 8.0 * n_orb_sample * s.n ** 3 * reps
+    return upd / dt, dt, os.cpu_count()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_0812_2801_gb300 import inputs
+    s = inputs.precision_c96(mu=10.0)
+    n_sample = 1
+    for _ in range(args.warmup):
+        cpu_oracle_rate(s, n_sample)
+    times = []
+    for _ in range(args.steps):
+        _, dt, cores = cpu_oracle_rate(s, n_sample)
+        times.append(dt)
+    tot = sum(times)
+    value = 8.0 * n_sample * s.n ** 3 * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "precision-64at-96^3 (Si-like, 128 orbitals, order 8, mu 10)",
+                   "sample": f"{n_sample} of 128 orbitals per step, full potential"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"one AETRS step (8 H applications) on {n_sample} of 128 orbitals of the 96^3 workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def time_md(emd, torch, sysin, precision, steps, warmup, profile=True):
+    """Device-resident timing of `steps` MD steps; returns dict."""
+    sysg = emd.System(sysin, precision)
+    h = sysg.handle
+    for _ in range(warmup):
+        sysg.propagate(1)
+    torch.cuda.synchronize()
+    emd.emd_set_option(h, emd.EMD_OPT_PROFILE, 1 if profile else 0)
+    emd.emd_kernel_stats(h, emd.EMD_KERNEL_HORNER)
+    emd.emd_kernel_stats(h, emd.EMD_KERNEL_ALL)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record()
+    for _ in range(steps):
+        sysg.propagate(1)
+    stop.record()
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(stop)
+    k_ms, k_n = emd.emd_kernel_stats(h, emd.EMD_KERNEL_HORNER)
+    _, launches = emd.emd_kernel_stats(h, emd.EMD_KERNEL_ALL)
+    emd.emd_set_option(h, emd.EMD_OPT_PROFILE, 0)
+    e = sysg.energy()
+    sysg.close()
+    return {"ms": ms, "stage_ms": k_ms, "stage_launches": k_n, "launches": launches,
+            "energy": e}
+
+
+def time_e2e(emd, torch, sysin, precision, steps):
+    """Through the public API with host buffers: every step uploads orbitals
+    and ions from pinned memory, propagates one MD step and reads back the
+    orbitals, forces and energy."""
+    import numpy as np
+    s = sysin
+    psi_pin = torch.empty(s.psi.shape, dtype=torch.complex128, pin_memory=True)
+    psi_pin.numpy()[...] = s.psi
+    out_pin = torch.empty(s.psi.shape, dtype=torch.complex128, pin_memory=True)
+    R = np.ascontiguousarray(s.R)
+    V = np.ascontiguousarray(s.V)
+    h = emd.emd_init_system(emd.config_for(s, precision))
+    psi_np = psi_pin.numpy()
+    out_np = out_pin.numpy()
+    import ctypes
+    lib = emd.load()
+    DP = ctypes.POINTER(ctypes.c_double)
+
+    def one():
+        emd.emd_set_ions(h, R, V)
+        emd.emd_set_orbitals(h, psi_np)
+        emd.emd_propagate(h, 1, s.dt, s.mu)
+        emd._check(lib.emd_get_state(h, None, None,
+                                     out_np.view(np.float64).ctypes.data_as(DP), None))
+        emd.emd_get_forces(h, s.n_atoms)
+        emd.emd_get_energy(h)
+
+    one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    emd.emd_destroy(h)
+    bi = s.psi.nbytes + R.nbytes + V.nbytes
+    bo = s.psi.nbytes + 3 * 8 * s.n_atoms + 9 * 8
+    return dt, bi, bo
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_0812_2801_gb300 import emd, inputs
+    emd.load()
+
+    s = inputs.precision_c96(mu=10.0)
+    n3 = s.n ** 3
+    upd_per_step = 8.0 * s.n_orb * n3
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # headline: FP32 orbitals
+    barrier()
+    with ClockSampler(local) as clk:
+        r32 = time_md(emd, torch, s, emd.EMD_FP32_ORBITALS, args.steps, args.warmup)
+    barrier()
+    ms = r32["ms"]
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * upd_per_step * args.steps / (ms * 1e-3)
+
+    # FP64 form on the same workload
+    r64 = time_md(emd, torch, s, emd.EMD_FP64, args.fp64_steps, 1)
+    v64 = upd_per_step * args.fp64_steps / (r64["ms"] * 1e-3)
+
+    # end to end through the C ABI with host buffers
+    e2e_dt, bi, bo = time_e2e(emd, torch, s, emd.EMD_FP32_ORBITALS, args.e2e_steps)
+    e2e_val = ws * upd_per_step * args.e2e_steps / e2e_dt
+
+    peak, peak_kind = measured_peaks()
+    stage_avg_s = r32["stage_ms"] * 1e-3 / max(1, r32["stage_launches"])
+    bytes_launch = BYTES_PER_UPDATE["f32"] * s.n_orb * n3
+    achieved = bytes_launch / stage_avg_s / 1e9
+    stage64_s = r64["stage_ms"] * 1e-3 / max(1, r64["stage_launches"])
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "precision-64at-96^3: 64 Si-like atoms, 128 orbitals, "
+                               "96^3 at 0.25 bohr, order 8, mu 10, dt 0.158; complex64 "
+                               "orbitals, FP64 rho/energy/forces/ions",
+                   "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (orbital set 906 MB)",
+                   "md_steps_per_s": ws * args.steps / (ms * 1e-3)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": TRAFFIC_PER_LAUNCH["f32"],
+                     "kernel": "horner_stage (FP32)",
+                     "bytes_per_launch": bytes_launch,
+                     "avg_launch_ms": stage_avg_s * 1e3},
+        "fp64": {"value": v64, "unit": UNIT, "ms_per_step": r64["ms"] / args.fp64_steps,
+                 "horner_stage_avg_ms": stage64_s * 1e3,
+                 "speedup_fp32_over_fp64": value / ws / v64},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bi,
+                "d2h_bytes_per_step": bo,
+                "note": "per step: set_ions + set_orbitals (pinned host, complex128), "
+                        "propagate 1 MD step, get_state(psi) + get_forces + get_energy"},
+        "gpu_launches": r32["launches"],
+        "clocks": clk.summary(),
+        "energy_total": r32["energy"]["total"],
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, secs, cores = cpu_oracle_rate(s, 8)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"one AETRS step (8 H applications) on 8 of 128 "
+                                          f"orbitals of the 96^3 workload ({secs:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

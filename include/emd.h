@@ -1,0 +1,197 @@
+/*
+ * emd.h -- C ABI of libemd, a GB300 (sm_103a) implementation of the
+ * per-step propagation of the modified Ehrenfest TDDFT molecular dynamics of
+ * Alonso, Andrade et al., arXiv:0812.2801.
+ *
+ * The method (paper, Sec. 4.1 eq. new_L and eq. new_EoM; Sec. 5.1):
+ *   i mu dphi_A/dt = H_KS phi_A          (complex Kohn-Sham orbitals)
+ *   M_J d^2 R_J/dt^2 = -grad_J E_KS      (classical ions)
+ * with E_KS of eq. E_KS on a periodic real-space grid with finite-difference
+ * derivatives (Sec. 5).  One step = velocity-Verlet positions, AETRS
+ * (eq. aetrs) with each half exponential exp(-i tau H), tau = dt/(2 mu)
+ * (eq. transf), replaced by its degree-4 Taylor polynomial (Sec. 5.1), the new
+ * density rho = f sum_A |phi_A|^2 (eq. density), Hartree + LDA potentials,
+ * Hellmann-Feynman forces and velocity-Verlet velocities.
+ *
+ * Units: atomic units throughout (bohr, hartree, electron mass, hbar = 1).
+ * Grid: N^3 points, spacing h, box [0, N h)^3, periodic.  Point (x, y, z)
+ * has coordinates (x h, y h, z h) and canonical flat index (z N + y) N + x.
+ *
+ * Conventions for every entry point:
+ *   - Return value: EMD_OK (0) or a positive EMD_E* status.  Nothing is
+ *     thrown across the ABI.  emd_last_error() returns a message for the
+ *     last failure on the calling thread (valid until the next call).
+ *   - Host pointers are owned by the caller; the library copies what it
+ *     needs before returning (inputs) or writes complete results (outputs).
+ *   - Device memory is owned by the library (cudaMalloc at emd_init_system,
+ *     released by emd_destroy).  Work is issued on the caller's CUDA stream
+ *     (emd_config.cuda_stream; NULL = the legacy default stream).
+ *   - Calls that return data to the host (emd_get_*) synchronise that stream;
+ *     emd_propagate only enqueues work.  Device-side consistency problems
+ *     found during propagation (a table overflow) are reported by the next
+ *     emd_get_* call.
+ *   - A system handle must not be used from two threads at once.
+ */
+#ifndef EMD_H
+#define EMD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define EMD_OK        0
+#define EMD_EINVAL    1   /* bad argument (sizes, order, neutrality, NULL) */
+#define EMD_ENOMEM    2   /* device or pinned host allocation failed      */
+#define EMD_ECUDA     3   /* a CUDA runtime call failed                   */
+#define EMD_EUNSTABLE 4   /* tau * lambda_max above the Taylor-4 bound, or
+                             the density lost its normalisation           */
+#define EMD_ESTATE    5   /* call out of order (e.g. propagate before
+                             orbitals and ions are set)                   */
+#define EMD_ETABLE    6   /* a per-point or per-tile atom list overflowed */
+
+/* orbital storage precision */
+#define EMD_FP64           0  /* complex128 orbitals, FP64 stencil          */
+#define EMD_FP32_ORBITALS  1  /* complex64 orbitals and stencil; density,
+                                 energies, forces and ions stay FP64        */
+
+/* options for emd_set_option */
+#define EMD_OPT_FROZEN_IONS  1  /* value != 0: ions fixed, no forces/VV      */
+#define EMD_OPT_PROFILE      2  /* value != 0: time Horner-stage launches     */
+#define EMD_OPT_CHECK_STABLE 3  /* value == 0: skip the stability refusal    */
+
+/* kernels that can be timed with EMD_OPT_PROFILE */
+#define EMD_KERNEL_HORNER    0  /* one Taylor/Horner stage u' = psi0 + a H u */
+#define EMD_KERNEL_ALL       1  /* every kernel the library launched (count
+                                   only, process-wide; ms_total = 0)      */
+
+/*
+ * Synthetic pseudo-atom (the paper uses Troullier-Martins pseudopotentials,
+ * Sec. 5; this stands in with the same structure: a local part plus a
+ * separable nonlocal part).
+ *   z       valence charge Z
+ *   mass    ionic mass M (electron masses)
+ *   a_loc   Gaussian ion charge g(d) = Z pi^-3/2 a^-3 exp(-d^2/a^2), so that
+ *           the local potential is -Z erf(d/a)/d (eq. ionicpotential)
+ *   r_loc   support radius of g on the grid (points with d < r_loc)
+ *   r_c     projector p(d) = pi^-3/4 r_c^-3/2 exp(-d^2/(2 r_c^2))
+ *   h_kb    strength of the term h_kb |p><p|
+ *   r_proj  support radius of p on the grid (d < r_proj)
+ * Both radii must not exceed the box length N h.
+ */
+typedef struct {
+  double z, mass, a_loc, r_loc, r_c, h_kb, r_proj;
+} emd_species;
+
+typedef struct {
+  int n;                 /* grid points per axis, 2*fd_order <= n <= 1024,
+                            and n may have no prime factor above 13     */
+  double h;              /* grid spacing (bohr), > 0                     */
+  int fd_order;          /* finite-difference order: 2, 4, 6 or 8        */
+  int n_orb;             /* number of orbitals, >= 1                     */
+  double occ;            /* occupation per orbital (2 = closed shell)    */
+  int precision;         /* EMD_FP64 or EMD_FP32_ORBITALS                */
+  int n_atoms;           /* number of atoms, >= 0                        */
+  emd_species species;   /* one species for all atoms                    */
+  void *cuda_stream;     /* cudaStream_t to issue work on, or NULL        */
+  int block_orbitals;    /* orbitals interleaved per grid point; 0 = auto */
+} emd_config;
+
+/* Energy components (hartree), eq. E_KS and eq. E_new:
+ *   kin_e   sum_A f <phi_A| -1/2 nabla^2_FD |phi_A>
+ *   nl      sum_{J,A} f h_kb |<p_J|phi_A>|^2
+ *   es      electrostatics: 1/2 h^3 sum n_tot v_es - sum_J Z^2/(sqrt(2 pi) a)
+ *           + sr, with n_tot = rho - sum_J g_J and v_es its periodic
+ *           potential (the G = 0 component is dropped)
+ *   xc      h^3 sum rho eps_xc (Perdew-Zunger LDA)
+ *   sr      1/2 sum' Z_J Z_K erfc(d/(sqrt2 a))/d over images, d < 12 bohr
+ *           (already included in es)
+ *   kin_ion sum_J M |V_J|^2 / 2
+ *   ks      kin_e + nl + es + xc
+ *   total   ks + kin_ion (the conserved energy of eq. E_new)
+ *   n_elec  h^3 sum rho (health check: equals n_orb * occ)            */
+typedef struct {
+  double kin_e, nl, es, xc, sr, kin_ion, ks, total, n_elec;
+} emd_energy;
+
+typedef struct emd_system emd_system;
+
+/* Create a system: validates cfg, allocates all device buffers.  *out is set
+ * on success.  Errors: EMD_EINVAL, EMD_ENOMEM, EMD_ECUDA. */
+int emd_init_system(const emd_config *cfg, emd_system **out);
+
+/* Set ions: R[n_atoms][3], V[n_atoms][3] (host, float64; x, y, z).
+ * n_atoms must equal cfg.n_atoms.  Positions may lie outside the box; they
+ * are folded with X - L floor(X/L) wherever a grid support is built.
+ * Recomputes the ionic potential; if orbitals are set, also rho, v_Hxc and
+ * F(0) and restarts the v_Hxc history. */
+int emd_set_ions(emd_system *s, int n_atoms, const double *R, const double *V);
+
+/* Set orbitals: psi is complex128 interleaved (re, im), canonical layout
+ * [n_orb][N][N][N] (host).  Orbitals should be orthonormal under
+ * <a|b> = h^3 sum conj(a) b; they are not modified.  Recomputes rho, v_Hxc,
+ * F(0) (if ions are set) and restarts the v_Hxc history (Sec. 2,
+ * eq. Ehr_ic: initial condition). */
+int emd_set_orbitals(emd_system *s, const double *psi);
+
+/* Advance n_steps MD steps of length dt with the electronic mass-like
+ * parameter mu (mu = 1: plain Ehrenfest).  field: NULL, or n_steps
+ * amplitudes e_n (host) of a uniform field along z in the length gauge,
+ * v_ext = e_n (z - L/2), held during step n, force Z e_n on each ion.
+ * Refuses with EMD_EUNSTABLE if tau*lambda_max > 2 sqrt(2), the Taylor-4
+ * stability bound on the imaginary axis (lambda_max estimated as the
+ * largest FD kinetic eigenvalue + max v_eff + h_kb).  Enqueues only. */
+int emd_propagate(emd_system *s, int n_steps, double dt, double mu,
+                  const double *field);
+
+/* F[n_atoms][3] = -dE_KS/dR at the current state (eq. new_EoM_b). */
+int emd_get_forces(emd_system *s, double *F);
+
+/* Energy components at the current state (see emd_energy). */
+int emd_get_energy(emd_system *s, emd_energy *out);
+
+/* Current state; any pointer may be NULL.  R, V: [n_atoms][3];
+ * psi: complex128 canonical [n_orb][N][N][N]; rho: [N][N][N]. */
+int emd_get_state(emd_system *s, double *R, double *V, double *psi, double *rho);
+
+/* Grid potentials of the current state, each [N][N][N] or NULL:
+ * v_loc (ionic, eq. ionicpotential), v_h (Hartree), v_xc (LDA),
+ * g_ion (sum of the Gaussian ion charges). */
+int emd_get_potentials(emd_system *s, double *v_loc, double *v_h, double *v_xc,
+                       double *g_ion);
+
+/* Projections c[n_atoms][n_orb] complex128 (re, im) of the current orbitals:
+ * c_JA = h^3 sum_r p_J(r) phi_A(r) (the separable term of H). */
+int emd_get_projections(emd_system *s, double *c);
+
+/* hpsi = H psi for n_vec orbitals (complex128 canonical [n_vec][N][N][N],
+ * host), with H = -1/2 nabla^2_FD + v_eff + sum_J h_kb |p_J><p_J| of the
+ * current state: v_eff = v_loc + v_H + v_xc, projectors at the current R
+ * (eq. new_EoM_a).  1 <= n_vec <= n_orb.  Uses the propagation kernels in
+ * the configured precision (FP32 mode rounds psi to complex64). */
+int emd_apply_hamiltonian(emd_system *s, int n_vec, const double *psi,
+                          double *hpsi);
+
+/* Set an EMD_OPT_* option. */
+int emd_set_option(emd_system *s, int option, double value);
+
+/* Accumulated device time (ms) and launch count of a timed kernel since
+ * EMD_OPT_PROFILE was enabled or the previous call (EMD_KERNEL_HORNER), or
+ * the number of kernels the library launched since the previous call
+ * (EMD_KERNEL_ALL).  Both counters reset on reading.  Synchronises. */
+int emd_kernel_stats(emd_system *s, int kernel, double *ms_total,
+                     long long *launches);
+
+/* Release all device memory and the handle.  NULL is accepted. */
+void emd_destroy(emd_system *s);
+
+/* Message of the last failure on this thread ("" if none). */
+const char *emd_last_error(void);
+
+/* Library version string. */
+const char *emd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EMD_H */

@@ -1,0 +1,180 @@
+// Internal declarations shared by the libemd translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "emd.h"
+
+#define EMD_PT_KMAX 16          // atoms per grid point in the point-major table
+#define EMD_TILE 8              // edge of the tiles that carry atom candidates
+#define EMD_TILE_CAND_MAX 160   // (atom, image) candidates per tile
+#define EMD_MAX_HALF_ORDER 6    // fd_order / 2 <= 6
+
+// error bits raised by kernels (device flag, read by emd_get_*)
+#define EMD_ERRBIT_PT   1       // per-point list overflow
+#define EMD_ERRBIT_TILE 2       // per-tile candidate overflow
+#define EMD_ERRBIT_AT   4       // per-atom table overflow
+
+template <typename T> struct cplx;
+template <> struct cplx<double> { typedef double2 type; };
+template <> struct cplx<float> { typedef float2 type; };
+
+struct SpeciesDev {
+  double z, mass, a_loc, r_loc, r_c, h_kb, r_proj;
+  double c_g;      // Z pi^-3/2 a^-3
+  double c_p;      // pi^-3/4 r_c^-3/2
+  double inv_a2;   // 1 / a^2
+  double inv_2rc2; // 1 / (2 r_c^2)
+  double inv_rc2;  // 1 / r_c^2
+};
+
+// One set of ion positions and every table derived from it.
+struct TableSet {
+  double *R;        // [n_atoms][3] positions as given (unwrapped)
+  double *Rw;       // [n_atoms][3] folded into [0, L)
+  int *tile_cnt;    // [n_tiles]
+  int *tile_ent;    // [n_tiles][EMD_TILE_CAND_MAX], J*27 + image
+  int *pt_cnt;      // [n3]
+  int *pt_J;        // [EMD_PT_KMAX][n3]
+  double *pt_p;     // [EMD_PT_KMAX][n3] p_J(r) summed over images
+  int *at_cnt;      // [n_atoms]
+  int *at_pt;       // [n_atoms][cap] flat grid index
+  double *at_p;     // [n_atoms][cap] p value of that (point, image)
+  double *at_d;     // [n_atoms][cap][3] displacement r - R_image
+  double *g_ion;    // [n3] sum of Gaussian ion charges
+  double *v_loc;    // [n3] Poisson(-g_ion)
+  int cap;
+};
+
+// ---------------------------------------------------------------------------
+// Exact displacement arithmetic.  The support decision d^2 < r^2 is an
+// integer decision taken in FP64 from the same operations, in the same
+// order and rounding, as the reference definition: no contraction into FMA.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double emd_wrap_pos(double X, double L) {
+  return __dsub_rn(X, __dmul_rn(L, floor(__ddiv_rn(X, L))));
+}
+__device__ __forceinline__ double emd_disp(int i, double h, double c, int nimg,
+                                           double L) {
+  return __dsub_rn(__dsub_rn(__dmul_rn((double)i, h), c),
+                   __dmul_rn((double)nimg, L));
+}
+__device__ __forceinline__ double emd_norm2(double dx, double dy, double dz) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                   __dmul_rn(dz, dz));
+}
+
+// Deterministic block reduction of NV doubles per thread (fixed tree order).
+// Requires blockDim.x a multiple of 32 and <= 1024.  Result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void emd_block_sum(double (&v)[NV], double *smem) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarp = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double a = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    v[k] = a;
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) smem[warp * NV + k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double a = 0.0;
+      for (int w = 0; w < nwarp; ++w) a += smem[w * NV + k];
+      v[k] = a;
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (defined in the .cu files).  All take the stream to issue on.
+// ---------------------------------------------------------------------------
+struct GridInfo {
+  int n, n3;
+  double h, L;
+};
+
+// Process-wide count of kernel launches issued by the library (for the
+// benchmark's launch count); defined in emd_api.cu.
+void emd_note_launches(int k);
+
+// tables.cu
+void emd_launch_wrap(const double *R, double *Rw, int n_atoms, double L,
+                     cudaStream_t st);
+void emd_launch_tables(const GridInfo &g, const SpeciesDev &sp, int n_atoms,
+                       TableSet &t, int *err, cudaStream_t st);
+void emd_launch_local_force(const GridInfo &g, const SpeciesDev &sp,
+                            int n_atoms, const double *Rw, const double *v_es_a,
+                            const double *v_es_b, double *F, cudaStream_t st);
+void emd_launch_short_range(const SpeciesDev &sp, int n_atoms, const double *R,
+                            double L, double *F, double *e_part,
+                            cudaStream_t st);
+void emd_launch_vv_positions(int n_atoms, const double *R, const double *V,
+                             const double *F, double dt, double mass,
+                             double *R_new, cudaStream_t st);
+void emd_launch_vv_velocities(int n_atoms, const double *F_loc,
+                              const double *F_nl, const double *F_sr,
+                              double field_z, double z, double *F,
+                              double *V, double dt, double mass, int update_v,
+                              cudaStream_t st);
+
+// poisson.cu
+void emd_fft_plan_check(int n, int *ok);   // host-only factor check
+int emd_fft_prepare(int n);                 // twiddle tables on the device
+void emd_launch_poisson(const GridInfo &g, const double *charge, double *v,
+                        double2 *work_a, double2 *work_b, cudaStream_t st);
+void emd_launch_lda(int n3, const double *rho, const double *v_h,
+                    double *eps_xc, double *v_xc, double *vhxc,
+                    cudaStream_t st);
+void emd_launch_veff(const GridInfo &g, const double *v_loc,
+                     const double *const *hist, int hist_len, double field,
+                     double *v_eff, float *v_eff_f, cudaStream_t st);
+// partials[b] = block sums of (a - c)(b + d); c, d, b may be NULL
+void emd_launch_dot_partials(int n3, const double *a, const double *b,
+                             const double *c, const double *d,
+                             double *partials, int nblocks, cudaStream_t st);
+void emd_launch_sum(const double *partials, int n, double *out,
+                    cudaStream_t st);
+
+// hpsi.cu
+struct StageArgs {
+  const void *u_in;
+  const void *psi0;
+  void *u_out;
+  const void *v_eff;       // double* (FP64) or float* (FP32)
+  const TableSet *tab;
+  const void *hc;          // [n_atoms][n_orb_pad] h_kb*c in orbital precision
+  double a;                // tau / k ; u_out = psi0 + (-i a) H u_in
+  int apply_only;          // 1: u_out = H u_in (psi0 unused)
+};
+struct OrbLayout {
+  int n, n3, bo, n_blk, n_orb, n_orb_pad, prec, half_order;
+  double h;
+  double w[EMD_MAX_HALF_ORDER + 1];   // w_0 = -3 c_0 / (2 h^2), w_k = -c_k/(2 h^2)
+};
+void emd_launch_stage(const OrbLayout &o, const StageArgs &a, cudaStream_t st);
+void emd_launch_project(const OrbLayout &o, const TableSet &t, int n_atoms,
+                        const void *u, double h3, double h_kb, double2 *c,
+                        void *hc, cudaStream_t st);
+void emd_launch_density(const OrbLayout &o, const void *u, double occ,
+                        double *rho, cudaStream_t st);
+void emd_launch_kinetic_partials(const OrbLayout &o, const void *u,
+                                 double *partials, int *nparts,
+                                 cudaStream_t st);
+void emd_launch_nl_force(const OrbLayout &o, const TableSet &t, int n_atoms,
+                         const void *u, const double2 *c, double h3,
+                         double coef, double inv_rc2, double *part,
+                         double *F_nl, cudaStream_t st);
+void emd_launch_pack(const OrbLayout &o, const double2 *canon, void *u,
+                     int n_vec, cudaStream_t st);
+void emd_launch_unpack(const OrbLayout &o, const void *u, double2 *canon,
+                       int n_vec, cudaStream_t st);
+void emd_launch_abs2_sum(const double2 *c, int n, double *out,
+                         cudaStream_t st);

@@ -1,0 +1,519 @@
+// The hot loop: one Taylor/Horner stage u_out = psi0 + (-i a) H u_in with
+//   H = -1/2 nabla^2_FD + v_eff + sum_J h_kb |p_J><p_J|     (eq. new_EoM_a)
+// on a periodic grid, plus the projections c_JA = <p_J|u_A>, the density
+// rho = f sum_A |phi_A|^2 (eq. density), the kinetic energy of eq. E_KS and
+// the nonlocal part of the Hellmann-Feynman force (eq. new_EoM_b).
+//
+// The degree-4 Taylor polynomial of exp(-i tau H) (Sec. 5.1) is evaluated in
+// nested form: u4 = psi0 + (-i tau/4) H psi0, u_k = psi0 + (-i tau/k) H u_{k+1},
+// k = 3, 2, 1, result u1.  Four stages per exponential, two exponentials per
+// AETRS step (eq. aetrs).
+//
+// Orbital layout: [block][n^3][bo] complex, bo orbitals of a block interleaved
+// per grid point, so one thread updates bo orbitals at one point and shares
+// the potential, the projector list and the index arithmetic between them.
+#include "emd_internal.cuh"
+
+namespace {
+
+// Stencil weights passed by value (kernel parameter space): w_0 = -3 c_0/(2h^2),
+// w_k = -c_k/(2h^2), so the kinetic term is w_0 u + sum_k w_k (6 neighbours).
+template <typename T> struct Weights { T w[EMD_MAX_HALF_ORDER + 1]; };
+
+template <typename T> Weights<T> weights_of(const OrbLayout &o) {
+  Weights<T> r;
+  for (int k = 0; k <= EMD_MAX_HALF_ORDER; ++k) r.w[k] = (T)o.w[k];
+  return r;
+}
+
+template <typename T, int BO, int M>
+__global__ void __launch_bounds__(128)
+k_stage(const typename cplx<T>::type *__restrict__ u_in,
+        const typename cplx<T>::type *__restrict__ psi0,
+        typename cplx<T>::type *__restrict__ u_out, const T *__restrict__ v_eff,
+        const int *__restrict__ pt_cnt, const int *__restrict__ pt_J,
+        const double *__restrict__ pt_p,
+        const typename cplx<T>::type *__restrict__ hc, int n, int ntx,
+        int n_orb_pad, T a, int apply_only, Weights<T> W) {
+  typedef typename cplx<T>::type V;
+  const int x = (blockIdx.x % ntx) * 32 + threadIdx.x;
+  const int y = (blockIdx.x / ntx) * 4 + threadIdx.y;
+  const int z = blockIdx.y;
+  const int blk = blockIdx.z;
+  if (x >= n || y >= n) return;
+  const size_t n3 = (size_t)n * n * n;
+  const int p = (z * n + y) * n + x;
+  const V *ub = u_in + (size_t)blk * n3 * BO;
+
+  V c0[BO], acc[BO];
+#pragma unroll
+  for (int j = 0; j < BO; ++j) {
+    c0[j] = ub[(size_t)p * BO + j];
+    acc[j].x = W.w[0] * c0[j].x;
+    acc[j].y = W.w[0] * c0[j].y;
+  }
+#pragma unroll
+  for (int k = 1; k <= M; ++k) {
+    int xp = x + k, xm = x - k, yp = y + k, ym = y - k, zp = z + k, zm = z - k;
+    if (xp >= n) xp -= n;
+    if (xm < 0) xm += n;
+    if (yp >= n) yp -= n;
+    if (ym < 0) ym += n;
+    if (zp >= n) zp -= n;
+    if (zm < 0) zm += n;
+    const size_t row = (size_t)(z * n + y) * n;
+    const size_t q[6] = {row + xp, row + xm, (size_t)(z * n + yp) * n + x,
+                         (size_t)(z * n + ym) * n + x, (size_t)(zp * n + y) * n + x,
+                         (size_t)(zm * n + y) * n + x};
+    const T w = W.w[k];
+#pragma unroll
+    for (int j = 0; j < BO; ++j) {
+      T sx = 0, sy = 0;
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        const V v = ub[q[e] * BO + j];
+        sx += v.x;
+        sy += v.y;
+      }
+      acc[j].x += w * sx;
+      acc[j].y += w * sy;
+    }
+  }
+  const T ve = v_eff[p];
+#pragma unroll
+  for (int j = 0; j < BO; ++j) {
+    acc[j].x += ve * c0[j].x;
+    acc[j].y += ve * c0[j].y;
+  }
+  const int cnt = pt_cnt[p];
+  for (int e = 0; e < cnt; ++e) {
+    const int J = pt_J[(size_t)e * n3 + p];
+    const T pv = (T)pt_p[(size_t)e * n3 + p];
+    const V *hcj = hc + (size_t)J * n_orb_pad + (size_t)blk * BO;
+#pragma unroll
+    for (int j = 0; j < BO; ++j) {
+      const V c = hcj[j];
+      acc[j].x += pv * c.x;
+      acc[j].y += pv * c.y;
+    }
+  }
+  V *ob = u_out + (size_t)blk * n3 * BO + (size_t)p * BO;
+  if (apply_only) {
+#pragma unroll
+    for (int j = 0; j < BO; ++j) ob[j] = acc[j];
+  } else {
+    const V *pb = psi0 + (size_t)blk * n3 * BO + (size_t)p * BO;
+#pragma unroll
+    for (int j = 0; j < BO; ++j) {
+      const V s = pb[j];
+      V o;
+      o.x = s.x + a * acc[j].y;
+      o.y = s.y - a * acc[j].x;
+      ob[j] = o;
+    }
+  }
+}
+
+// c[J][A] = h^3 sum_e p_e u_A(pt_e) over atom J's (point, image) entries;
+// hc = h_kb c in orbital precision.  One block per (atom, orbital block).
+template <typename T, int BO>
+__global__ void __launch_bounds__(256)
+k_project(const typename cplx<T>::type *__restrict__ u, size_t n3,
+          const int *__restrict__ at_cnt, const int *__restrict__ at_pt,
+          const double *__restrict__ at_p, int cap, double h3, double h_kb,
+          int n_orb_pad, double2 *c, typename cplx<T>::type *hc) {
+  typedef typename cplx<T>::type V;
+  __shared__ double red[8 * 2 * BO];
+  const int J = blockIdx.x, blk = blockIdx.y;
+  const int cnt = at_cnt[J];
+  const V *ub = u + (size_t)blk * n3 * BO;
+  double acc[2 * BO];
+#pragma unroll
+  for (int k = 0; k < 2 * BO; ++k) acc[k] = 0.0;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const size_t idx = (size_t)J * cap + e;
+    const int pt = at_pt[idx];
+    const double pv = at_p[idx];
+#pragma unroll
+    for (int j = 0; j < BO; ++j) {
+      const V v = ub[(size_t)pt * BO + j];
+      acc[2 * j] += pv * (double)v.x;
+      acc[2 * j + 1] += pv * (double)v.y;
+    }
+  }
+  emd_block_sum<2 * BO>(acc, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < BO; ++j) {
+      const size_t o = (size_t)J * n_orb_pad + (size_t)blk * BO + j;
+      const double re = h3 * acc[2 * j], im = h3 * acc[2 * j + 1];
+      c[o] = make_double2(re, im);
+      V w;
+      w.x = (T)(h_kb * re);
+      w.y = (T)(h_kb * im);
+      hc[o] = w;
+    }
+  }
+}
+
+template <typename T, int BO>
+__global__ void k_density(const typename cplx<T>::type *__restrict__ u,
+                          size_t n3, int n_blk, double occ, double *rho) {
+  typedef typename cplx<T>::type V;
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n3) return;
+  double acc = 0.0;
+  for (int b = 0; b < n_blk; ++b) {
+    const V *ub = u + ((size_t)b * n3 + p) * BO;
+#pragma unroll
+    for (int j = 0; j < BO; ++j) {
+      const double re = (double)ub[j].x, im = (double)ub[j].y;
+      acc += re * re + im * im;
+    }
+  }
+  rho[p] = occ * acc;
+}
+
+// partial[b] = sum over the points of block b and all orbitals of
+// Re(conj(u) (-1/2 nabla^2_FD u)), FP64.
+template <typename T, int BO, int M>
+__global__ void __launch_bounds__(256)
+k_kinetic(const typename cplx<T>::type *__restrict__ u, int n, int n_blk,
+          double *part, Weights<double> W) {
+  typedef typename cplx<T>::type V;
+  __shared__ double red[8];
+  const size_t n3 = (size_t)n * n * n;
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  if (p < n3) {
+    const int x = p % n, y = (p / n) % n, z = p / ((size_t)n * n);
+    for (int b = 0; b < n_blk; ++b) {
+      const V *ub = u + (size_t)b * n3 * BO;
+      for (int j = 0; j < BO; ++j) {
+        const V c0 = ub[p * BO + j];
+        double lx = W.w[0] * (double)c0.x, ly = W.w[0] * (double)c0.y;
+        for (int k = 1; k <= M; ++k) {
+          const int xp = (x + k) % n, xm = (x - k + n) % n;
+          const int yp = (y + k) % n, ym = (y - k + n) % n;
+          const int zp = (z + k) % n, zm = (z - k + n) % n;
+          const size_t q[6] = {(size_t)(z * n + y) * n + xp, (size_t)(z * n + y) * n + xm,
+                               (size_t)(z * n + yp) * n + x, (size_t)(z * n + ym) * n + x,
+                               (size_t)(zp * n + y) * n + x, (size_t)(zm * n + y) * n + x};
+          double sx = 0, sy = 0;
+          for (int e = 0; e < 6; ++e) {
+            const V v = ub[q[e] * BO + j];
+            sx += (double)v.x;
+            sy += (double)v.y;
+          }
+          lx += W.w[k] * sx;
+          ly += W.w[k] * sy;
+        }
+        acc[0] += (double)c0.x * lx + (double)c0.y * ly;
+      }
+    }
+  }
+  emd_block_sum<1>(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
+}
+
+// Nonlocal force partials: for atom J and orbital block blk,
+// part[J][blk][a] = coef * sum_j Re(conj(c_JA) dc_JA,a),
+// dc_JA,a = h^3 sum_e p_e d_e,a / r_c^2 u_A(pt_e)  (= d c_JA / d R_J,a).
+template <typename T, int BO>
+__global__ void __launch_bounds__(256)
+k_nl_force(const typename cplx<T>::type *__restrict__ u, size_t n3, int n_blk,
+           const int *__restrict__ at_cnt, const int *__restrict__ at_pt,
+           const double *__restrict__ at_p, const double *__restrict__ at_d,
+           int cap, const double2 *__restrict__ c, int n_orb_pad, int n_orb,
+           double h3, double coef, double inv_rc2, double *part) {
+  typedef typename cplx<T>::type V;
+  __shared__ double red[8 * 6 * BO];
+  const int J = blockIdx.x, blk = blockIdx.y;
+  const int cnt = at_cnt[J];
+  const V *ub = u + (size_t)blk * n3 * BO;
+  double acc[6 * BO];
+#pragma unroll
+  for (int k = 0; k < 6 * BO; ++k) acc[k] = 0.0;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const size_t idx = (size_t)J * cap + e;
+    const int pt = at_pt[idx];
+    const double pv = at_p[idx] * inv_rc2;
+    const double d0 = at_d[3 * idx], d1 = at_d[3 * idx + 1], d2 = at_d[3 * idx + 2];
+#pragma unroll
+    for (int j = 0; j < BO; ++j) {
+      const V v = ub[(size_t)pt * BO + j];
+      const double wr = pv * (double)v.x, wi = pv * (double)v.y;
+      acc[6 * j + 0] += wr * d0;
+      acc[6 * j + 1] += wi * d0;
+      acc[6 * j + 2] += wr * d1;
+      acc[6 * j + 3] += wi * d1;
+      acc[6 * j + 4] += wr * d2;
+      acc[6 * j + 5] += wi * d2;
+    }
+  }
+  emd_block_sum<6 * BO>(acc, red);
+  if (threadIdx.x == 0) {
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < BO; ++j) {
+      const int A = blk * BO + j;
+      if (A >= n_orb) continue;
+      const double2 cj = c[(size_t)J * n_orb_pad + A];
+      for (int a = 0; a < 3; ++a) {
+        const double dr = h3 * acc[6 * j + 2 * a], di = h3 * acc[6 * j + 2 * a + 1];
+        f[a] += cj.x * dr + cj.y * di;   // Re(conj(c) dc)
+      }
+    }
+    for (int a = 0; a < 3; ++a)
+      part[((size_t)J * n_blk + blk) * 3 + a] = coef * f[a];
+  }
+}
+
+__global__ void k_nl_force_sum(const double *part, int n_atoms, int n_blk,
+                               double *F) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * n_atoms) return;
+  const int J = i / 3, a = i % 3;
+  double s = 0.0;
+  for (int b = 0; b < n_blk; ++b) s += part[((size_t)J * n_blk + b) * 3 + a];
+  F[i] = s;
+}
+
+template <typename T, int BO>
+__global__ void k_pack(const double2 *__restrict__ canon,
+                       typename cplx<T>::type *__restrict__ u, size_t n3,
+                       int n_vec, int n_blk_vec) {
+  typedef typename cplx<T>::type V;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t tot = (size_t)n_blk_vec * n3 * BO;
+  if (i >= tot) return;
+  const int j = i % BO;
+  const size_t p = (i / BO) % n3;
+  const int b = i / (BO * n3);
+  const int A = b * BO + j;
+  V v;
+  if (A < n_vec) {
+    const double2 s = canon[(size_t)A * n3 + p];
+    v.x = (T)s.x;
+    v.y = (T)s.y;
+  } else {
+    v.x = 0;
+    v.y = 0;
+  }
+  u[i] = v;
+}
+
+template <typename T, int BO>
+__global__ void k_unpack(const typename cplx<T>::type *__restrict__ u,
+                         double2 *__restrict__ canon, size_t n3, int n_vec) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)n_vec * n3) return;
+  const int A = i / n3;
+  const size_t p = i % n3;
+  const int b = A / BO, j = A % BO;
+  const typename cplx<T>::type v = u[((size_t)b * n3 + p) * BO + j];
+  canon[i] = make_double2((double)v.x, (double)v.y);
+}
+
+__global__ void __launch_bounds__(256)
+k_abs2_sum(const double2 *c, int n, double *out) {
+  __shared__ double red[8];
+  double acc[1] = {0.0};
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    acc[0] += c[i].x * c[i].x + c[i].y * c[i].y;
+  emd_block_sum<1>(acc, red);
+  if (threadIdx.x == 0) *out = acc[0];
+}
+
+// ---- dispatch -------------------------------------------------------------
+
+template <typename T, int BO, int M>
+void stage_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
+  typedef typename cplx<T>::type V;
+  const int ntx = (o.n + 31) / 32, nty = (o.n + 3) / 4;
+  dim3 grid(ntx * nty, o.n, o.n_blk), block(32, 4);
+  k_stage<T, BO, M><<<grid, block, 0, st>>>(
+      (const V *)a.u_in, (const V *)a.psi0, (V *)a.u_out, (const T *)a.v_eff,
+      a.tab->pt_cnt, a.tab->pt_J, a.tab->pt_p, (const V *)a.hc, o.n, ntx,
+      o.n_orb_pad, (T)a.a, a.apply_only, weights_of<T>(o));
+}
+
+template <typename T, int BO>
+void stage_m(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
+  switch (o.half_order) {
+    case 1: stage_t<T, BO, 1>(o, a, st); break;
+    case 2: stage_t<T, BO, 2>(o, a, st); break;
+    case 3: stage_t<T, BO, 3>(o, a, st); break;
+    case 4: stage_t<T, BO, 4>(o, a, st); break;
+  }
+}
+
+#define EMD_DISPATCH_BO(T, FN, ...)                  \
+  switch (o.bo) {                                    \
+    case 1: FN<T, 1>(__VA_ARGS__); break;            \
+    case 2: FN<T, 2>(__VA_ARGS__); break;            \
+    case 4: FN<T, 4>(__VA_ARGS__); break;            \
+  }
+
+template <typename T, int BO>
+void project_t(const OrbLayout &o, const TableSet &t, int n_atoms,
+               const void *u, double h3, double h_kb, double2 *c, void *hc,
+               cudaStream_t st) {
+  typedef typename cplx<T>::type V;
+  dim3 grid(n_atoms, o.n_blk);
+  k_project<T, BO><<<grid, 256, 0, st>>>((const V *)u, (size_t)o.n3, t.at_cnt,
+                                         t.at_pt, t.at_p, t.cap, h3, h_kb,
+                                         o.n_orb_pad, c, (V *)hc);
+}
+
+template <typename T, int BO>
+void density_t(const OrbLayout &o, const void *u, double occ, double *rho,
+               cudaStream_t st) {
+  typedef typename cplx<T>::type V;
+  k_density<T, BO><<<(o.n3 + 255) / 256, 256, 0, st>>>((const V *)u,
+                                                       (size_t)o.n3, o.n_blk,
+                                                       occ, rho);
+}
+
+template <typename T, int BO, int M>
+void kinetic_tm(const OrbLayout &o, const void *u, double *part, int nb,
+                cudaStream_t st) {
+  typedef typename cplx<T>::type V;
+  k_kinetic<T, BO, M><<<nb, 256, 0, st>>>((const V *)u, o.n, o.n_blk, part,
+                                          weights_of<double>(o));
+}
+template <typename T, int BO>
+void kinetic_t(const OrbLayout &o, const void *u, double *part, int nb,
+               cudaStream_t st) {
+  switch (o.half_order) {
+    case 1: kinetic_tm<T, BO, 1>(o, u, part, nb, st); break;
+    case 2: kinetic_tm<T, BO, 2>(o, u, part, nb, st); break;
+    case 3: kinetic_tm<T, BO, 3>(o, u, part, nb, st); break;
+    case 4: kinetic_tm<T, BO, 4>(o, u, part, nb, st); break;
+  }
+}
+
+template <typename T, int BO>
+void nlf_t(const OrbLayout &o, const TableSet &t, int n_atoms, const void *u,
+           const double2 *c, double h3, double coef, double inv_rc2,
+           double *part, cudaStream_t st) {
+  typedef typename cplx<T>::type V;
+  dim3 grid(n_atoms, o.n_blk);
+  k_nl_force<T, BO><<<grid, 256, 0, st>>>((const V *)u, (size_t)o.n3, o.n_blk,
+                                          t.at_cnt, t.at_pt, t.at_p, t.at_d,
+                                          t.cap, c, o.n_orb_pad, o.n_orb, h3,
+                                          coef, inv_rc2, part);
+}
+
+template <typename T, int BO>
+void pack_t(const OrbLayout &o, const double2 *canon, void *u, int n_vec,
+            cudaStream_t st) {
+  typedef typename cplx<T>::type V;
+  const int nbv = (n_vec + BO - 1) / BO;
+  const size_t tot = (size_t)nbv * o.n3 * BO;
+  k_pack<T, BO><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+      canon, (V *)u, (size_t)o.n3, n_vec, nbv);
+}
+
+template <typename T, int BO>
+void unpack_t(const OrbLayout &o, const void *u, double2 *canon, int n_vec,
+              cudaStream_t st) {
+  typedef typename cplx<T>::type V;
+  const size_t tot = (size_t)n_vec * o.n3;
+  k_unpack<T, BO><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+      (const V *)u, canon, (size_t)o.n3, n_vec);
+}
+
+}  // namespace
+
+void emd_launch_stage(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
+  emd_note_launches(1);
+  if (o.prec == EMD_FP64) {
+    switch (o.bo) {
+      case 1: stage_m<double, 1>(o, a, st); break;
+      case 2: stage_m<double, 2>(o, a, st); break;
+      case 4: stage_m<double, 4>(o, a, st); break;
+    }
+  } else {
+    switch (o.bo) {
+      case 1: stage_m<float, 1>(o, a, st); break;
+      case 2: stage_m<float, 2>(o, a, st); break;
+      case 4: stage_m<float, 4>(o, a, st); break;
+    }
+  }
+}
+
+void emd_launch_project(const OrbLayout &o, const TableSet &t, int n_atoms,
+                        const void *u, double h3, double h_kb, double2 *c,
+                        void *hc, cudaStream_t st) {
+  if (n_atoms <= 0) return;
+  emd_note_launches(1);
+  if (o.prec == EMD_FP64) {
+    EMD_DISPATCH_BO(double, project_t, o, t, n_atoms, u, h3, h_kb, c, hc, st)
+  } else {
+    EMD_DISPATCH_BO(float, project_t, o, t, n_atoms, u, h3, h_kb, c, hc, st)
+  }
+}
+
+void emd_launch_density(const OrbLayout &o, const void *u, double occ,
+                        double *rho, cudaStream_t st) {
+  emd_note_launches(1);
+  if (o.prec == EMD_FP64) {
+    EMD_DISPATCH_BO(double, density_t, o, u, occ, rho, st)
+  } else {
+    EMD_DISPATCH_BO(float, density_t, o, u, occ, rho, st)
+  }
+}
+
+void emd_launch_kinetic_partials(const OrbLayout &o, const void *u,
+                                 double *partials, int *nparts,
+                                 cudaStream_t st) {
+  emd_note_launches(1);
+  const int nb = (o.n3 + 255) / 256;
+  *nparts = nb;
+  if (o.prec == EMD_FP64) {
+    EMD_DISPATCH_BO(double, kinetic_t, o, u, partials, nb, st)
+  } else {
+    EMD_DISPATCH_BO(float, kinetic_t, o, u, partials, nb, st)
+  }
+}
+
+void emd_launch_nl_force(const OrbLayout &o, const TableSet &t, int n_atoms,
+                         const void *u, const double2 *c, double h3,
+                         double coef, double inv_rc2, double *part,
+                         double *F_nl, cudaStream_t st) {
+  if (n_atoms <= 0) return;
+  emd_note_launches(2);
+  if (o.prec == EMD_FP64) {
+    EMD_DISPATCH_BO(double, nlf_t, o, t, n_atoms, u, c, h3, coef, inv_rc2, part, st)
+  } else {
+    EMD_DISPATCH_BO(float, nlf_t, o, t, n_atoms, u, c, h3, coef, inv_rc2, part, st)
+  }
+  const int m = 3 * n_atoms;
+  k_nl_force_sum<<<(m + 127) / 128, 128, 0, st>>>(part, n_atoms, o.n_blk, F_nl);
+}
+
+void emd_launch_pack(const OrbLayout &o, const double2 *canon, void *u,
+                     int n_vec, cudaStream_t st) {
+  emd_note_launches(1);
+  if (o.prec == EMD_FP64) {
+    EMD_DISPATCH_BO(double, pack_t, o, canon, u, n_vec, st)
+  } else {
+    EMD_DISPATCH_BO(float, pack_t, o, canon, u, n_vec, st)
+  }
+}
+
+void emd_launch_unpack(const OrbLayout &o, const void *u, double2 *canon,
+                       int n_vec, cudaStream_t st) {
+  emd_note_launches(1);
+  if (o.prec == EMD_FP64) {
+    EMD_DISPATCH_BO(double, unpack_t, o, u, canon, n_vec, st)
+  } else {
+    EMD_DISPATCH_BO(float, unpack_t, o, u, canon, n_vec, st)
+  }
+}
+
+void emd_launch_abs2_sum(const double2 *c, int n, double *out,
+                         cudaStream_t st) {
+  emd_note_launches(1);
+  k_abs2_sum<<<1, 256, 0, st>>>(c, n, out);
+}

@@ -1,0 +1,368 @@
+// Hartree/ionic electrostatics by a periodic spectral Poisson solve, the
+// Perdew-Zunger LDA, the effective potential of each AETRS half and
+// deterministic grid reductions.
+//
+// Paper: the Hartree term of E_KS (eq. E_KS) and the ionic potential
+// (eq. ionicpotential) are electrostatic potentials; the paper's finite
+// systems use an interpolating-scaling-function Poisson solver (Sec. 5), the
+// periodic boxes here solve nabla^2 v = -4 pi n in Fourier space with the
+// G = 0 component set to zero.  XC: Perdew-Zunger LDA (Sec. 5), adiabatic
+// (instantaneous density, Sec. 4.1).  H(t+dt) of AETRS uses a v_Hxc
+// extrapolated from previous steps (Sec. 5.1, eq. aetrs).
+//
+// The 3-D FFT is three passes of batched 1-D FFTs along the contiguous axis;
+// each pass writes its output transposed ([a][b][k] -> [k][a][b]) so the
+// next axis becomes contiguous and three passes restore the layout.  Each
+// 1-D FFT is a mixed-radix Stockham autosort transform in shared memory
+// (radix 4, 2, 3, 5 and a direct DFT for other small primes) with twiddles
+// precomputed once per grid size.
+#include <cmath>
+#include <vector>
+#include "emd_internal.cuh"
+
+namespace {
+
+constexpr int kMaxStages = 16;
+constexpr int kMaxRadix = 13;
+
+struct FftPlan {
+  int n, ns, lines;
+  int rad[kMaxStages];
+  int tw_off[kMaxStages];   // twiddles exp(-2 pi i jm r / (Ns R)), [jm][r]
+  int root_off[kMaxStages]; // roots exp(-2 pi i m / R), m < R
+};
+
+// exp(-2 pi i num / den) evaluated in extended precision on the host.
+double2 unit_root(long num, long den) {
+  const long double PI_L = 3.141592653589793238462643383279502884L;
+  const long double ang = -2.0L * PI_L * (long double)num / (long double)den;
+  return make_double2((double)cosl(ang), (double)sinl(ang));
+}
+
+bool make_plan(int n, FftPlan &p, std::vector<double2> &tab) {
+  p.n = n;
+  p.ns = 0;
+  int m = n;
+  const int order[] = {4, 2, 3, 5, 7, 11, 13};
+  for (int r : order) {
+    while (m % r == 0) {
+      if (p.ns >= kMaxStages) return false;
+      p.rad[p.ns++] = r;
+      m /= r;
+    }
+  }
+  if (m != 1) return false;
+  tab.clear();
+  int Ns = 1;
+  for (int s = 0; s < p.ns; ++s) {
+    const int R = p.rad[s];
+    p.tw_off[s] = (int)tab.size();
+    for (int jm = 0; jm < Ns; ++jm)
+      for (int r = 0; r < R; ++r) {
+        // angle = -2 pi jm r / (Ns R), reduced exactly as a rational
+        const long num = (long)jm * r % ((long)Ns * R);
+        tab.push_back(unit_root(num, (long)Ns * R));
+      }
+    p.root_off[s] = (int)tab.size();
+    for (int q = 0; q < R; ++q) tab.push_back(unit_root(q, R));
+    Ns *= R;
+  }
+  p.lines = n >= 1280 ? 1 : (1280 / n > 8 ? 8 : 1280 / n);
+  return true;
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ double2 csub(double2 a, double2 b) {
+  return make_double2(a.x - b.x, a.y - b.y);
+}
+// multiply by sign * i
+__device__ __forceinline__ double2 cmuli(double2 a, int sign) {
+  return sign > 0 ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
+}
+
+// One pass: 1-D FFTs of length n along the contiguous axis of [a][b][n],
+// output transposed to [k][a][b].  IN_REAL: input is a real array.
+// OUT_REAL: write the real part times `scale` to a real array.
+template <bool IN_REAL, bool OUT_REAL>
+__global__ void __launch_bounds__(256)
+k_fft_pass(const void *in, void *out, FftPlan pl, const double2 *tab,
+           int sign, double scale) {
+  extern __shared__ double2 sm[];
+  const int n = pl.n, L = pl.lines;
+  const int nlines = n * n;
+  const int l0 = blockIdx.x * L;
+  double2 *b0 = sm, *b1 = sm + L * n;
+  for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
+    const int l = t / n, i = t - l * n, line = l0 + l;
+    double2 v = make_double2(0.0, 0.0);
+    if (line < nlines) {
+      if (IN_REAL)
+        v.x = static_cast<const double *>(in)[(size_t)line * n + i];
+      else
+        v = static_cast<const double2 *>(in)[(size_t)line * n + i];
+    }
+    b0[t] = v;
+  }
+  __syncthreads();
+  int Ns = 1;
+  for (int s = 0; s < pl.ns; ++s) {
+    const int R = pl.rad[s];
+    const int m = n / R;
+    const double2 *tw = tab + pl.tw_off[s];
+    const double2 *root = tab + pl.root_off[s];
+    for (int t = threadIdx.x; t < L * m; t += blockDim.x) {
+      const int l = t / m, j = t - l * m;
+      const double2 *x = b0 + l * n;
+      double2 *y = b1 + l * n;
+      const int jm = j % Ns;
+      const int base = (j / Ns) * Ns * R + jm;
+      double2 v[kMaxRadix];
+      for (int r = 0; r < R; ++r) {
+        double2 a = x[j + r * m];
+        if (r > 0 && jm > 0) {
+          double2 w = tw[jm * R + r];
+          if (sign > 0) w.y = -w.y;
+          a = cmul(a, w);
+        }
+        v[r] = a;
+      }
+      if (R == 4) {
+        const double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        const double2 t2 = cadd(v[1], v[3]), t3 = cmuli(csub(v[1], v[3]), sign);
+        y[base] = cadd(t0, t2);
+        y[base + Ns] = cadd(t1, t3);
+        y[base + 2 * Ns] = csub(t0, t2);
+        y[base + 3 * Ns] = csub(t1, t3);
+      } else if (R == 2) {
+        y[base] = cadd(v[0], v[1]);
+        y[base + Ns] = csub(v[0], v[1]);
+      } else if (R == 3) {
+        const double c3 = 0.86602540378443864676;  // sqrt(3)/2
+        const double2 sm_ = cadd(v[1], v[2]), df = csub(v[1], v[2]);
+        const double2 a = make_double2(v[0].x - 0.5 * sm_.x, v[0].y - 0.5 * sm_.y);
+        double2 b = cmuli(df, sign);
+        b.x *= c3;
+        b.y *= c3;
+        y[base] = cadd(v[0], sm_);
+        y[base + Ns] = cadd(a, b);
+        y[base + 2 * Ns] = csub(a, b);
+      } else {
+        for (int k = 0; k < R; ++k) {
+          double2 acc = v[0];
+          for (int r = 1; r < R; ++r) {
+            double2 w = root[(r * k) % R];
+            if (sign > 0) w.y = -w.y;
+            acc = cadd(acc, cmul(v[r], w));
+          }
+          y[base + k * Ns] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    double2 *tmp = b0;
+    b0 = b1;
+    b1 = tmp;
+    Ns *= R;
+  }
+  for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
+    const int k = t / L, l = t - k * L, line = l0 + l;
+    if (line >= nlines) continue;
+    const int a = line / n, b = line - a * n;
+    const size_t o = ((size_t)k * n + a) * n + b;
+    const double2 v = b0[l * n + k];
+    if (OUT_REAL)
+      static_cast<double *>(out)[o] = v.x * scale;
+    else
+      static_cast<double2 *>(out)[o] = v;
+  }
+}
+
+// v(G) = 4 pi n(G) / |G|^2 (G != 0), v(0) = 0; also folds in 1/N^3 of the
+// unnormalised inverse transform.
+__global__ void k_poisson_kernel(double2 *a, int n, double L) {
+  const size_t n3 = (size_t)n * n * n;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  const int kx = i % n, ky = (i / n) % n, kz = i / ((size_t)n * n);
+  const int mx = 2 * kx < n ? kx : kx - n;
+  const int my = 2 * ky < n ? ky : ky - n;
+  const int mz = 2 * kz < n ? kz : kz - n;
+  const double g = 2.0 * M_PI / L;
+  const double gx = g * mx, gy = g * my, gz = g * mz;
+  const double G2 = gz * gz + gy * gy + gx * gx;
+  double2 v = a[i];
+  if (mx == 0 && my == 0 && mz == 0) {
+    v = make_double2(0.0, 0.0);
+  } else {
+    const double f = 4.0 * M_PI / G2 / (double)n3;
+    v.x *= f;
+    v.y *= f;
+  }
+  a[i] = v;
+}
+
+// Perdew-Zunger LDA (unpolarised): eps_xc, v_xc; vhxc = v_h + v_xc.
+__global__ void k_lda(int n3, const double *rho, const double *vh,
+                      double *eps, double *vxc, double *vhxc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  const double r = rho[i];
+  double e = 0.0, v = 0.0;
+  if (r >= 1e-30) {
+    const double ex = -0.75 * cbrt(3.0 * r / M_PI);
+    const double vx = (4.0 / 3.0) * ex;
+    const double rs = cbrt(3.0 / (4.0 * M_PI * r));
+    double ec, vc;
+    if (rs >= 1.0) {
+      const double gam = -0.1423, b1 = 1.0529, b2 = 0.3334;
+      const double s = sqrt(rs);
+      const double q = 1.0 + b1 * s + b2 * rs;
+      ec = gam / q;
+      vc = gam * (1.0 + (7.0 / 6.0) * b1 * s + (4.0 / 3.0) * b2 * rs) / (q * q);
+    } else {
+      const double A = 0.0311, B = -0.048, C = 0.0020, D = -0.0116;
+      const double lx = log(rs);
+      ec = A * lx + B + C * rs * lx + D * rs;
+      vc = A * lx + (B - A / 3.0) + (2.0 / 3.0) * C * rs * lx +
+           ((2.0 * D - C) / 3.0) * rs;
+    }
+    e = ex + ec;
+    v = vx + vc;
+  }
+  eps[i] = e;
+  vxc[i] = v;
+  vhxc[i] = vh[i] + v;
+}
+
+// v_eff = v_loc + extrapolated v_Hxc + field * (z - L/2).
+__global__ void k_veff(int n, double h, double L, const double *vloc,
+                       const double *h0, const double *h1, const double *h2,
+                       int hist_len, double field, double *ve, float *vef) {
+  const int n3 = n * n * n;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  double x;
+  if (hist_len <= 1)
+    x = h0[i];
+  else if (hist_len == 2)
+    x = 2.0 * h0[i] - h1[i];
+  else
+    x = 3.0 * h0[i] - 3.0 * h1[i] + h2[i];
+  double v = vloc[i] + x;
+  if (field != 0.0) {
+    const int z = i / (n * n);
+    v += field * (z * h - 0.5 * L);
+  }
+  ve[i] = v;
+  if (vef) vef[i] = (float)v;
+}
+
+// partial[b] = sum over block b of (a - c)(b + d) (c, d optional).
+__global__ void __launch_bounds__(256)
+k_dot4(int n, const double *a, const double *b, const double *c,
+       const double *d, double *part) {
+  __shared__ double red[8];
+  double acc[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += gridDim.x * blockDim.x) {
+    const double x = c ? a[i] - c[i] : a[i];
+    const double y = b ? (d ? b[i] + d[i] : b[i]) : 1.0;
+    acc[0] += x * y;
+  }
+  emd_block_sum<1>(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
+}
+
+__global__ void __launch_bounds__(256)
+k_sum(const double *part, int n, double *out) {
+  __shared__ double red[8];
+  double acc[1] = {0.0};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc[0] += part[i];
+  emd_block_sum<1>(acc, red);
+  if (threadIdx.x == 0) *out = acc[0];
+}
+
+struct PlanCache {
+  int n = -1;
+  FftPlan plan;
+  double2 *tab = nullptr;
+};
+PlanCache g_cache[4];
+
+const PlanCache *get_plan(int n) {
+  for (auto &c : g_cache)
+    if (c.n == n) return &c;
+  for (auto &c : g_cache) {
+    if (c.n == -1) {
+      std::vector<double2> tab;
+      if (!make_plan(n, c.plan, tab)) return nullptr;
+      if (cudaMalloc(&c.tab, tab.size() * sizeof(double2)) != cudaSuccess)
+        return nullptr;
+      cudaMemcpy(c.tab, tab.data(), tab.size() * sizeof(double2),
+                 cudaMemcpyHostToDevice);
+      c.n = n;
+      return &c;
+    }
+  }
+  return nullptr;
+}
+
+}  // namespace
+
+void emd_fft_plan_check(int n, int *ok) {
+  FftPlan p;
+  std::vector<double2> t;
+  *ok = make_plan(n, p, t);
+}
+
+int emd_fft_prepare(int n) { return get_plan(n) != nullptr ? 0 : 1; }
+
+void emd_launch_poisson(const GridInfo &g, const double *charge, double *v,
+                        double2 *wa, double2 *wb, cudaStream_t st) {
+  emd_note_launches(7);
+  const PlanCache *pc = get_plan(g.n);
+  const FftPlan &p = pc->plan;
+  const int blocks = (g.n * g.n + p.lines - 1) / p.lines;
+  const size_t smem = 2 * (size_t)p.lines * g.n * sizeof(double2);
+  k_fft_pass<true, false><<<blocks, 256, smem, st>>>(charge, wa, p, pc->tab, -1, 1.0);
+  k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wa, wb, p, pc->tab, -1, 1.0);
+  k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wb, wa, p, pc->tab, -1, 1.0);
+  k_poisson_kernel<<<(g.n3 + 255) / 256, 256, 0, st>>>(wa, g.n, g.L);
+  k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wa, wb, p, pc->tab, +1, 1.0);
+  k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wb, wa, p, pc->tab, +1, 1.0);
+  k_fft_pass<false, true><<<blocks, 256, smem, st>>>(wa, v, p, pc->tab, +1, 1.0);
+}
+
+void emd_launch_lda(int n3, const double *rho, const double *v_h,
+                    double *eps_xc, double *v_xc, double *vhxc,
+                    cudaStream_t st) {
+  emd_note_launches(1);
+  k_lda<<<(n3 + 255) / 256, 256, 0, st>>>(n3, rho, v_h, eps_xc, v_xc, vhxc);
+}
+
+void emd_launch_veff(const GridInfo &g, const double *v_loc,
+                     const double *const *hist, int hist_len, double field,
+                     double *v_eff, float *v_eff_f, cudaStream_t st) {
+  emd_note_launches(1);
+  k_veff<<<(g.n3 + 255) / 256, 256, 0, st>>>(
+      g.n, g.h, g.L, v_loc, hist[0], hist_len > 1 ? hist[1] : hist[0],
+      hist_len > 2 ? hist[2] : hist[0], hist_len, field, v_eff, v_eff_f);
+}
+
+void emd_launch_dot_partials(int n3, const double *a, const double *b,
+                             const double *c, const double *d,
+                             double *partials, int nblocks, cudaStream_t st) {
+  emd_note_launches(1);
+  k_dot4<<<nblocks, 256, 0, st>>>(n3, a, b, c, d, partials);
+}
+
+void emd_launch_sum(const double *partials, int n, double *out,
+                    cudaStream_t st) {
+  emd_note_launches(1);
+  k_sum<<<1, 256, 0, st>>>(partials, n, out);
+}

@@ -1,0 +1,378 @@
+// Atom-dependent grid data for one set of ion positions: folded positions,
+// per-tile atom candidates, the point-major projector table with the Gaussian
+// ion charge, the atom-major projector table, and the ionic force terms.
+//
+// Paper: ionic potential as a sum of per-atom terms (Sec. 5.2,
+// eq. ionicpotential); Hellmann-Feynman forces (eq. new_EoM_b) whose local
+// part (eq. ionicforces) is taken here as the exact derivative of the
+// discrete electrostatic energy with respect to R_J (the gradient acts on the
+// analytic Gaussian charge, not on the grid density); velocity Verlet for the
+// ions (Sec. 5.1).
+#include "emd_internal.cuh"
+
+namespace {
+
+__global__ void k_wrap(const double *R, double *Rw, int n, double L) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) Rw[i] = emd_wrap_pos(R[i], L);
+}
+
+// Conservative (atom, image) candidates per tile of EMD_TILE^3 points: every
+// pair whose support sphere can reach a point of the tile.  The exact
+// per-point decision is taken later in FP64.
+__global__ void k_tile_candidates(int n, double h, double L, const double *Rw,
+                                  int n_atoms, float r_max, int *tile_cnt,
+                                  int *tile_ent, int *err) {
+  const int nt = (n + EMD_TILE - 1) / EMD_TILE;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt * nt * nt) return;
+  const int tx = t % nt, ty = (t / nt) % nt, tz = t / (nt * nt);
+  const float lo[3] = {(float)(tx * EMD_TILE * h), (float)(ty * EMD_TILE * h),
+                       (float)(tz * EMD_TILE * h)};
+  const float hi[3] = {(float)(min(tx * EMD_TILE + EMD_TILE - 1, n - 1) * h),
+                       (float)(min(ty * EMD_TILE + EMD_TILE - 1, n - 1) * h),
+                       (float)(min(tz * EMD_TILE + EMD_TILE - 1, n - 1) * h)};
+  const float rr = (r_max + 0.05f) * (r_max + 0.05f);
+  int cnt = 0;
+  for (int J = 0; J < n_atoms; ++J) {
+    for (int img = 0; img < 27; ++img) {
+      const int ni[3] = {img % 3 - 1, (img / 3) % 3 - 1, img / 9 - 1};
+      float d2 = 0.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        float c = (float)Rw[3 * J + a] + (float)(ni[a] * L);
+        float d = fmaxf(fmaxf(lo[a] - c, c - hi[a]), 0.f);
+        d2 += d * d;
+      }
+      if (d2 < rr) {
+        if (cnt < EMD_TILE_CAND_MAX) {
+          tile_ent[t * EMD_TILE_CAND_MAX + cnt] = J * 27 + img;
+          ++cnt;
+        } else {
+          atomicOr(err, EMD_ERRBIT_TILE);
+        }
+      }
+    }
+  }
+  tile_cnt[t] = cnt;
+}
+
+// Point-major table: for each grid point the atoms whose projector reaches it
+// (p summed over that atom's images), in increasing atom order; and the total
+// Gaussian ion charge at the point.  One block = one tile.
+__global__ void __launch_bounds__(512)
+k_point_table(int n, int n3, double h, double L, const double *Rw,
+              SpeciesDev sp, const int *tile_cnt, const int *tile_ent,
+              int *pt_cnt, int *pt_J, double *pt_p, double *g_ion, int *err) {
+  __shared__ int cand[EMD_TILE_CAND_MAX];
+  const int nt = (n + EMD_TILE - 1) / EMD_TILE;
+  const int t = blockIdx.x;
+  const int tx = t % nt, ty = (t / nt) % nt, tz = t / (nt * nt);
+  const int nc = tile_cnt[t];
+  for (int i = threadIdx.x; i < nc; i += blockDim.x)
+    cand[i] = tile_ent[t * EMD_TILE_CAND_MAX + i];
+  __syncthreads();
+  const int x = tx * EMD_TILE + (threadIdx.x & 7);
+  const int y = ty * EMD_TILE + ((threadIdx.x >> 3) & 7);
+  const int z = tz * EMD_TILE + (threadIdx.x >> 6);
+  if (x >= n || y >= n || z >= n) return;
+  const int p = (z * n + y) * n + x;
+  const double rp2 = __dmul_rn(sp.r_proj, sp.r_proj);
+  const double rl2 = __dmul_rn(sp.r_loc, sp.r_loc);
+  int cnt = 0, curJ = -1;
+  double psum = 0.0, gsum = 0.0;
+  bool hit = false;
+  for (int e = 0; e < nc; ++e) {
+    const int code = cand[e];
+    const int J = code / 27, img = code % 27;
+    if (J != curJ) {
+      if (hit) {
+        if (cnt < EMD_PT_KMAX) {
+          pt_J[cnt * n3 + p] = curJ;
+          pt_p[cnt * n3 + p] = psum;
+          ++cnt;
+        } else {
+          atomicOr(err, EMD_ERRBIT_PT);
+        }
+      }
+      curJ = J;
+      psum = 0.0;
+      hit = false;
+    }
+    const double dx = emd_disp(x, h, Rw[3 * J + 0], img % 3 - 1, L);
+    const double dy = emd_disp(y, h, Rw[3 * J + 1], (img / 3) % 3 - 1, L);
+    const double dz = emd_disp(z, h, Rw[3 * J + 2], img / 9 - 1, L);
+    const double d2 = emd_norm2(dx, dy, dz);
+    if (d2 < rp2) {
+      psum += sp.c_p * exp(-d2 * sp.inv_2rc2);
+      hit = true;
+    }
+    if (d2 < rl2) gsum += sp.c_g * exp(-d2 * sp.inv_a2);
+  }
+  if (hit) {
+    if (cnt < EMD_PT_KMAX) {
+      pt_J[cnt * n3 + p] = curJ;
+      pt_p[cnt * n3 + p] = psum;
+      ++cnt;
+    } else {
+      atomicOr(err, EMD_ERRBIT_PT);
+    }
+  }
+  pt_cnt[p] = cnt;
+  g_ion[p] = gsum;
+}
+
+// Index box of the grid points an image sphere can reach along one axis.
+__device__ __forceinline__ void axis_range(double c, int nimg, double L,
+                                           double h, double r, int n, int &lo,
+                                           int &hi) {
+  const double cc = c + nimg * L;
+  lo = max(0, (int)floor((cc - r) / h) - 1);
+  hi = min(n - 1, (int)ceil((cc + r) / h) + 1);
+}
+
+// Atom-major projector table: every (point, image) pair within r_proj of atom
+// J, in image order then box order (deterministic), with p and d = r - R_img.
+__global__ void __launch_bounds__(256)
+k_atom_table(int n, double h, double L, const double *Rw, SpeciesDev sp,
+             int cap, int *at_cnt, int *at_pt, double *at_p, double *at_d,
+             int *err) {
+  __shared__ int warp_tot[8];
+  __shared__ int s_base;
+  const int J = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double c[3] = {Rw[3 * J], Rw[3 * J + 1], Rw[3 * J + 2]};
+  const double rp2 = __dmul_rn(sp.r_proj, sp.r_proj);
+  if (threadIdx.x == 0) s_base = 0;
+  __syncthreads();
+  for (int img = 0; img < 27; ++img) {
+    const int ni[3] = {img % 3 - 1, (img / 3) % 3 - 1, img / 9 - 1};
+    int lo[3], hi[3];
+    bool empty = false;
+    for (int a = 0; a < 3; ++a) {
+      axis_range(c[a], ni[a], L, h, sp.r_proj, n, lo[a], hi[a]);
+      if (lo[a] > hi[a]) empty = true;
+    }
+    if (empty) continue;
+    const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1,
+              ez = hi[2] - lo[2] + 1;
+    const int nbox = ex * ey * ez;
+    for (int b0 = 0; b0 < nbox; b0 += blockDim.x) {
+      const int k = b0 + threadIdx.x;
+      bool flag = false;
+      double dx = 0, dy = 0, dz = 0, d2 = 0;
+      int pidx = 0;
+      if (k < nbox) {
+        const int ix = lo[0] + k % ex, iy = lo[1] + (k / ex) % ey,
+                  iz = lo[2] + k / (ex * ey);
+        dx = emd_disp(ix, h, c[0], ni[0], L);
+        dy = emd_disp(iy, h, c[1], ni[1], L);
+        dz = emd_disp(iz, h, c[2], ni[2], L);
+        d2 = emd_norm2(dx, dy, dz);
+        flag = d2 < rp2;
+        pidx = (iz * n + iy) * n + ix;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, flag);
+      const int pre = __popc(m & ((1u << lane) - 1u));
+      if (lane == 0) warp_tot[warp] = __popc(m);
+      __syncthreads();
+      int off = s_base, tot = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        if (w < warp) off += warp_tot[w];
+        tot += warp_tot[w];
+      }
+      if (flag) {
+        const int e = off + pre;
+        if (e < cap) {
+          at_pt[(size_t)J * cap + e] = pidx;
+          at_p[(size_t)J * cap + e] = sp.c_p * exp(-d2 * sp.inv_2rc2);
+          double *dd = at_d + 3 * ((size_t)J * cap + e);
+          dd[0] = dx;
+          dd[1] = dy;
+          dd[2] = dz;
+        } else {
+          atomicOr(err, EMD_ERRBIT_AT);
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_base += tot;
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) at_cnt[J] = min(s_base, cap);
+}
+
+// F_J^loc = h^3 sum_r v_es(r) g_J(d) 2 d / a^2 over the Gaussian support
+// (-dE_es/dR_J of 1/2 h^3 sum n_tot v_es, n_tot = rho - sum g).
+__global__ void __launch_bounds__(256)
+k_local_force(int n, double h, double L, const double *Rw, SpeciesDev sp,
+              const double *va, const double *vb, double *F) {
+  __shared__ double red[8 * 3];
+  const int J = blockIdx.x;
+  const double c[3] = {Rw[3 * J], Rw[3 * J + 1], Rw[3 * J + 2]};
+  const double rl2 = __dmul_rn(sp.r_loc, sp.r_loc);
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int img = 0; img < 27; ++img) {
+    const int ni[3] = {img % 3 - 1, (img / 3) % 3 - 1, img / 9 - 1};
+    int lo[3], hi[3];
+    bool empty = false;
+    for (int a = 0; a < 3; ++a) {
+      axis_range(c[a], ni[a], L, h, sp.r_loc, n, lo[a], hi[a]);
+      if (lo[a] > hi[a]) empty = true;
+    }
+    if (empty) continue;
+    const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1,
+              ez = hi[2] - lo[2] + 1;
+    const int nbox = ex * ey * ez;
+    for (int k = threadIdx.x; k < nbox; k += blockDim.x) {
+      const int ix = lo[0] + k % ex, iy = lo[1] + (k / ex) % ey,
+                iz = lo[2] + k / (ex * ey);
+      const double dx = emd_disp(ix, h, c[0], ni[0], L);
+      const double dy = emd_disp(iy, h, c[1], ni[1], L);
+      const double dz = emd_disp(iz, h, c[2], ni[2], L);
+      const double d2 = emd_norm2(dx, dy, dz);
+      if (d2 < rl2) {
+        const int p = (iz * n + iy) * n + ix;
+        const double g = sp.c_g * exp(-d2 * sp.inv_a2);
+        const double w = (va[p] + vb[p]) * g * (2.0 * sp.inv_a2);
+        acc[0] += w * dx;
+        acc[1] += w * dy;
+        acc[2] += w * dz;
+      }
+    }
+  }
+  emd_block_sum<3>(acc, red);
+  if (threadIdx.x == 0) {
+    const double h3 = h * h * h;
+    F[3 * J + 0] = h3 * acc[0];
+    F[3 * J + 1] = h3 * acc[1];
+    F[3 * J + 2] = h3 * acc[2];
+  }
+}
+
+// Short-range ion-ion term E_sr = 1/2 sum' Z^2 erfc(d/s)/d (s = sqrt2 a, d <
+// 12 bohr, all images) and its force.  One thread per atom.
+__global__ void k_short_range(SpeciesDev sp, int n_atoms, const double *Rw,
+                              double L, int nmax, double *F, double *e_part) {
+  const int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= n_atoms) return;
+  const double s = sqrt(2.0) * sp.a_loc;
+  const double zz = sp.z * sp.z;
+  const double rcut = 12.0;
+  const double k2 = 2.0 / (s * sqrt(M_PI));
+  double e = 0.0, f[3] = {0.0, 0.0, 0.0};
+  for (int K = 0; K < n_atoms; ++K) {
+    for (int nz = -nmax; nz <= nmax; ++nz)
+      for (int ny = -nmax; ny <= nmax; ++ny)
+        for (int nx = -nmax; nx <= nmax; ++nx) {
+          if (K == J && nx == 0 && ny == 0 && nz == 0) continue;
+          const double dv0 = Rw[3 * J] - Rw[3 * K] - nx * L;
+          const double dv1 = Rw[3 * J + 1] - Rw[3 * K + 1] - ny * L;
+          const double dv2 = Rw[3 * J + 2] - Rw[3 * K + 2] - nz * L;
+          const double d = sqrt(dv0 * dv0 + dv1 * dv1 + dv2 * dv2);
+          if (d >= rcut || d <= 0.0) continue;
+          const double ef = erfc(d / s) / d;
+          e += ef;
+          const double fm = zz * (ef / d + k2 * exp(-d * d / (s * s)) / d) / d;
+          f[0] += fm * dv0;
+          f[1] += fm * dv1;
+          f[2] += fm * dv2;
+        }
+  }
+  e_part[J] = 0.5 * zz * e;
+  F[3 * J] = f[0];
+  F[3 * J + 1] = f[1];
+  F[3 * J + 2] = f[2];
+}
+
+// R(t+dt) = R + V dt + F dt^2 / (2M), in the reference's rounding order.
+__global__ void k_vv_positions(int n, const double *R, const double *V,
+                               const double *F, double dt, double c2,
+                               double *Rn) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n)
+    Rn[i] = __dadd_rn(__dadd_rn(R[i], __dmul_rn(V[i], dt)), __dmul_rn(F[i], c2));
+}
+
+// F_new = (F_loc + F_nl) + F_sr (+ Z e on z); V += (F_old + F_new) dt/(2M).
+__global__ void k_vv_velocities(int n_atoms, const double *Fl,
+                                const double *Fn, const double *Fs,
+                                double fz, double *F, double *V, double c1,
+                                int update_v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * n_atoms) return;
+  double f = __dadd_rn(__dadd_rn(Fl[i], Fn[i]), Fs[i]);
+  if (i % 3 == 2) f = __dadd_rn(f, fz);
+  if (update_v) V[i] = __dadd_rn(V[i], __dmul_rn(__dadd_rn(F[i], f), c1));
+  F[i] = f;
+}
+
+}  // namespace
+
+void emd_launch_wrap(const double *R, double *Rw, int n_atoms, double L,
+                     cudaStream_t st) {
+  if (n_atoms <= 0) return;
+  emd_note_launches(1);
+  int n = 3 * n_atoms;
+  k_wrap<<<(n + 127) / 128, 128, 0, st>>>(R, Rw, n, L);
+}
+
+void emd_launch_tables(const GridInfo &g, const SpeciesDev &sp, int n_atoms,
+                       TableSet &t, int *err, cudaStream_t st) {
+  emd_note_launches(2 + (n_atoms > 0));
+  const int nt = (g.n + EMD_TILE - 1) / EMD_TILE;
+  const int ntiles = nt * nt * nt;
+  const float rmax = (float)fmax(sp.r_proj, sp.r_loc);
+  k_tile_candidates<<<(ntiles + 127) / 128, 128, 0, st>>>(
+      g.n, g.h, g.L, t.Rw, n_atoms, rmax, t.tile_cnt, t.tile_ent, err);
+  k_point_table<<<ntiles, 512, 0, st>>>(g.n, g.n3, g.h, g.L, t.Rw, sp,
+                                        t.tile_cnt, t.tile_ent, t.pt_cnt,
+                                        t.pt_J, t.pt_p, t.g_ion, err);
+  if (n_atoms > 0)
+    k_atom_table<<<n_atoms, 256, 0, st>>>(g.n, g.h, g.L, t.Rw, sp, t.cap,
+                                          t.at_cnt, t.at_pt, t.at_p, t.at_d,
+                                          err);
+}
+
+void emd_launch_local_force(const GridInfo &g, const SpeciesDev &sp,
+                            int n_atoms, const double *Rw, const double *v_es_a,
+                            const double *v_es_b, double *F, cudaStream_t st) {
+  if (n_atoms <= 0) return;
+  emd_note_launches(1);
+  k_local_force<<<n_atoms, 256, 0, st>>>(g.n, g.h, g.L, Rw, sp, v_es_a,
+                                         v_es_b, F);
+}
+
+void emd_launch_short_range(const SpeciesDev &sp, int n_atoms, const double *Rw,
+                            double L, double *F, double *e_part,
+                            cudaStream_t st) {
+  if (n_atoms <= 0) return;
+  emd_note_launches(1);
+  const int nmax = (int)ceil(12.0 / L) + 1;
+  k_short_range<<<(n_atoms + 63) / 64, 64, 0, st>>>(sp, n_atoms, Rw, L, nmax,
+                                                     F, e_part);
+}
+
+void emd_launch_vv_positions(int n_atoms, const double *R, const double *V,
+                             const double *F, double dt, double mass,
+                             double *R_new, cudaStream_t st) {
+  if (n_atoms <= 0) return;
+  emd_note_launches(1);
+  const double c2 = (dt * dt) / (2.0 * mass);
+  int n = 3 * n_atoms;
+  k_vv_positions<<<(n + 127) / 128, 128, 0, st>>>(n, R, V, F, dt, c2, R_new);
+}
+
+void emd_launch_vv_velocities(int n_atoms, const double *F_loc,
+                              const double *F_nl, const double *F_sr,
+                              double field_z, double z, double *F, double *V,
+                              double dt, double mass, int update_v,
+                              cudaStream_t st) {
+  if (n_atoms <= 0) return;
+  emd_note_launches(1);
+  const double c1 = dt / (2.0 * mass);
+  const double fz = z * field_z;
+  int n = 3 * n_atoms;
+  k_vv_velocities<<<(n + 127) / 128, 128, 0, st>>>(n_atoms, F_loc, F_nl, F_sr,
+                                                    fz, F, V, c1, update_v);
+}

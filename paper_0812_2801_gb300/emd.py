@@ -1,0 +1,241 @@
+"""Thin ctypes binding of libemd (see include/emd.h for the contract).
+
+Argument marshalling only: every step of the propagation runs in the CUDA
+library.  Loading fails loudly if ``libemd.so`` has not been built; there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libemd.so")
+
+EMD_OK, EMD_EINVAL, EMD_ENOMEM, EMD_ECUDA, EMD_EUNSTABLE, EMD_ESTATE, EMD_ETABLE = range(7)
+EMD_FP64, EMD_FP32_ORBITALS = 0, 1
+EMD_OPT_FROZEN_IONS, EMD_OPT_PROFILE, EMD_OPT_CHECK_STABLE = 1, 2, 3
+EMD_KERNEL_HORNER, EMD_KERNEL_ALL = 0, 1
+
+
+class EmdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libemd error {code}: {msg}")
+        self.code = code
+
+
+class emd_species(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("z", "mass", "a_loc", "r_loc", "r_c", "h_kb", "r_proj")]
+
+
+class emd_config(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("h", ctypes.c_double),
+                ("fd_order", ctypes.c_int), ("n_orb", ctypes.c_int),
+                ("occ", ctypes.c_double), ("precision", ctypes.c_int),
+                ("n_atoms", ctypes.c_int), ("species", emd_species),
+                ("cuda_stream", ctypes.c_void_p),
+                ("block_orbitals", ctypes.c_int)]
+
+
+class emd_energy(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("kin_e", "nl", "es", "xc", "sr", "kin_ion", "ks", "total", "n_elec")]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+_DPTR = ctypes.POINTER(ctypes.c_double)
+
+
+def load() -> ctypes.CDLL:
+    """Load libemd.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.emd_init_system.argtypes = [ctypes.POINTER(emd_config), ctypes.POINTER(vp)]
+    lib.emd_set_ions.argtypes = [vp, ip, _DPTR, _DPTR]
+    lib.emd_set_orbitals.argtypes = [vp, _DPTR]
+    lib.emd_propagate.argtypes = [vp, ip, dp, dp, _DPTR]
+    lib.emd_get_forces.argtypes = [vp, _DPTR]
+    lib.emd_get_energy.argtypes = [vp, ctypes.POINTER(emd_energy)]
+    lib.emd_get_state.argtypes = [vp, _DPTR, _DPTR, _DPTR, _DPTR]
+    lib.emd_get_potentials.argtypes = [vp, _DPTR, _DPTR, _DPTR, _DPTR]
+    lib.emd_get_projections.argtypes = [vp, _DPTR]
+    lib.emd_apply_hamiltonian.argtypes = [vp, ip, _DPTR, _DPTR]
+    lib.emd_set_option.argtypes = [vp, ip, dp]
+    lib.emd_kernel_stats.argtypes = [vp, ip, _DPTR, ctypes.POINTER(ctypes.c_longlong)]
+    lib.emd_destroy.argtypes = [vp]
+    lib.emd_destroy.restype = None
+    lib.emd_last_error.restype = ctypes.c_char_p
+    lib.emd_version.restype = ctypes.c_char_p
+    for name in ("emd_init_system", "emd_set_ions", "emd_set_orbitals",
+                 "emd_propagate", "emd_get_forces", "emd_get_energy",
+                 "emd_get_state", "emd_get_potentials", "emd_get_projections",
+                 "emd_apply_hamiltonian", "emd_set_option", "emd_kernel_stats"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code: int) -> None:
+    if code != EMD_OK:
+        raise EmdError(code, load().emd_last_error().decode())
+
+
+def _dptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_DPTR)
+
+
+def _c128(a: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a
+
+
+# ---- one-to-one wrappers of the C entry points -----------------------------
+
+def emd_init_system(cfg: emd_config) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().emd_init_system(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def emd_set_ions(h, R: np.ndarray, V: np.ndarray) -> None:
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    _check(load().emd_set_ions(h, R.shape[0], _dptr(R), _dptr(V)))
+
+
+def emd_set_orbitals(h, psi: np.ndarray) -> None:
+    psi = _c128(psi)
+    _check(load().emd_set_orbitals(h, psi.view(np.float64).ctypes.data_as(_DPTR)))
+
+
+def emd_propagate(h, n_steps: int, dt: float, mu: float,
+                  field: Optional[np.ndarray] = None) -> None:
+    f = None if field is None else np.ascontiguousarray(field, dtype=np.float64)
+    _check(load().emd_propagate(h, int(n_steps), float(dt), float(mu), _dptr(f)))
+
+
+def emd_get_forces(h, n_atoms: int) -> np.ndarray:
+    F = np.zeros((n_atoms, 3))
+    _check(load().emd_get_forces(h, _dptr(F)))
+    return F
+
+
+def emd_get_energy(h) -> dict:
+    e = emd_energy()
+    _check(load().emd_get_energy(h, ctypes.byref(e)))
+    return e.as_dict()
+
+
+def emd_get_state(h, n_atoms: int, n_orb: int, n: int, want_psi=True, want_rho=True):
+    R = np.zeros((n_atoms, 3))
+    V = np.zeros((n_atoms, 3))
+    psi = np.zeros((n_orb, n, n, n), dtype=np.complex128) if want_psi else None
+    rho = np.zeros((n, n, n)) if want_rho else None
+    _check(load().emd_get_state(
+        h, _dptr(R), _dptr(V),
+        None if psi is None else psi.view(np.float64).ctypes.data_as(_DPTR),
+        _dptr(rho)))
+    return R, V, psi, rho
+
+
+def emd_get_potentials(h, n: int):
+    out = [np.zeros((n, n, n)) for _ in range(4)]
+    _check(load().emd_get_potentials(h, *[_dptr(a) for a in out]))
+    return dict(zip(("v_loc", "v_h", "v_xc", "g_ion"), out))
+
+
+def emd_get_projections(h, n_atoms: int, n_orb: int) -> np.ndarray:
+    c = np.zeros((n_atoms, n_orb), dtype=np.complex128)
+    _check(load().emd_get_projections(h, c.view(np.float64).ctypes.data_as(_DPTR)))
+    return c
+
+
+def emd_apply_hamiltonian(h, psi: np.ndarray) -> np.ndarray:
+    psi = _c128(psi)
+    out = np.zeros_like(psi)
+    _check(load().emd_apply_hamiltonian(
+        h, psi.shape[0], psi.view(np.float64).ctypes.data_as(_DPTR),
+        out.view(np.float64).ctypes.data_as(_DPTR)))
+    return out
+
+
+def emd_set_option(h, option: int, value: float) -> None:
+    _check(load().emd_set_option(h, int(option), float(value)))
+
+
+def emd_kernel_stats(h, kernel: int = EMD_KERNEL_HORNER):
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    _check(load().emd_kernel_stats(h, int(kernel), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def emd_destroy(h) -> None:
+    if h:
+        load().emd_destroy(h)
+
+
+# ---- convenience -----------------------------------------------------------
+
+def config_for(sysin, precision: int = EMD_FP64, stream: int = 0,
+               block_orbitals: int = 0) -> emd_config:
+    sp = sysin.species
+    return emd_config(n=sysin.n, h=sysin.h, fd_order=sysin.fd_order,
+                      n_orb=sysin.n_orb, occ=sysin.occ, precision=precision,
+                      n_atoms=sysin.n_atoms,
+                      species=emd_species(sp.z, sp.mass, sp.a_loc, sp.r_loc,
+                                          sp.r_c, sp.h_kb, sp.r_proj),
+                      cuda_stream=stream or None,
+                      block_orbitals=block_orbitals)
+
+
+class System:
+    """Owns one libemd handle for a ``SystemInput``."""
+
+    def __init__(self, sysin, precision: int = EMD_FP64, stream: int = 0,
+                 block_orbitals: int = 0):
+        self.sysin = sysin
+        self.handle = emd_init_system(config_for(sysin, precision, stream, block_orbitals))
+        emd_set_ions(self.handle, sysin.R, sysin.V)
+        emd_set_orbitals(self.handle, sysin.psi)
+
+    def propagate(self, n_steps, dt=None, mu=None, field=None):
+        emd_propagate(self.handle, n_steps, self.sysin.dt if dt is None else dt,
+                      self.sysin.mu if mu is None else mu, field)
+
+    def forces(self):
+        return emd_get_forces(self.handle, self.sysin.n_atoms)
+
+    def energy(self):
+        return emd_get_energy(self.handle)
+
+    def state(self, want_psi=True, want_rho=True):
+        s = self.sysin
+        return emd_get_state(self.handle, s.n_atoms, s.n_orb, s.n, want_psi, want_rho)
+
+    def close(self):
+        emd_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None):
+                self.close()
+        except Exception:
+            pass

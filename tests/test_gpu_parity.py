@@ -1,0 +1,182 @@
+"""GPU vs oracle parity through the C ABI (FP64 path).
+
+Tolerances: max |delta psi| <= 1e-10, forces and energy components <= 1e-9
+relative (FP64), as the method's FP64 parity requirement states; the single
+operators (H psi, potentials, projections) are compared at 1e-12 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import emd_oracle as O
+from paper_0812_2801_gb300 import emd, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def small():
+    return inputs.small_system(n=20, h=0.3, fd_order=6, n_atoms=3, seed=5, n_orb=5)
+
+
+def test_hamiltonian_apply_matches_oracle(small):
+    s = small
+    g = emd.System(s)
+    st = O.init_state(s)
+    rng = np.random.default_rng(2)
+    u = rng.normal(size=(3, s.n, s.n, s.n)) + 1j * rng.normal(size=(3, s.n, s.n, s.n))
+    H = O.Hamiltonian(st.v_loc + st.v_h + st.v_xc, st.tables, s.species, s.h, s.fd_order)
+    assert rel(emd.emd_apply_hamiltonian(g.handle, u), H.apply(u)) < 1e-12
+    g.close()
+
+
+def test_initial_potentials_projections_forces_energy(small):
+    s = small
+    g = emd.System(s)
+    st = O.init_state(s)
+    pot = emd.emd_get_potentials(g.handle, s.n)
+    assert rel(pot["g_ion"], st.g_ion) < 1e-12
+    assert rel(pot["v_loc"], st.v_loc) < 1e-12
+    assert rel(pot["v_h"], st.v_h) < 1e-12
+    assert rel(pot["v_xc"], st.v_xc) < 1e-12
+    c = emd.emd_get_projections(g.handle, s.n_atoms, s.n_orb)
+    assert rel(c, O.projections(st.psi, st.tables, s.species, s.h)) < 1e-12
+    assert rel(g.forces(), st.F) < 1e-10
+    eg = g.energy()
+    eo = O.energies(st)
+    for k in ("kin_e", "nl", "es", "xc", "sr", "kin_ion", "total"):
+        assert abs(eg[k] - eo[k]) <= 1e-10 * max(abs(eo[k]), 1e-12), k
+    assert abs(eg["n_elec"] - s.occ * s.n_orb) < 1e-10
+    g.close()
+
+
+@pytest.mark.parametrize("bo", [1, 2, 4])
+def test_md_steps_match_oracle_ragged_blocks(small, bo):
+    """5 orbitals in blocks of 1, 2, 4 (ragged last block), 20^3 grid (not a
+    multiple of the 32x4 thread tile), 4 MD steps."""
+    s = small
+    g = emd.System(s, block_orbitals=bo)
+    g.propagate(4, dt=0.04, mu=1.0)
+    R, V, psi, rho = g.state()
+    F = g.forces()
+    eg = g.energy()
+    g.close()
+    st = O.run(s, 4, dt=0.04, mu=1.0)
+    assert np.max(np.abs(psi - st.psi)) <= 1e-10
+    assert rel(rho, st.rho) < 1e-10
+    assert rel(R, st.R) < 1e-12
+    assert rel(V, st.V) < 1e-9
+    assert rel(F, st.F) < 1e-9
+    eo = O.energies(st)
+    for k in ("kin_e", "nl", "es", "xc", "total"):
+        assert abs(eg[k] - eo[k]) <= 1e-9 * abs(eo[k]), k
+
+
+def test_tiny_workload_50_steps_parity():
+    """8 atoms, 16 orbitals, 32^3, order 4, mu = 1, dt = 0.05, 50 steps."""
+    s = inputs.tiny_fp64()
+    g = emd.System(s)
+    g.propagate(s.n_steps)
+    R, V, psi, rho = g.state()
+    F = g.forces()
+    eg = g.energy()
+    g.close()
+    st = O.run(s, s.n_steps)
+    assert np.max(np.abs(psi - st.psi)) <= 1e-10
+    assert rel(F, st.F) <= 1e-9
+    eo = O.energies(st)
+    for k in ("kin_e", "nl", "es", "xc", "total"):
+        assert abs(eg[k] - eo[k]) <= 1e-9 * abs(eo[k]), k
+    # orthonormality kept without constraints (Sec. 4.2, eq. escpro)
+    f = psi.reshape(s.n_orb, -1)
+    S = (f.conj() @ f.T) * s.h ** 3
+    assert np.max(np.abs(S - np.eye(s.n_orb))) < 1e-7
+
+
+def test_mu_scaling_bitwise_on_gpu(small):
+    s = small
+    out = []
+    for dt, mu in ((0.3, 7.0), (0.3 / 7.0, 1.0)):
+        g = emd.System(s)
+        emd.emd_set_option(g.handle, emd.EMD_OPT_FROZEN_IONS, 1)
+        g.propagate(3, dt=dt, mu=mu)
+        out.append(g.state()[2])
+        g.close()
+    assert np.array_equal(out[0], out[1])
+
+
+def test_runs_are_deterministic(small):
+    res = []
+    for _ in range(2):
+        g = emd.System(s := small)
+        g.propagate(3, dt=0.04, mu=1.0)
+        res.append((g.state()[2], g.forces()))
+        g.close()
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
+
+
+def test_unstable_time_step_refused():
+    """Taylor-4 on the imaginary axis is stable only for tau*lambda <= 2 sqrt 2:
+    the 96^3 order-8 workload at mu = 1, dt = 0.05 lies outside."""
+    s = inputs.small_system(n=32, h=0.25, fd_order=8, n_atoms=2, seed=3)
+    g = emd.System(s)
+    with pytest.raises(emd.EmdError) as ei:
+        g.propagate(1, dt=0.05, mu=1.0)
+    assert ei.value.code == emd.EMD_EUNSTABLE
+    g.propagate(1, dt=0.025, mu=1.0)
+    g.close()
+
+
+def test_propagate_before_state_is_refused(small):
+    h = emd.emd_init_system(emd.config_for(small))
+    with pytest.raises(emd.EmdError) as ei:
+        emd.emd_propagate(h, 1, 0.05, 1.0)
+    assert ei.value.code == emd.EMD_ESTATE
+    emd.emd_destroy(h)
+
+
+def test_fp32_orbitals_close_to_fp64(small):
+    """complex64 orbitals and stencil, FP64 density/energy/forces."""
+    s = small
+    res = {}
+    for prec in (emd.EMD_FP64, emd.EMD_FP32_ORBITALS):
+        g = emd.System(s, prec)
+        e0 = g.energy()["total"]
+        g.propagate(10, dt=0.04, mu=1.0)
+        res[prec] = (g.state()[2], g.forces(), g.energy()["total"], e0)
+        g.close()
+    psi64, F64, E64, E064 = res[emd.EMD_FP64]
+    psi32, F32, E32, E032 = res[emd.EMD_FP32_ORBITALS]
+    assert np.max(np.abs(psi32 - psi64)) < 1e-5
+    assert rel(F32, F64) < 1e-4
+    assert abs(E32 - E64) < 1e-5 * abs(E64)
+
+
+def test_precision_workload_sampled_hamiltonian():
+    """Full-size 96^3, 64-atom, order-8 workload (the benchmark shape): H psi
+    of 8 orbitals at sampled points against the oracle evaluated point by
+    point, in FP64 and in the FP32-orbital form."""
+    s = inputs.precision_c96(mu=10.0)
+    st_tables = O.atom_tables(s.R, s.species, s.n, s.h)
+    rng = np.random.default_rng(7)
+    pts = [tuple(int(v) for v in rng.integers(0, s.n, size=3)) for _ in range(24)]
+    pts += [(0, 0, 0), (95, 95, 95), (0, 95, 47)]
+    orbs = list(range(8))
+    for prec, tol in ((emd.EMD_FP64, 1e-11), (emd.EMD_FP32_ORBITALS, 2e-5)):
+        g = emd.System(s, prec)
+        pot = emd.emd_get_potentials(g.handle, s.n)
+        u = s.psi[:8]
+        hu = emd.emd_apply_hamiltonian(g.handle, u)
+        g.close()
+        v_eff = pot["v_loc"] + pot["v_h"] + pot["v_xc"]
+        c = O.projections(u, st_tables, s.species, s.h)
+        ref = O.hamiltonian_at_points(u, v_eff, c, s.R, s.species, s.h, s.fd_order, pts, orbs)
+        got = np.array([[hu[a, z, y, x] for (z, y, x) in pts] for a in orbs])
+        scale = np.max(np.abs(ref))
+        assert np.max(np.abs(got - ref)) < tol * scale, prec
