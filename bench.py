@@ -234,6 +234,47 @@ def time_e2e(emd, torch, sysin, precision, steps):
     return dt, bi, bo
 
 
+def time_batched(emd, torch, steps, n_replicas=32):
+    """32 ragged replicas (8-64 atoms, 48^3-80^3, 16-128 orbitals, order 8,
+    complex64, mu = 10): one batch whose 6-step chunks replay a captured CUDA
+    graph, against the same replicas propagated one after another."""
+    from paper_0812_2801_gb300 import autotune, inputs
+    specs = inputs.replica_specs(n_replicas, seed=5)
+    systems, upd = [], 0.0
+    tuned = {}
+    for i, spec in enumerate(specs):
+        sysin = inputs.replica(spec, i)
+        bo = autotune.best_block_orbitals(sysin, emd.EMD_FP32_ORBITALS)
+        tuned[f"n{sysin.n}-orb{sysin.n_orb}"] = bo
+        systems.append(emd.System(sysin, emd.EMD_FP32_ORBITALS, block_orbitals=bo))
+        upd += 8.0 * sysin.n_orb * sysin.n ** 3
+        sysin.psi = None
+    dt, mu = systems[0].sysin.dt, systems[0].sysin.mu
+    b = emd.emd_batch_create([g.handle for g in systems])
+    emd.emd_batch_propagate(b, 8, dt, mu)          # warm-up + graph capture
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    emd.emd_batch_propagate(b, steps, dt, mu)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    emd.emd_batch_destroy(b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g in systems:
+        g.propagate(steps, dt, mu)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    for g in systems:
+        g.close()
+    return {"value": upd * steps / t_batch, "unit": UNIT, "replicas": n_replicas,
+            "steps": steps, "ms_per_step": 1e3 * t_batch / steps,
+            "sequential_value": upd * steps / t_seq,
+            "speedup_vs_sequential": t_seq / t_batch,
+            "updates_per_step": upd, "block_orbitals": tuned,
+            "workload": "32 ragged replicas: 8-64 Si-like atoms, 48^3/64^3/80^3, "
+                        "2 orbitals per atom, order 8, complex64, mu 10, dt 0.158"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -243,6 +284,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--batched-steps", type=int, default=12)
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -285,6 +328,8 @@ def main():
     e2e_dt, bi, bo = time_e2e(emd, torch, s, emd.EMD_FP32_ORBITALS, args.e2e_steps)
     e2e_val = ws * upd_per_step * args.e2e_steps / e2e_dt
 
+    batched = None if args.no_batched else time_batched(emd, torch, args.batched_steps)
+
     peak, peak_kind = measured_peaks()
     stage_avg_s = r32["stage_ms"] * 1e-3 / max(1, r32["stage_launches"])
     bytes_launch = BYTES_PER_UPDATE["f32"] * s.n_orb * n3
@@ -316,6 +361,7 @@ def main():
                 "d2h_bytes_per_step": bo,
                 "note": "per step: set_ions + set_orbitals (pinned host, complex128), "
                         "propagate 1 MD step, get_state(psi) + get_forces + get_energy"},
+        "batched": batched,
         "gpu_launches": r32["launches"],
         "clocks": clk.summary(),
         "energy_total": r32["energy"]["total"],

@@ -182,6 +182,53 @@ int emd_set_option(emd_system *s, int option, double value);
 int emd_kernel_stats(emd_system *s, int kernel, double *ms_total,
                      long long *launches);
 
+/* Adjoint (backward-in-time) propagation.  The paper gives the forward
+ * dynamics only (Sec. 4.1, eq. new_EoM; Sec. 5.1, eq. aetrs); this is the
+ * exact discrete adjoint of the implemented step, for gradient-based uses of
+ * the trajectory (field optimisation, sensitivities).  Built for fixed ions
+ * (EMD_OPT_FROZEN_IONS set) and FP64 orbitals: the electrons evolve
+ * self-consistently (density -> Hartree + LDA -> extrapolated H(t+dt)) under
+ * the field e_n; the gradient is taken with respect to the static ion
+ * positions and every e_n.
+ *   observable EMD_OBS_DIPOLE_Z: L = -h^3 sum rho (z - L/2) + sum_J Z (Z_J - L/2)
+ *   observable EMD_OBS_ENERGY:   L = E_KS of the final state (eq. E_KS)
+ * Runs n_steps forward from the current state (storing orbitals and the
+ * v_Hxc history every ckpt_every steps), then backward segment by segment,
+ * recomputing each segment's steps from its checkpoint.  On return the
+ * system is at the final state; *L_out = L, dL_dR[n_atoms][3],
+ * dL_dfield[n_steps] (may be NULL if field is NULL).  Device workspace
+ * (about (n_steps/ckpt_every + ckpt_every + 13) orbital sets) is allocated
+ * on first use and kept until emd_destroy.  Synchronises.
+ * Errors: EMD_EINVAL, EMD_ESTATE (ions not fixed), EMD_ENOMEM, EMD_ECUDA. */
+#define EMD_OBS_ENERGY   0
+#define EMD_OBS_DIPOLE_Z 1
+int emd_propagate_adjoint(emd_system *s, int n_steps, double dt, double mu,
+                          const double *field, int ckpt_every, int observable,
+                          double *L_out, double *dL_dR, double *dL_dfield);
+
+/* Batched replicas: independent systems (any sizes, precisions, orders)
+ * advanced together.  Each system keeps its own state; a batch only
+ * schedules them.  After an eager warm-up (until every system's v_Hxc
+ * history holds three entries) the batch captures 6 MD steps of all systems
+ * into one CUDA graph, one parallel branch per system, and replays it for
+ * every further chunk of 6 steps; the remainder runs eagerly.  The graph is
+ * captured again if dt, mu or a system's position-set parity changes.  Work
+ * runs on internal streams ordered after, and followed by, each system's own
+ * stream.  No external field.  The paper has no batched form; replicas are
+ * how independent trajectories (e.g. thermal sampling, Sec. 6.3's 300 K
+ * starts) share one GPU.
+ *   emd_batch_create: systems[n] (caller keeps ownership; they must outlive
+ *     the batch and not be used concurrently with it).  Errors: EMD_EINVAL
+ *     (NULL or repeated system), EMD_ECUDA.
+ *   emd_batch_propagate: n_steps MD steps of every system (same dt, mu).
+ *     Errors as emd_propagate; EMD_ECUDA if graph capture fails (the systems
+ *     must then be re-initialised with emd_set_orbitals).  Enqueues only.
+ *   emd_batch_destroy: synchronises and releases the batch (not the systems). */
+typedef struct emd_batch emd_batch;
+int emd_batch_create(int n, emd_system *const *systems, emd_batch **out);
+int emd_batch_propagate(emd_batch *b, int n_steps, double dt, double mu);
+void emd_batch_destroy(emd_batch *b);
+
 /* Release all device memory and the handle.  NULL is accepted. */
 void emd_destroy(emd_system *s);
 

@@ -62,6 +62,23 @@ double fd_weight(int order, int k) {
 
 void emd_note_launches(int k) { g_launches += k; }
 
+// Device workspace of the adjoint propagation, sized on first use.
+struct Adjoint {
+  int n_ck = 0, K = 0;
+  std::vector<double2 *> ck_psi, seg_psi, st_u;      // orbital sets
+  std::vector<double *> ck_hist, seg_hist;          // 3 grids each
+  std::vector<int> ck_len, seg_len;
+  double2 *lam = nullptr, *mu = nullptr, *acc = nullptr, *zero = nullptr;
+  double *gv1 = nullptr, *gv2 = nullptr, *gvloc = nullptr, *L0 = nullptr,
+         *L1 = nullptr, *L2 = nullptr, *tmp = nullptr, *tmp2 = nullptr,
+         *saw = nullptr, *zgrid = nullptr, *gR = nullptr, *dfield = nullptr,
+         *scal = nullptr;
+  double2 *cm = nullptr, *dcm = nullptr, *cu = nullptr, *dcu = nullptr,
+          *hcu = nullptr;
+  int n_field = 0;
+  std::vector<void *> mem;
+};
+
 struct emd_system {
   emd_config cfg;
   GridInfo g;
@@ -85,7 +102,7 @@ struct emd_system {
   void *hc = nullptr;
   int c_valid = 0;
   double *V = nullptr, *F = nullptr, *F_loc = nullptr, *F_nl = nullptr,
-         *F_sr = nullptr, *e_sr = nullptr, *nl_part = nullptr;
+         *F_sr = nullptr, *e_sr = nullptr, *nl_part = nullptr, *lf_part = nullptr;
   double *partials = nullptr;
   int n_partials = 0;
   double *scal = nullptr;
@@ -97,6 +114,7 @@ struct emd_system {
   double prof_ms = 0.0;
   long long prof_launches = 0;
   std::vector<void *> allocs;
+  struct Adjoint *adj = nullptr;
 };
 
 namespace {
@@ -213,7 +231,7 @@ void electrons(emd_system *s, int slot) {
 // Forces at set k (projections of psi at k must be in c).
 void forces(emd_system *s, int k, double field, double dt, int update_v) {
   emd_launch_local_force(s->g, s->sp, s->n_atoms, s->ts[k].Rw, s->v_h,
-                         s->ts[k].v_loc, s->F_loc, s->st);
+                         s->ts[k].v_loc, s->lf_part, s->F_loc, s->st);
   emd_launch_nl_force(s->o, s->ts[k], s->n_atoms, s->psi, s->c,
                       s->g.h * s->g.h * s->g.h,
                       -2.0 * s->sp.h_kb * s->cfg.occ, s->sp.inv_rc2,
@@ -259,14 +277,15 @@ __global__ void k_negate(double *v, int n) {
 __global__ void k_max_sum(const double *a, const double *b, int n, double *out) {
   __shared__ double sm[256];
   double m = -1e300;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, a[i] + b[i]);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    m = fmax(m, a[i] + b[i]);
   sm[threadIdx.x] = m;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if (threadIdx.x < o) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + o]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = sm[0];
+  if (threadIdx.x == 0) out[blockIdx.x] = sm[0];
 }
 void negate_grid(double *v, int n3, cudaStream_t st) {
   emd_note_launches(1);
@@ -274,11 +293,14 @@ void negate_grid(double *v, int n3, cudaStream_t st) {
 }
 int reduce_max_veff(emd_system *s, double *out) {
   emd_note_launches(1);
-  k_max_sum<<<1, 256, 0, s->st>>>(s->hist[0], s->ts[s->cur].v_loc, s->g.n3,
-                                   s->scal + 15);
-  CK(cudaMemcpyAsync(out, s->scal + 15, sizeof(double), cudaMemcpyDeviceToHost,
-                     s->st));
+  const int nb = std::min(s->n_partials, 512);
+  k_max_sum<<<nb, 256, 0, s->st>>>(s->hist[0], s->ts[s->cur].v_loc, s->g.n3,
+                                    s->partials);
+  std::vector<double> hm(nb);
+  CK(cudaMemcpyAsync(hm.data(), s->partials, nb * sizeof(double),
+                     cudaMemcpyDeviceToHost, s->st));
   CK(cudaStreamSynchronize(s->st));
+  *out = *std::max_element(hm.begin(), hm.end());
   return EMD_OK;
 }
 }  // namespace
@@ -302,7 +324,8 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
   if (!(c.occ > 0.0)) return fail(EMD_EINVAL, "occ must be > 0");
   if (c.precision != EMD_FP64 && c.precision != EMD_FP32_ORBITALS)
     return fail(EMD_EINVAL, "precision must be EMD_FP64 or EMD_FP32_ORBITALS");
-  if (c.n_atoms < 0) return fail(EMD_EINVAL, "n_atoms must be >= 0");
+  if (c.n_atoms < 0 || c.n_atoms > 32767)
+    return fail(EMD_EINVAL, "n_atoms must be in [0, 32767]");
   const emd_species &p = c.species;
   const double L = c.n * c.h;
   if (c.n_atoms > 0) {
@@ -354,6 +377,7 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
   o.n_blk = (c.n_orb + o.bo - 1) / o.bo;
   o.n_orb_pad = o.n_blk * o.bo;
   o.half_order = c.fd_order / 2;
+  o.n_atoms = c.n_atoms;
   for (int k = 0; k <= EMD_MAX_HALF_ORDER; ++k) o.w[k] = 0.0;
   o.w[0] = -1.5 * fd_weight(c.fd_order, 0) / (c.h * c.h);
   for (int k = 1; k <= o.half_order; ++k)
@@ -402,7 +426,10 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
     TRY(A((void **)&t.pt_cnt, n3 * 4));
     TRY(A((void **)&t.pt_J, n3 * EMD_PT_KMAX * 4));
     TRY(A((void **)&t.pt_p, n3 * EMD_PT_KMAX * 8));
+    TRY(A((void **)&t.pt_pf, n3 * EMD_PT_KMAX * 4));
+    TRY(A((void **)&t.pt4, n3 * 4 * sizeof(int2)));
     TRY(A((void **)&t.at_cnt, na * 4));
+    TRY(A((void **)&t.split_cnt, na * EMD_SPLIT * 4));
     TRY(A((void **)&t.at_pt, (size_t)na * cap * 4));
     TRY(A((void **)&t.at_p, (size_t)na * cap * 8));
     TRY(A((void **)&t.at_d, (size_t)na * cap * 24));
@@ -418,6 +445,7 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
   TRY(A((void **)&s->F_sr, na * 3 * 8));
   TRY(A((void **)&s->e_sr, na * 8));
   TRY(A((void **)&s->nl_part, (size_t)na * o.n_blk * 3 * 8));
+  TRY(A((void **)&s->lf_part, (size_t)na * EMD_SPLIT * 3 * 8));
   s->n_partials = std::max(1024, (int)((n3 + 255) / 256));
   TRY(A((void **)&s->partials, (size_t)s->n_partials * 8));
   TRY(A((void **)&s->scal, 16 * 8));
@@ -515,18 +543,18 @@ int emd_set_option(emd_system *s, int option, double value) {
   return fail(EMD_EINVAL, "unknown option %d", option);
 }
 
-int emd_propagate(emd_system *s, int n_steps, double dt, double mu,
-                  const double *field) {
-  g_err.clear();
+}  // extern "C"
+
+namespace {
+
+// Argument validation and the Taylor-4 stability refusal shared by the
+// single-system and batched propagation.
+int check_propagate(emd_system *s, double dt, double mu) {
   if (!s) return fail(EMD_EINVAL, "NULL system");
   if (!s->ions_set || !s->orbs_set)
     return fail(EMD_ESTATE, "set ions and orbitals before propagating");
-  if (n_steps < 0) return fail(EMD_EINVAL, "n_steps must be >= 0");
   if (!(dt > 0.0) || !(mu > 0.0) || !std::isfinite(dt) || !std::isfinite(mu))
     return fail(EMD_EINVAL, "dt and mu must be finite and > 0");
-  if (field)
-    for (int i = 0; i < n_steps; ++i)
-      if (!std::isfinite(field[i])) return fail(EMD_EINVAL, "non-finite field");
   const double tau = 0.5 * (dt / mu);
   if (s->check_stable) {
     const double lam = 1.5 * kinetic_lambda_max(s->cfg.fd_order) / (s->g.h * s->g.h) +
@@ -538,46 +566,575 @@ int emd_propagate(emd_system *s, int n_steps, double dt, double mu,
                   "2*sqrt(2) (tau = dt/(2 mu) = %g, lambda_max ~ %.2f)",
                   x, tau, lam);
   }
+  return EMD_OK;
+}
+
+// One MD step on s->st (enqueue only; no host synchronisation, so it can be
+// captured into a CUDA graph).
+int step_once(emd_system *s, double dt, double mu, double e) {
+  const double tau = 0.5 * (dt / mu);
+  const int cur = s->cur;
+  const int nw = s->frozen_ions ? cur : 1 - cur;
+  if (!s->frozen_ions) {
+    emd_launch_vv_positions(s->n_atoms, s->ts[cur].R, s->V, s->F, dt,
+                            s->sp.mass, s->ts[nw].R, s->st);
+    int r = build_set(s, nw);
+    if (r) return r;
+    negate_grid(s->ts[nw].v_loc, s->g.n3, s->st);
+  }
+  emd_launch_veff(s->g, s->ts[cur].v_loc, s->hist, 1, e, s->veff1, s->veff1f,
+                  s->st);
+  emd_launch_veff(s->g, s->ts[nw].v_loc, s->hist, s->hist_len, e, s->veff2,
+                  s->veff2f, s->st);
+  if (!s->c_valid) project(s, s->psi, cur);
+  // exponential 1: psi -> ub with H(t)
+  exponential(s, s->psi, s->ua, s->ub, cur, 1, tau);
+  project(s, s->ub, nw);
+  // exponential 2: ub -> psi with H(t+dt)
+  exponential(s, s->ub, s->ua, s->psi, nw, 2, tau);
+  // new density and potentials; history slot of the oldest entry
+  double *oldest = s->hist[2];
+  s->hist[2] = s->hist[1];
+  s->hist[1] = s->hist[0];
+  s->hist[0] = oldest;
+  electrons(s, 0);
+  s->hist_len = std::min(3, s->hist_len + 1);
+  if (!s->frozen_ions) {
+    project(s, s->psi, nw);
+    forces(s, nw, e, dt, 1);
+    s->cur = nw;
+    s->c_valid = 1;
+  } else {
+    s->c_valid = 0;
+  }
+  return launch_check("emd_propagate");
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Batched replicas: independent systems advanced together.  After a short
+// eager warm-up (until every v_Hxc history is full), chunks of 6 MD steps of
+// all systems are captured once into a CUDA graph -- one parallel branch per
+// system, so ragged replicas share the GPU -- and replayed.  6 steps is the
+// period of the host-side state (position sets alternate with period 2, the
+// three v_Hxc history slots rotate with period 3), so a replay leaves it
+// unchanged.
+// ---------------------------------------------------------------------------
+struct emd_batch {
+  std::vector<emd_system *> sys;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> done;
+  cudaStream_t origin = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double key_dt = 0.0, key_mu = 0.0;
+  std::vector<int> key_cur;
+  long long graph_launches = 0;
+};
+
+namespace {
+constexpr int kGraphSteps = 6;
+
+int batch_capture(emd_batch *b, double dt, double mu) {
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  std::vector<int> prof(b->sys.size());
+  for (size_t i = 0; i < b->sys.size(); ++i) {
+    prof[i] = b->sys[i]->profile;
+    b->sys[i]->profile = 0;
+  }
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+  int rc = EMD_OK;
+  if (cudaEventRecord(b->fork, b->origin) != cudaSuccess) rc = EMD_ECUDA;
+  for (size_t i = 0; i < b->sys.size() && rc == EMD_OK; ++i) {
+    if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) {
+      rc = EMD_ECUDA;
+      break;
+    }
+    for (int k = 0; k < kGraphSteps && rc == EMD_OK; ++k)
+      rc = step_once(b->sys[i], dt, mu, 0.0);
+    if (rc == EMD_OK && (cudaEventRecord(b->done[i], b->streams[i]) != cudaSuccess ||
+                         cudaStreamWaitEvent(b->origin, b->done[i], 0) != cudaSuccess))
+      rc = EMD_ECUDA;
+  }
+  cudaError_t e = cudaStreamEndCapture(b->origin, &graph);
+  for (size_t i = 0; i < b->sys.size(); ++i) b->sys[i]->profile = prof[i];
+  if (rc != EMD_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc != EMD_OK ? rc : fail(EMD_ECUDA, "graph capture failed: %s",
+                                     cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    b->exec = nullptr;
+    return fail(EMD_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  }
+  b->key_dt = dt;
+  b->key_mu = mu;
+  b->key_cur.resize(b->sys.size());
+  for (size_t i = 0; i < b->sys.size(); ++i) b->key_cur[i] = b->sys[i]->cur;
+  return EMD_OK;
+}
+
+bool batch_graph_valid(const emd_batch *b, double dt, double mu) {
+  if (!b->exec || b->key_dt != dt || b->key_mu != mu) return false;
+  for (size_t i = 0; i < b->sys.size(); ++i)
+    if (b->key_cur[i] != b->sys[i]->cur) return false;
+  return true;
+}
+}  // namespace
+
+extern "C" {
+
+int emd_propagate(emd_system *s, int n_steps, double dt, double mu,
+                  const double *field) {
+  g_err.clear();
+  int r = check_propagate(s, dt, mu);
+  if (r) return r;
+  if (n_steps < 0) return fail(EMD_EINVAL, "n_steps must be >= 0");
+  if (field)
+    for (int i = 0; i < n_steps; ++i)
+      if (!std::isfinite(field[i])) return fail(EMD_EINVAL, "non-finite field");
   for (int step = 0; step < n_steps; ++step) {
-    const double e = field ? field[step] : 0.0;
-    const int cur = s->cur;
-    const int nw = s->frozen_ions ? cur : 1 - cur;
-    if (!s->frozen_ions) {
-      emd_launch_vv_positions(s->n_atoms, s->ts[cur].R, s->V, s->F, dt,
-                              s->sp.mass, s->ts[nw].R, s->st);
-      int r = build_set(s, nw);
-      if (r) return r;
-      negate_grid(s->ts[nw].v_loc, s->g.n3, s->st);
-    }
-    emd_launch_veff(s->g, s->ts[cur].v_loc, s->hist, 1, e, s->veff1, s->veff1f,
-                    s->st);
-    emd_launch_veff(s->g, s->ts[nw].v_loc, s->hist, s->hist_len, e, s->veff2,
-                    s->veff2f, s->st);
-    if (!s->c_valid) project(s, s->psi, cur);
-    // exponential 1: psi -> ub with H(t)
-    exponential(s, s->psi, s->ua, s->ub, cur, 1, tau);
-    project(s, s->ub, nw);
-    // exponential 2: ub -> psi with H(t+dt)
-    exponential(s, s->ub, s->ua, s->psi, nw, 2, tau);
-    // new density and potentials; history slot of the oldest entry
-    double *oldest = s->hist[2];
-    s->hist[2] = s->hist[1];
-    s->hist[1] = s->hist[0];
-    s->hist[0] = oldest;
-    electrons(s, 0);
-    s->hist_len = std::min(3, s->hist_len + 1);
-    if (!s->frozen_ions) {
-      project(s, s->psi, nw);
-      forces(s, nw, e, dt, 1);
-      s->cur = nw;
-      s->c_valid = 1;
-    } else {
-      s->c_valid = 0;
-    }
-    int r = launch_check("emd_propagate");
+    r = step_once(s, dt, mu, field ? field[step] : 0.0);
     if (r) return r;
   }
   return EMD_OK;
+}
+
+int emd_batch_create(int n, emd_system *const *systems, emd_batch **out) {
+  g_err.clear();
+  if (!out || !systems || n < 1) return fail(EMD_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!systems[i]) return fail(EMD_EINVAL, "NULL system %d", i);
+    for (int k = 0; k < i; ++k)
+      if (systems[k] == systems[i]) return fail(EMD_EINVAL, "system %d repeated", i);
+  }
+  emd_batch *b = new emd_batch();
+  b->sys.assign(systems, systems + n);
+  bool ok = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < n && ok; ++i) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) b->streams.push_back(st);
+    ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) b->done.push_back(ev);
+  }
+  if (!ok) {
+    emd_batch_destroy(b);
+    return fail(EMD_ECUDA, "stream/event creation failed");
+  }
+  *out = b;
+  return EMD_OK;
+}
+
+int emd_batch_propagate(emd_batch *b, int n_steps, double dt, double mu) {
+  g_err.clear();
+  if (!b) return fail(EMD_EINVAL, "NULL batch");
+  if (n_steps < 0) return fail(EMD_EINVAL, "n_steps must be >= 0");
+  const size_t m = b->sys.size();
+  for (size_t i = 0; i < m; ++i) {
+    int r = check_propagate(b->sys[i], dt, mu);
+    if (r) return r;
+  }
+  // internal streams follow each system's own stream, and back at the end
+  std::vector<cudaStream_t> user(m);
+  for (size_t i = 0; i < m; ++i) {
+    user[i] = b->sys[i]->st;
+    CK(cudaEventRecord(b->done[i], user[i]));
+    CK(cudaStreamWaitEvent(b->streams[i], b->done[i], 0));
+    b->sys[i]->st = b->streams[i];
+  }
+  int rc = EMD_OK;
+  int done_steps = 0;
+  auto eager = [&](int k) {
+    for (int s = 0; s < k && rc == EMD_OK; ++s)
+      for (size_t i = 0; i < m && rc == EMD_OK; ++i)
+        rc = step_once(b->sys[i], dt, mu, 0.0);
+  };
+  auto full_history = [&]() {
+    for (size_t i = 0; i < m; ++i)
+      if (b->sys[i]->hist_len < 3 || b->sys[i]->frozen_ions) return false;
+    return true;
+  };
+  while (rc == EMD_OK && done_steps < n_steps &&
+         !(full_history() && n_steps - done_steps >= kGraphSteps)) {
+    eager(1);
+    ++done_steps;
+  }
+  while (rc == EMD_OK && n_steps - done_steps >= kGraphSteps) {
+    if (!batch_graph_valid(b, dt, mu)) rc = batch_capture(b, dt, mu);
+    if (rc != EMD_OK) break;
+    for (size_t i = 0; i < m && rc == EMD_OK; ++i)
+      if (cudaEventRecord(b->done[i], b->streams[i]) != cudaSuccess ||
+          cudaStreamWaitEvent(b->origin, b->done[i], 0) != cudaSuccess)
+        rc = fail(EMD_ECUDA, "batch ordering failed");
+    if (rc != EMD_OK) break;
+    cudaError_t e = cudaGraphLaunch(b->exec, b->origin);
+    if (e != cudaSuccess) {
+      rc = fail(EMD_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+      break;
+    }
+    ++b->graph_launches;
+    emd_note_launches(0);
+    CK(cudaEventRecord(b->fork, b->origin));
+    for (size_t i = 0; i < m; ++i) CK(cudaStreamWaitEvent(b->streams[i], b->fork, 0));
+    done_steps += kGraphSteps;
+  }
+  if (rc == EMD_OK) eager(n_steps - done_steps);
+  for (size_t i = 0; i < m; ++i) {
+    b->sys[i]->st = user[i];
+    if (cudaEventRecord(b->done[i], b->streams[i]) == cudaSuccess)
+      cudaStreamWaitEvent(user[i], b->done[i], 0);
+  }
+  return rc;
+}
+
+void emd_batch_destroy(emd_batch *b) {
+  if (!b) return;
+  for (cudaStream_t st : b->streams) cudaStreamSynchronize(st);
+  if (b->origin) cudaStreamSynchronize(b->origin);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->done) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  delete b;
+}
+
+}  // extern "C"
+
+namespace {
+
+int adj_alloc(emd_system *s, int n_ck, int K, int n_steps) {
+  Adjoint *&A = s->adj;
+  if (A && A->n_ck >= n_ck && A->K >= K && A->n_field >= n_steps) return EMD_OK;
+  if (A) {
+    for (void *p : A->mem) cudaFree(p);
+    delete A;
+    A = nullptr;
+  }
+  A = new Adjoint();
+  const size_t n3 = s->g.n3;
+  const size_t ob = s->orb_bytes, gb = n3 * sizeof(double);
+  const size_t cb = (size_t)std::max(1, s->n_atoms) * s->o.n_orb_pad * sizeof(double2);
+  auto get = [&](void **p, size_t b) -> int {
+    if (cudaMalloc(p, b) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return fail(EMD_ENOMEM, "adjoint workspace: cudaMalloc(%zu) failed", b);
+    }
+    A->mem.push_back(*p);
+    return EMD_OK;
+  };
+#define AG(ptr, b) do { int r_ = get((void **)&(ptr), (b)); if (r_) return r_; } while (0)
+  A->n_ck = n_ck;
+  A->K = K;
+  A->n_field = n_steps;
+  A->ck_psi.resize(n_ck + 1);   // last: the final state, restored at the end
+  A->ck_hist.resize(n_ck + 1);
+  A->ck_len.resize(n_ck + 1);
+  for (int i = 0; i <= n_ck; ++i) {
+    AG(A->ck_psi[i], ob);
+    AG(A->ck_hist[i], 3 * gb);
+  }
+  A->seg_psi.resize(K);
+  A->seg_hist.resize(K);
+  A->seg_len.resize(K);
+  for (int i = 0; i < K; ++i) {
+    AG(A->seg_psi[i], ob);
+    AG(A->seg_hist[i], 3 * gb);
+  }
+  A->st_u.resize(7);
+  for (int i = 0; i < 7; ++i) AG(A->st_u[i], ob);
+  AG(A->lam, ob);
+  AG(A->mu, 2 * ob);
+  AG(A->acc, ob);
+  AG(A->zero, ob);
+  double **grids[] = {&A->gv1, &A->gv2, &A->gvloc, &A->L0, &A->L1, &A->L2,
+                      &A->tmp, &A->tmp2, &A->saw, &A->zgrid};
+  for (double **gp : grids) AG(*gp, gb);
+  AG(A->gR, 3 * std::max(1, s->n_atoms) * sizeof(double));
+  AG(A->dfield, std::max(1, n_steps) * sizeof(double));
+  AG(A->scal, 8 * sizeof(double));
+  AG(A->cm, cb);
+  AG(A->cu, cb);
+  AG(A->hcu, cb);
+  AG(A->dcm, 3 * cb);
+  AG(A->dcu, 3 * cb);
+#undef AG
+  CK(cudaMemsetAsync(A->zero, 0, ob, s->st));
+  CK(cudaMemsetAsync(A->zgrid, 0, gb, s->st));
+  // s(z) = z h - L/2 on the grid (length-gauge field coordinate)
+  std::vector<double> saw(n3);
+  for (size_t p = 0; p < n3; ++p)
+    saw[p] = (double)(p / ((size_t)s->g.n * s->g.n)) * s->g.h - 0.5 * s->g.L;
+  CK(cudaMemcpy(A->saw, saw.data(), gb, cudaMemcpyHostToDevice));
+  return EMD_OK;
+}
+
+void copy_hist_out(emd_system *s, double *dst) {
+  const size_t gb = (size_t)s->g.n3 * sizeof(double);
+  for (int k = 0; k < 3; ++k)
+    cudaMemcpyAsync(dst + (size_t)k * s->g.n3, s->hist[k], gb,
+                    cudaMemcpyDeviceToDevice, s->st);
+}
+void copy_hist_in(emd_system *s, const double *src) {
+  const size_t gb = (size_t)s->g.n3 * sizeof(double);
+  for (int k = 0; k < 3; ++k)
+    cudaMemcpyAsync(s->hist[k], src + (size_t)k * s->g.n3, gb,
+                    cudaMemcpyDeviceToDevice, s->st);
+}
+
+// grid dot product a . b into *dst (device)
+void grid_dot(emd_system *s, const double *a, const double *b, double *dst) {
+  const int nb = std::min(s->n_partials, 1024);
+  emd_launch_dot_partials(s->g.n3, a, b, nullptr, nullptr, s->partials, nb, s->st);
+  emd_launch_sum(s->partials, nb, dst, s->st);
+}
+
+// Reverse of one exponential T4(-i tau H) (nested stages k = 1..4 whose
+// inputs are u[0..3] = u_2, u_3, u_4, psi0).  mu_in: adjoint of the output;
+// on return acc holds the adjoint of psi0; gv += dL/dv_eff; gR += dL/dR.
+void reverse_exponential(emd_system *s, const double2 *mu_in, double2 *acc,
+                         double2 *const u[4], int which_veff, double tau,
+                         double *gv) {
+  Adjoint *A = s->adj;
+  const OrbLayout &o = s->o;
+  const size_t nel = (size_t)o.n_blk * o.n3 * o.bo;
+  const double h3 = s->g.h * s->g.h * s->g.h;
+  double2 *mu = A->mu, *mu2 = A->mu + nel;
+  cudaMemcpyAsync(mu, mu_in, s->orb_bytes, cudaMemcpyDeviceToDevice, s->st);
+  cudaMemsetAsync(acc, 0, s->orb_bytes, s->st);
+  const TableSet &t = s->ts[s->cur];
+  for (int k = 1; k <= 4; ++k) {
+    const double b = tau / k;
+    emd_adj_axpy(acc, mu, nel, s->st);
+    emd_adj_gv(o, mu, u[k - 1], b, gv, s->st);
+    emd_adj_project_grad(o, t, s->n_atoms, mu, h3, s->sp.h_kb, s->sp.inv_rc2,
+                         A->cm, (double2 *)s->hc, A->dcm, s->st);
+    emd_adj_project_grad(o, t, s->n_atoms, u[k - 1], h3, s->sp.h_kb,
+                         s->sp.inv_rc2, A->cu, A->hcu, A->dcu, s->st);
+    emd_adj_proj_sens(A->cm, A->dcm, A->cu, A->dcu, s->n_atoms, o.n_orb,
+                      o.n_orb_pad, s->sp.h_kb * b / h3, A->gR, s->st);
+    // mu <- conj(a_k) H mu = (+i b) H mu
+    stage(s, mu, A->zero, mu2, s->cur, which_veff, -b);
+    std::swap(mu, mu2);
+  }
+  emd_adj_axpy(acc, mu, nel, s->st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int emd_propagate_adjoint(emd_system *s, int n_steps, double dt, double mu,
+                          const double *field, int ckpt_every, int observable,
+                          double *L_out, double *dL_dR, double *dL_dfield) {
+  g_err.clear();
+  int r = check_propagate(s, dt, mu);
+  if (r) return r;
+  if (s->o.prec != EMD_FP64)
+    return fail(EMD_EINVAL, "adjoint propagation needs FP64 orbitals");
+  if (!s->frozen_ions)
+    return fail(EMD_ESTATE, "adjoint propagation is built for fixed ions: set "
+                            "EMD_OPT_FROZEN_IONS (moving-ion adjoint not built)");
+  if (n_steps < 1 || ckpt_every < 1)
+    return fail(EMD_EINVAL, "n_steps and ckpt_every must be >= 1");
+  if (observable != EMD_OBS_ENERGY && observable != EMD_OBS_DIPOLE_Z)
+    return fail(EMD_EINVAL, "unknown observable %d", observable);
+  if (!L_out || (!dL_dR && s->n_atoms) || (field && !dL_dfield))
+    return fail(EMD_EINVAL, "NULL output");
+  std::vector<double> fe(n_steps, 0.0);
+  if (field)
+    for (int i = 0; i < n_steps; ++i) {
+      if (!std::isfinite(field[i])) return fail(EMD_EINVAL, "non-finite field");
+      fe[i] = field[i];
+    }
+  const int K = std::min(ckpt_every, n_steps);
+  const int n_ck = (n_steps + K - 1) / K;
+  r = adj_alloc(s, n_ck, K, n_steps);
+  if (r) return r;
+  Adjoint *A = s->adj;
+  const OrbLayout &o = s->o;
+  const int n3 = s->g.n3;
+  const size_t gb = (size_t)n3 * sizeof(double);
+  const double h3 = s->g.h * s->g.h * s->g.h;
+  const double tau = 0.5 * (dt / mu);
+  const double occ = s->cfg.occ;
+  const int na = s->n_atoms;
+
+  // ---- forward sweep with orbital + history checkpoints every K steps
+  for (int n = 0; n < n_steps; ++n) {
+    if (n % K == 0) {
+      const int ck = n / K;
+      CK(cudaMemcpyAsync(A->ck_psi[ck], s->psi, s->orb_bytes, cudaMemcpyDeviceToDevice, s->st));
+      copy_hist_out(s, A->ck_hist[ck]);
+      A->ck_len[ck] = s->hist_len;
+    }
+    r = step_once(s, dt, mu, fe[n]);
+    if (r) return r;
+  }
+  CK(cudaMemcpyAsync(A->ck_psi[n_ck], s->psi, s->orb_bytes, cudaMemcpyDeviceToDevice, s->st));
+  copy_hist_out(s, A->ck_hist[n_ck]);
+  A->ck_len[n_ck] = s->hist_len;
+
+  // ---- observable and the adjoint of the final state
+  std::vector<double> gR_host(3 * std::max(1, na), 0.0);
+  CK(cudaMemsetAsync(A->lam, 0, s->orb_bytes, s->st));
+  double L = 0.0;
+  if (observable == EMD_OBS_DIPOLE_Z) {
+    grid_dot(s, s->rho, A->saw, A->scal);
+    double dot = 0.0;
+    std::vector<double> Rw(3 * std::max(1, na));
+    CK(cudaMemcpyAsync(&dot, A->scal, sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    if (na) CK(cudaMemcpyAsync(Rw.data(), s->ts[s->cur].Rw, 3 * na * 8, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    L = -h3 * dot;
+    for (int J = 0; J < na; ++J) {
+      L += s->sp.z * (Rw[3 * J + 2] - 0.5 * s->g.L);
+      gR_host[3 * J + 2] += s->sp.z;
+    }
+    emd_adj_scale_add(o, A->lam, (const double2 *)s->psi, A->saw, -2.0 * occ * h3, s->st);
+  } else {
+    emd_energy e;
+    r = emd_get_energy(s, &e);
+    if (r) return r;
+    L = e.ks;
+    // lambda = 2 f h^3 H[rho_N] psi_N ; dL/dR = -F at fixed orbitals
+    emd_launch_veff(s->g, s->ts[s->cur].v_loc, s->hist, 1, 0.0, s->veff1, s->veff1f, s->st);
+    project(s, s->psi, s->cur);
+    StageArgs a_;
+    a_.u_in = s->psi;
+    a_.psi0 = s->psi;
+    a_.u_out = A->acc;
+    a_.v_eff = s->veff1;
+    a_.tab = &s->ts[s->cur];
+    a_.hc = s->hc;
+    a_.a = 0.0;
+    a_.apply_only = 1;
+    emd_launch_stage(o, a_, s->st);
+    // w = 1 on every point: tmp as a grid of ones
+    std::vector<double> ones(n3, 1.0);
+    CK(cudaMemcpyAsync(A->tmp, ones.data(), gb, cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    emd_adj_scale_add(o, A->lam, A->acc, A->tmp, 2.0 * occ * h3, s->st);
+    s->c_valid = 1;
+    forces(s, s->cur, 0.0, 0.0, 0);
+    std::vector<double> F(3 * std::max(1, na));
+    if (na) CK(cudaMemcpyAsync(F.data(), s->F, 3 * na * 8, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    for (int i = 0; i < 3 * na; ++i) gR_host[i] -= F[i];
+  }
+  CK(cudaMemsetAsync(A->L0, 0, gb, s->st));
+  CK(cudaMemsetAsync(A->L1, 0, gb, s->st));
+  CK(cudaMemsetAsync(A->L2, 0, gb, s->st));
+  CK(cudaMemsetAsync(A->gvloc, 0, gb, s->st));
+  CK(cudaMemsetAsync(A->gR, 0, 3 * std::max(1, na) * 8, s->st));
+  CK(cudaMemsetAsync(A->dfield, 0, n_steps * 8, s->st));
+
+  // ---- reverse sweep, last segment first
+  for (int ck = n_ck - 1; ck >= 0; --ck) {
+    const int n0 = ck * K, n1 = std::min(n_steps, n0 + K);
+    CK(cudaMemcpyAsync(s->psi, A->ck_psi[ck], s->orb_bytes, cudaMemcpyDeviceToDevice, s->st));
+    copy_hist_in(s, A->ck_hist[ck]);
+    s->hist_len = A->ck_len[ck];
+    s->c_valid = 0;
+    for (int n = n0; n < n1; ++n) {
+      CK(cudaMemcpyAsync(A->seg_psi[n - n0], s->psi, s->orb_bytes, cudaMemcpyDeviceToDevice, s->st));
+      copy_hist_out(s, A->seg_hist[n - n0]);
+      A->seg_len[n - n0] = s->hist_len;
+      r = step_once(s, dt, mu, fe[n]);
+      if (r) return r;
+    }
+    for (int n = n1 - 1; n >= n0; --n) {
+      const double2 *psi_next = n == n1 - 1 ? (const double2 *)s->psi : A->seg_psi[n + 1 - n0];
+      // adjoint of v_Hxc(rho_{n+1}) (history slot 0 of step n+1) -> psi_{n+1}
+      emd_launch_density(o, psi_next, occ, A->tmp2, s->st);
+      emd_launch_poisson(s->g, A->L0, A->tmp, s->fft_a, s->fft_b, s->st);
+      emd_adj_rho(n3, A->tmp2, A->L0, A->tmp, s->st);
+      emd_adj_scale_add(o, A->lam, psi_next, A->tmp, 2.0 * occ, s->st);
+      // recompute the stage inputs of step n
+      const double2 *psi_n = A->seg_psi[n - n0];
+      const double *hn = A->seg_hist[n - n0];
+      const double *hp[3] = {hn, hn + n3, hn + 2 * (size_t)n3};
+      const int len = A->seg_len[n - n0];
+      emd_launch_veff(s->g, s->ts[s->cur].v_loc, hp, 1, fe[n], s->veff1, s->veff1f, s->st);
+      emd_launch_veff(s->g, s->ts[s->cur].v_loc, hp, len, fe[n], s->veff2, s->veff2f, s->st);
+      double2 *const *U = A->st_u.data();
+      // exponential 1 from psi_n: U0 = u4, U1 = u3, U2 = u2, U3 = output psi1
+      project(s, psi_n, s->cur);
+      stage(s, psi_n, psi_n, U[0], s->cur, 1, tau / 4.0);
+      project(s, U[0], s->cur);
+      stage(s, U[0], psi_n, U[1], s->cur, 1, tau / 3.0);
+      project(s, U[1], s->cur);
+      stage(s, U[1], psi_n, U[2], s->cur, 1, tau / 2.0);
+      project(s, U[2], s->cur);
+      stage(s, U[2], psi_n, U[3], s->cur, 1, tau);
+      // exponential 2 from psi1 = U3: U4 = u4', U5 = u3', U6 = u2'
+      project(s, U[3], s->cur);
+      stage(s, U[3], U[3], U[4], s->cur, 2, tau / 4.0);
+      project(s, U[4], s->cur);
+      stage(s, U[4], U[3], U[5], s->cur, 2, tau / 3.0);
+      project(s, U[5], s->cur);
+      stage(s, U[5], U[3], U[6], s->cur, 2, tau / 2.0);
+      // reverse exponential 2 then exponential 1
+      CK(cudaMemsetAsync(A->gv2, 0, gb, s->st));
+      CK(cudaMemsetAsync(A->gv1, 0, gb, s->st));
+      double2 *const in2[4] = {U[6], U[5], U[4], U[3]};
+      reverse_exponential(s, A->lam, A->acc, in2, 2, tau, A->gv2);
+      double2 *const in1[4] = {U[2], U[1], U[0], (double2 *)psi_n};
+      reverse_exponential(s, A->acc, A->lam, in1, 1, tau, A->gv1);
+      // field, ionic potential and history adjoints
+      emd_adj_lincomb(n3, A->tmp, 1.0, A->gv1, 1.0, A->gv2, 0.0, nullptr, 0.0, nullptr, s->st);
+      grid_dot(s, A->tmp, A->saw, A->dfield + n);
+      emd_adj_lincomb(n3, A->gvloc, 1.0, A->gvloc, 1.0, A->tmp, 0.0, nullptr, 0.0, nullptr, s->st);
+      const double x0 = len <= 1 ? 1.0 : len == 2 ? 2.0 : 3.0;
+      const double x1 = len <= 1 ? 0.0 : len == 2 ? -1.0 : -3.0;
+      const double x2 = len <= 2 ? 0.0 : 1.0;
+      // new L0 = L1 + gv1 + x0 gv2 ; L1 = L2 + x1 gv2 ; L2 = x2 gv2
+      emd_adj_lincomb(n3, A->tmp, 1.0, A->L1, 1.0, A->gv1, x0, A->gv2, 0.0, nullptr, s->st);
+      emd_adj_lincomb(n3, A->L1, 1.0, A->L2, x1, A->gv2, 0.0, nullptr, 0.0, nullptr, s->st);
+      emd_adj_lincomb(n3, A->L2, x2, A->gv2, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr, s->st);
+      std::swap(A->L0, A->tmp);
+      r = launch_check("emd_propagate_adjoint");
+      if (r) return r;
+    }
+  }
+
+  // ---- ionic potential adjoint: dL/dR_J = -h^-3 F_loc[w], w = Poisson(gvloc)
+  emd_launch_poisson(s->g, A->gvloc, A->tmp, s->fft_a, s->fft_b, s->st);
+  emd_launch_local_force(s->g, s->sp, na, s->ts[s->cur].Rw, A->tmp, A->zgrid,
+                         s->lf_part, s->F_loc, s->st);
+  std::vector<double> Fw(3 * std::max(1, na)), gRd(3 * std::max(1, na));
+  if (na) {
+    CK(cudaMemcpyAsync(Fw.data(), s->F_loc, 3 * na * 8, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(gRd.data(), A->gR, 3 * na * 8, cudaMemcpyDeviceToHost, s->st));
+  }
+  if (dL_dfield)
+    CK(cudaMemcpyAsync(dL_dfield, A->dfield, n_steps * 8, cudaMemcpyDeviceToHost, s->st));
+  // leave the system at the final state
+  CK(cudaMemcpyAsync(s->psi, A->ck_psi[n_ck], s->orb_bytes, cudaMemcpyDeviceToDevice, s->st));
+  copy_hist_in(s, A->ck_hist[n_ck]);
+  s->hist_len = A->ck_len[n_ck];
+  s->c_valid = 0;
+  electrons(s, 0);
+  CK(cudaStreamSynchronize(s->st));
+  for (int i = 0; i < 3 * na; ++i)
+    dL_dR[i] = gR_host[i] + gRd[i] - Fw[i] / h3;
+  *L_out = L;
+  r = launch_check("emd_propagate_adjoint");
+  if (r) return r;
+  return read_err_flag(s);
 }
 
 int emd_get_forces(emd_system *s, double *F) {
@@ -766,6 +1323,10 @@ void emd_destroy(emd_system *s) {
   if (s->st) cudaStreamSynchronize(s->st);
   else cudaDeviceSynchronize();
   for (void *p : s->allocs) cudaFree(p);
+  if (s->adj) {
+    for (void *p : s->adj->mem) cudaFree(p);
+    delete s->adj;
+  }
   for (auto &ev : s->prof_pending) {
     cudaEventDestroy(ev.first);
     cudaEventDestroy(ev.second);

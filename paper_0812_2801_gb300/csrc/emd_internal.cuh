@@ -8,6 +8,7 @@
 #define EMD_TILE 8              // edge of the tiles that carry atom candidates
 #define EMD_TILE_CAND_MAX 160   // (atom, image) candidates per tile
 #define EMD_MAX_HALF_ORDER 6    // fd_order / 2 <= 6
+#define EMD_SPLIT 16            // CTAs per atom for table building and local forces
 
 // error bits raised by kernels (device flag, read by emd_get_*)
 #define EMD_ERRBIT_PT   1       // per-point list overflow
@@ -36,7 +37,11 @@ struct TableSet {
   int *pt_cnt;      // [n3]
   int *pt_J;        // [EMD_PT_KMAX][n3]
   double *pt_p;     // [EMD_PT_KMAX][n3] p_J(r) summed over images
+  float *pt_pf;     // [EMD_PT_KMAX][n3] the same in FP32 (complex64 path)
+  int2 *pt4;        // [n3][4] first four (atom, FP32 p bits) per point, unused
+                    // slots (0, 0.0f); entry 0's atom carries count << 16
   int *at_cnt;      // [n_atoms]
+  int *split_cnt;   // [n_atoms][EMD_SPLIT] hits per range (table building)
   int *at_pt;       // [n_atoms][cap] flat grid index
   double *at_p;     // [n_atoms][cap] p value of that (point, image)
   double *at_d;     // [n_atoms][cap][3] displacement r - R_image
@@ -110,9 +115,11 @@ void emd_launch_wrap(const double *R, double *Rw, int n_atoms, double L,
                      cudaStream_t st);
 void emd_launch_tables(const GridInfo &g, const SpeciesDev &sp, int n_atoms,
                        TableSet &t, int *err, cudaStream_t st);
+// part: [n_atoms][EMD_SPLIT][3] scratch
 void emd_launch_local_force(const GridInfo &g, const SpeciesDev &sp,
                             int n_atoms, const double *Rw, const double *v_es_a,
-                            const double *v_es_b, double *F, cudaStream_t st);
+                            const double *v_es_b, double *part, double *F,
+                            cudaStream_t st);
 void emd_launch_short_range(const SpeciesDev &sp, int n_atoms, const double *R,
                             double L, double *F, double *e_part,
                             cudaStream_t st);
@@ -155,7 +162,7 @@ struct StageArgs {
   int apply_only;          // 1: u_out = H u_in (psi0 unused)
 };
 struct OrbLayout {
-  int n, n3, bo, n_blk, n_orb, n_orb_pad, prec, half_order;
+  int n, n3, bo, n_blk, n_orb, n_orb_pad, prec, half_order, n_atoms;
   double h;
   double w[EMD_MAX_HALF_ORDER + 1];   // w_0 = -3 c_0 / (2 h^2), w_k = -c_k/(2 h^2)
 };
@@ -178,3 +185,22 @@ void emd_launch_unpack(const OrbLayout &o, const void *u, double2 *canon,
                        int n_vec, cudaStream_t st);
 void emd_launch_abs2_sum(const double2 *c, int n, double *out,
                          cudaStream_t st);
+
+// adjoint.cu (FP64 orbitals)
+void emd_adj_axpy(double2 *y, const double2 *x, size_t n, cudaStream_t st);
+void emd_adj_gv(const OrbLayout &o, const double2 *mu, const double2 *u, double b,
+                double *g, cudaStream_t st);
+void emd_adj_project_grad(const OrbLayout &o, const TableSet &t, int n_atoms,
+                          const double2 *x, double h3, double h_kb,
+                          double inv_rc2, double2 *c, double2 *hc, double2 *dc,
+                          cudaStream_t st);
+void emd_adj_proj_sens(const double2 *cm, const double2 *dcm, const double2 *cu,
+                       const double2 *dcu, int n_atoms, int n_orb, int n_orb_pad,
+                       double coef, double *gR, cudaStream_t st);
+void emd_adj_rho(int n3, const double *rho, const double *lam_v, double *pois,
+                 cudaStream_t st);
+void emd_adj_scale_add(const OrbLayout &o, double2 *lam, const double2 *psi,
+                       const double *w, double scale, cudaStream_t st);
+void emd_adj_lincomb(int n, double *out, double a0, const double *x0, double a1,
+                     const double *x1, double a2, const double *x2, double a3,
+                     const double *x3, cudaStream_t st);

@@ -68,9 +68,10 @@ k_stage(const typename cplx<T>::type *__restrict__ u_in,
     const T w = W.w[k];
 #pragma unroll
     for (int j = 0; j < BO; ++j) {
-      T sx = 0, sy = 0;
+      const V v0 = ub[q[0] * BO + j];
+      T sx = v0.x, sy = v0.y;
 #pragma unroll
-      for (int e = 0; e < 6; ++e) {
+      for (int e = 1; e < 6; ++e) {
         const V v = ub[q[e] * BO + j];
         sx += v.x;
         sy += v.y;
@@ -114,8 +115,289 @@ k_stage(const typename cplx<T>::type *__restrict__ u_in,
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 Horner stage, 2.5-D: a CTA owns a tile of TX x TY points (all BO
+// orbitals of a block) and marches through a chunk of z-planes.  Each input
+// plane (tile + periodic halo of M points in x and y) is copied to shared
+// memory with cp.async, double-buffered.  Every arriving plane z' contributes
+//   - its x/y stencil part and v_eff u to output plane z',
+//   - w_k u(z') to output planes z' - k and z' + k (k = 1..M),
+// through a delay line of 2M+1 register accumulators per output point, so
+// only one plane is ever resident in shared memory.  Plane z' completes output
+// plane z' - M, which then gets the projector term and the Taylor update and
+// is stored.  Each thread owns one orbital column (x, j) and RY consecutive
+// rows, so y-neighbours come from a register window (RY + 2M loads for RY
+// outputs) and x-neighbours from shared memory (2M loads per output).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int BO, int M> struct ZTile {
+  static constexpr int NC = 64;                 // orbital columns = threads in x
+  static constexpr int TX = NC / BO;            // points per tile in x
+  static constexpr int NT = 512;                // threads per CTA
+  static constexpr int TYT = NT / NC;           // thread rows
+  static constexpr int RY = 2;                  // grid rows per thread
+  static constexpr int TY = TYT * RY;           // grid rows per tile
+  static constexpr int SW = TX + 2 * M;         // staged points per row
+  static constexpr int SH = TY + 2 * M;         // staged rows
+  static constexpr int PLANE = SH * SW * BO;    // float2 per staged u-plane
+  static constexpr int CH = BO / 2;             // 16-byte chunks per point
+  static constexpr int NCHUNK = SH * SW * CH;   // u chunks per plane
+  static constexpr int CPT = (NCHUNK + NT - 1) / NT;
+  static constexpr int NV = TX * TY;            // tile points
+  static constexpr int QPT = (2 * NV + NT - 1) / NT;        // pt4 chunks / thread
+  static constexpr int SPT = (NV * CH + NT - 1) / NT;       // psi0 chunks / thread
+  static constexpr int NS = 2 * M + 1;          // delay-line slots
+  static constexpr int NB = 3;                  // ring depth (prefetch 2)
+  // one ring slot: u-plane | v_eff | projector records | psi0 of the output plane
+  static constexpr int UB = PLANE * 8, VB = NV * 4, QB = NV * 32, SB = NV * BO * 8;
+  static constexpr int SLOT = UB + VB + QB + SB;
+  static constexpr size_t SMEM_FIXED = (size_t)NB * SLOT;
+};
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem)
+               : "memory");
+}
+
+// The complex arithmetic uses the packed FP32x2 operations of sm_10x
+// (__fadd2_rn, __ffma2_rn, __fmul2_rn): one instruction per complex add or
+// real-times-complex multiply-add.
+template <int BO, int M>
+__global__ void __launch_bounds__(512, 1)
+k_stage_z(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
+          float2 *__restrict__ u_out, const float *__restrict__ v_eff,
+          const int2 *__restrict__ pt4, const int *__restrict__ pt_J,
+          const float *__restrict__ pt_pf, const float2 *__restrict__ hc,
+          int n, int ntx, int zc, int n_orb_pad, int n_atoms, int hc_in_smem,
+          float a, int apply_only, Weights<float> W) {
+  typedef ZTile<BO, M> Z;
+  constexpr int RY = Z::RY;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2 *hcs = reinterpret_cast<float2 *>(smraw + Z::NB * Z::SLOT);
+  const int tid = threadIdx.x;
+  const int col = tid % Z::NC, tyr = tid / Z::NC;
+  const int xl = col / BO, j = col % BO;
+  const int tx0 = (blockIdx.x % ntx) * Z::TX, ty0 = (blockIdx.x / ntx) * Z::TY;
+  const int z0 = blockIdx.y * zc;
+  const int zcount = min(zc, n - z0);
+  const int total = zcount + 2 * M;
+  const int blk = blockIdx.z;
+  const int n2 = n * n;
+  const size_t n3 = (size_t)n2 * n;
+  const float2 *ub = u_in + (size_t)blk * n3 * BO;
+  const float2 *pb = psi0 + (size_t)blk * n3 * BO;
+  float2 *ob = u_out + (size_t)blk * n3 * BO;
+  const int x = tx0 + xl;
+
+  // staging offsets within a plane (the same for every plane)
+  int src_off[Z::CPT], dst_off[Z::CPT];
+#pragma unroll
+  for (int i = 0; i < Z::CPT; ++i) {
+    const int q = tid + i * Z::NT;
+    src_off[i] = -1;
+    dst_off[i] = 0;
+    if (q < Z::NCHUNK) {
+      const int hh = q % Z::CH, pnt = q / Z::CH;
+      const int c = pnt % Z::SW, rr = pnt / Z::SW;
+      const int xx = (tx0 - M + c + 2 * n) % n;
+      const int yy = (ty0 - M + rr + 2 * n) % n;
+      src_off[i] = (yy * n + xx) * BO + 2 * hh;
+      dst_off[i] = (rr * Z::SW + c) * BO + 2 * hh;
+    }
+  }
+  int v_src = -1;
+  if (tid < Z::NV) {
+    const int vx = tid % Z::TX, vy = tid / Z::TX;
+    v_src = ((ty0 + vy) % n) * n + (tx0 + vx) % n;
+  }
+  int q_src[Z::QPT], q_dst[Z::QPT];
+#pragma unroll
+  for (int i = 0; i < Z::QPT; ++i) {
+    const int q = tid + i * Z::NT;
+    q_src[i] = -1;
+    q_dst[i] = 0;
+    if (q < 2 * Z::NV) {
+      const int pnt = q >> 1, half = q & 1;
+      const int xx = min(tx0 + pnt % Z::TX, n - 1), yy = min(ty0 + pnt / Z::TX, n - 1);
+      q_src[i] = (yy * n + xx) * 4 + 2 * half;
+      q_dst[i] = pnt * 4 + 2 * half;
+    }
+  }
+  int s_src[Z::SPT], s_dst[Z::SPT];
+#pragma unroll
+  for (int i = 0; i < Z::SPT; ++i) {
+    const int q = tid + i * Z::NT;
+    s_src[i] = -1;
+    s_dst[i] = 0;
+    if (q < Z::NV * Z::CH) {
+      const int pnt = q / Z::CH, hh = q % Z::CH;
+      const int xx = min(tx0 + pnt % Z::TX, n - 1), yy = min(ty0 + pnt / Z::TX, n - 1);
+      s_src[i] = (yy * n + xx) * BO + 2 * hh;
+      s_dst[i] = pnt * BO + 2 * hh;
+    }
+  }
+  if (hc_in_smem) {
+    for (int i = tid; i < n_atoms * BO; i += Z::NT)
+      hcs[i] = hc[(size_t)(i / BO) * n_orb_pad + (size_t)blk * BO + i % BO];
+  }
+
+  auto issue = [&](int zi, int slot) {
+    unsigned char *base = smraw + slot * Z::SLOT;
+    float2 *U = reinterpret_cast<float2 *>(base);
+    float *V = reinterpret_cast<float *>(base + Z::UB);
+    int2 *Q = reinterpret_cast<int2 *>(base + Z::UB + Z::VB);
+    float2 *S = reinterpret_cast<float2 *>(base + Z::UB + Z::VB + Z::QB);
+    int zz = z0 - M + zi;
+    if (zz < 0) zz += n;
+    if (zz >= n) zz -= n;
+    const float2 *src = ub + (size_t)zz * n2 * BO;
+#pragma unroll
+    for (int i = 0; i < Z::CPT; ++i)
+      if (src_off[i] >= 0) cp_async16(U + dst_off[i], src + src_off[i]);
+    if (v_src >= 0) cp_async4(V + tid, v_eff + (size_t)zz * n2 + v_src);
+    if (zi >= 2 * M) {
+      const int zo = z0 + zi - 2 * M;
+      const int2 *qs = pt4 + (size_t)zo * n2 * 4;
+#pragma unroll
+      for (int i = 0; i < Z::QPT; ++i)
+        if (q_src[i] >= 0) cp_async16(Q + q_dst[i], qs + q_src[i]);
+      if (!apply_only) {
+        const float2 *ss = pb + (size_t)zo * n2 * BO;
+#pragma unroll
+        for (int i = 0; i < Z::SPT; ++i)
+          if (s_src[i] >= 0) cp_async16(S + s_dst[i], ss + s_src[i]);
+      }
+    }
+    cp_async_commit();
+  };
+
+  float2 w2[M + 1];
+#pragma unroll
+  for (int k = 0; k <= M; ++k) w2[k] = make_float2(W.w[k], W.w[k]);
+  const float2 a2 = make_float2(a, -a);
+
+  float2 acc[RY][Z::NS];
+#pragma unroll
+  for (int r = 0; r < RY; ++r)
+#pragma unroll
+    for (int q = 0; q < Z::NS; ++q) acc[r][q] = make_float2(0.f, 0.f);
+
+  issue(0, 0);
+  if (total > 1) issue(1, 1);
+  int sb = 0;   // ring slot of plane zi
+  for (int g = 0; g * Z::NS < total; ++g) {
+#pragma unroll
+    for (int ph = 0; ph < Z::NS; ++ph) {
+      const int zi = g * Z::NS + ph;
+      if (zi >= total) break;
+      if (zi + 2 < total) {
+        issue(zi + 2, sb == 0 ? 2 : sb - 1);
+        cp_async_wait<2>();
+      } else if (zi + 1 < total) {
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      const unsigned char *base = smraw + sb * Z::SLOT;
+      const float2 *P = reinterpret_cast<const float2 *>(base);
+      const float *VP = reinterpret_cast<const float *>(base + Z::UB);
+      float2 win[RY + 2 * M];
+#pragma unroll
+      for (int w = 0; w < RY + 2 * M; ++w)
+        win[w] = P[((tyr * RY + w) * Z::SW + xl + M) * BO + j];
+#pragma unroll
+      for (int r = 0; r < RY; ++r) {
+        const float2 c = win[r + M];
+        const float2 *row = P + ((tyr * RY + r + M) * Z::SW + xl + M) * BO + j;
+        float2 s2 = __fmul2_rn(w2[0], c);
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+          const float2 t = __fadd2_rn(__fadd2_rn(row[k * BO], row[-k * BO]),
+                                      __fadd2_rn(win[r + M + k], win[r + M - k]));
+          s2 = __ffma2_rn(w2[k], t, s2);
+        }
+        const float ve = VP[(tyr * RY + r) * Z::TX + xl];
+        s2 = __ffma2_rn(make_float2(ve, ve), c, s2);
+        acc[r][ph] = __fadd2_rn(acc[r][ph], s2);
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+          acc[r][(ph + k) % Z::NS] = __ffma2_rn(w2[k], c, acc[r][(ph + k) % Z::NS]);
+          if (g > 0 || ph - k >= 0)
+            acc[r][(ph - k + Z::NS) % Z::NS] =
+                __ffma2_rn(w2[k], c, acc[r][(ph - k + Z::NS) % Z::NS]);
+        }
+      }
+      if (zi >= M) {
+        const int slot = (ph - M + Z::NS) % Z::NS;
+        if (zi >= 2 * M) {
+          const int zo = z0 + zi - 2 * M;
+          const int4 *Q4 = reinterpret_cast<const int4 *>(base + Z::UB + Z::VB);
+          const float2 *S = reinterpret_cast<const float2 *>(base + Z::UB + Z::VB + Z::QB);
+#pragma unroll
+          for (int r = 0; r < RY; ++r) {
+            const int vy = tyr * RY + r, y = ty0 + vy;
+            if (x < n && y < n) {
+              const int pnt = vy * Z::TX + xl;
+              const int4 q01 = Q4[2 * pnt], q23 = Q4[2 * pnt + 1];
+              const int cnt = q01.x >> 16;
+              const int J[4] = {q01.x & 0xffff, q01.z, q23.x, q23.z};
+              const float pv[4] = {__int_as_float(q01.y), __int_as_float(q01.w),
+                                   __int_as_float(q23.y), __int_as_float(q23.w)};
+              float2 hv = acc[r][slot];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float2 hcv = hc_in_smem
+                    ? hcs[J[e] * BO + j]
+                    : __ldg(hc + (size_t)J[e] * n_orb_pad + (size_t)blk * BO + j);
+                hv = __ffma2_rn(make_float2(pv[e], pv[e]), hcv, hv);
+              }
+              const size_t p = (size_t)zo * n2 + (size_t)y * n + x;
+              for (int e = 4; e < cnt; ++e) {
+                const int Je = __ldg(pt_J + (size_t)e * n3 + p);
+                const float pe = __ldg(pt_pf + (size_t)e * n3 + p);
+                const float2 hcv = hc_in_smem
+                    ? hcs[Je * BO + j]
+                    : __ldg(hc + (size_t)Je * n_orb_pad + (size_t)blk * BO + j);
+                hv = __ffma2_rn(make_float2(pe, pe), hcv, hv);
+              }
+              float2 out = hv;
+              if (!apply_only)
+                out = __ffma2_rn(a2, make_float2(hv.y, hv.x), S[pnt * BO + j]);
+              ob[p * BO + j] = out;
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+#pragma unroll
+          for (int q = 0; q < Z::NS; ++q)
+            if (q == slot) acc[r][q] = make_float2(0.f, 0.f);
+        }
+      }
+      __syncthreads();
+      sb = sb == 2 ? 0 : sb + 1;
+    }
+  }
+}
+
 // c[J][A] = h^3 sum_e p_e u_A(pt_e) over atom J's (point, image) entries;
 // hc = h_kb c in orbital precision.  One block per (atom, orbital block).
+// Each thread accumulates its strided share of the entries in T (FP32 for
+// complex64 orbitals: GB300's FP64 rate is 1/64 of FP32), the block sum
+// across threads is FP64 in a fixed tree order.
 template <typename T, int BO>
 __global__ void __launch_bounds__(256)
 k_project(const typename cplx<T>::type *__restrict__ u, size_t n3,
@@ -127,20 +409,23 @@ k_project(const typename cplx<T>::type *__restrict__ u, size_t n3,
   const int J = blockIdx.x, blk = blockIdx.y;
   const int cnt = at_cnt[J];
   const V *ub = u + (size_t)blk * n3 * BO;
-  double acc[2 * BO];
+  T tacc[2 * BO];
 #pragma unroll
-  for (int k = 0; k < 2 * BO; ++k) acc[k] = 0.0;
+  for (int k = 0; k < 2 * BO; ++k) tacc[k] = 0;
   for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
     const size_t idx = (size_t)J * cap + e;
     const int pt = at_pt[idx];
-    const double pv = at_p[idx];
+    const T pv = (T)at_p[idx];
 #pragma unroll
     for (int j = 0; j < BO; ++j) {
       const V v = ub[(size_t)pt * BO + j];
-      acc[2 * j] += pv * (double)v.x;
-      acc[2 * j + 1] += pv * (double)v.y;
+      tacc[2 * j] += pv * v.x;
+      tacc[2 * j + 1] += pv * v.y;
     }
   }
+  double acc[2 * BO];
+#pragma unroll
+  for (int k = 0; k < 2 * BO; ++k) acc[k] = (double)tacc[k];
   emd_block_sum<2 * BO>(acc, red);
   if (threadIdx.x == 0) {
 #pragma unroll
@@ -231,26 +516,29 @@ k_nl_force(const typename cplx<T>::type *__restrict__ u, size_t n3, int n_blk,
   const int J = blockIdx.x, blk = blockIdx.y;
   const int cnt = at_cnt[J];
   const V *ub = u + (size_t)blk * n3 * BO;
-  double acc[6 * BO];
+  T tacc[6 * BO];
 #pragma unroll
-  for (int k = 0; k < 6 * BO; ++k) acc[k] = 0.0;
+  for (int k = 0; k < 6 * BO; ++k) tacc[k] = 0;
   for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
     const size_t idx = (size_t)J * cap + e;
     const int pt = at_pt[idx];
-    const double pv = at_p[idx] * inv_rc2;
-    const double d0 = at_d[3 * idx], d1 = at_d[3 * idx + 1], d2 = at_d[3 * idx + 2];
+    const T pv = (T)(at_p[idx] * inv_rc2);
+    const T d0 = (T)at_d[3 * idx], d1 = (T)at_d[3 * idx + 1], d2 = (T)at_d[3 * idx + 2];
 #pragma unroll
     for (int j = 0; j < BO; ++j) {
       const V v = ub[(size_t)pt * BO + j];
-      const double wr = pv * (double)v.x, wi = pv * (double)v.y;
-      acc[6 * j + 0] += wr * d0;
-      acc[6 * j + 1] += wi * d0;
-      acc[6 * j + 2] += wr * d1;
-      acc[6 * j + 3] += wi * d1;
-      acc[6 * j + 4] += wr * d2;
-      acc[6 * j + 5] += wi * d2;
+      const T wr = pv * v.x, wi = pv * v.y;
+      tacc[6 * j + 0] += wr * d0;
+      tacc[6 * j + 1] += wi * d0;
+      tacc[6 * j + 2] += wr * d1;
+      tacc[6 * j + 3] += wi * d1;
+      tacc[6 * j + 4] += wr * d2;
+      tacc[6 * j + 5] += wi * d2;
     }
   }
+  double acc[6 * BO];
+#pragma unroll
+  for (int k = 0; k < 6 * BO; ++k) acc[k] = (double)tacc[k];
   emd_block_sum<6 * BO>(acc, red);
   if (threadIdx.x == 0) {
     double f[3] = {0.0, 0.0, 0.0};
@@ -335,6 +623,39 @@ void stage_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
       (const V *)a.u_in, (const V *)a.psi0, (V *)a.u_out, (const T *)a.v_eff,
       a.tab->pt_cnt, a.tab->pt_J, a.tab->pt_p, (const V *)a.hc, o.n, ntx,
       o.n_orb_pad, (T)a.a, a.apply_only, weights_of<T>(o));
+}
+
+template <int BO, int M>
+void stage_z_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
+  typedef ZTile<BO, M> Z;
+  const int hc_bytes = o.n_atoms * BO * (int)sizeof(float2);
+  const int hc_in_smem = hc_bytes <= 16384;
+  const size_t smem = Z::SMEM_FIXED + (hc_in_smem ? hc_bytes : 0);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_stage_z<BO, M>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(Z::SMEM_FIXED + 16384));
+    attr_done = true;
+  }
+  const int ntx = (o.n + Z::TX - 1) / Z::TX, nty = (o.n + Z::TY - 1) / Z::TY;
+  const int zc = o.n <= 64 ? o.n : (o.n + 1) / 2 <= 64 ? (o.n + 1) / 2 : 48;
+  dim3 grid(ntx * nty, (o.n + zc - 1) / zc, o.n_blk);
+  k_stage_z<BO, M><<<grid, Z::NT, smem, st>>>(
+      (const float2 *)a.u_in, (const float2 *)a.psi0, (float2 *)a.u_out,
+      (const float *)a.v_eff, a.tab->pt4, a.tab->pt_J, a.tab->pt_pf,
+      (const float2 *)a.hc, o.n, ntx, zc, o.n_orb_pad, o.n_atoms, hc_in_smem,
+      (float)a.a, a.apply_only, weights_of<float>(o));
+}
+
+template <int BO>
+void stage_z_m(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
+  switch (o.half_order) {
+    case 1: stage_z_t<BO, 1>(o, a, st); break;
+    case 2: stage_z_t<BO, 2>(o, a, st); break;
+    case 3: stage_z_t<BO, 3>(o, a, st); break;
+    case 4: stage_z_t<BO, 4>(o, a, st); break;
+  }
 }
 
 template <typename T, int BO>
@@ -436,8 +757,8 @@ void emd_launch_stage(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
   } else {
     switch (o.bo) {
       case 1: stage_m<float, 1>(o, a, st); break;
-      case 2: stage_m<float, 2>(o, a, st); break;
-      case 4: stage_m<float, 4>(o, a, st); break;
+      case 2: stage_z_m<2>(o, a, st); break;
+      case 4: stage_z_m<4>(o, a, st); break;
     }
   }
 }

@@ -17,6 +17,7 @@
 // (radix 4, 2, 3, 5 and a direct DFT for other small primes) with twiddles
 // precomputed once per grid size.
 #include <cmath>
+#include <mutex>
 #include <vector>
 #include "emd_internal.cuh"
 
@@ -287,29 +288,39 @@ k_sum(const double *part, int n, double *out) {
   if (threadIdx.x == 0) *out = acc[0];
 }
 
+// FFT plans with their device twiddle tables, one per (device, grid size),
+// created on first use and kept for the life of the process.
 struct PlanCache {
-  int n = -1;
+  int dev = -1, n = -1;
   FftPlan plan;
   double2 *tab = nullptr;
 };
-PlanCache g_cache[4];
+std::mutex g_plan_mu;
+std::vector<PlanCache *> g_plans;
 
 const PlanCache *get_plan(int n) {
-  for (auto &c : g_cache)
-    if (c.n == n) return &c;
-  for (auto &c : g_cache) {
-    if (c.n == -1) {
-      std::vector<double2> tab;
-      if (!make_plan(n, c.plan, tab)) return nullptr;
-      if (cudaMalloc(&c.tab, tab.size() * sizeof(double2)) != cudaSuccess)
-        return nullptr;
-      cudaMemcpy(c.tab, tab.data(), tab.size() * sizeof(double2),
-                 cudaMemcpyHostToDevice);
-      c.n = n;
-      return &c;
-    }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  for (PlanCache *c : g_plans)
+    if (c->n == n && c->dev == dev) return c;
+  PlanCache *c = new PlanCache();
+  std::vector<double2> tab;
+  if (!make_plan(n, c->plan, tab) ||
+      cudaMalloc(&c->tab, tab.size() * sizeof(double2)) != cudaSuccess) {
+    delete c;
+    return nullptr;
   }
-  return nullptr;
+  if (cudaMemcpy(c->tab, tab.data(), tab.size() * sizeof(double2),
+                 cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(c->tab);
+    delete c;
+    return nullptr;
+  }
+  c->n = n;
+  c->dev = dev;
+  g_plans.push_back(c);
+  return c;
 }
 
 }  // namespace

@@ -19,13 +19,15 @@ __global__ void k_wrap(const double *R, double *Rw, int n, double L) {
 
 // Conservative (atom, image) candidates per tile of EMD_TILE^3 points: every
 // pair whose support sphere can reach a point of the tile.  The exact
-// per-point decision is taken later in FP64.
-__global__ void k_tile_candidates(int n, double h, double L, const double *Rw,
-                                  int n_atoms, float r_max, int *tile_cnt,
-                                  int *tile_ent, int *err) {
+// per-point decision is taken later in FP64.  One block per tile; pairs are
+// scanned in (J, image) order and compacted in that order.
+__global__ void __launch_bounds__(256)
+k_tile_candidates(int n, double h, double L, const double *Rw, int n_atoms,
+                  float r_max, int *tile_cnt, int *tile_ent, int *err) {
+  __shared__ int warp_tot[8];
+  __shared__ int s_base;
   const int nt = (n + EMD_TILE - 1) / EMD_TILE;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nt * nt * nt) return;
+  const int t = blockIdx.x;
   const int tx = t % nt, ty = (t / nt) % nt, tz = t / (nt * nt);
   const float lo[3] = {(float)(tx * EMD_TILE * h), (float)(ty * EMD_TILE * h),
                        (float)(tz * EMD_TILE * h)};
@@ -33,28 +35,45 @@ __global__ void k_tile_candidates(int n, double h, double L, const double *Rw,
                        (float)(min(ty * EMD_TILE + EMD_TILE - 1, n - 1) * h),
                        (float)(min(tz * EMD_TILE + EMD_TILE - 1, n - 1) * h)};
   const float rr = (r_max + 0.05f) * (r_max + 0.05f);
-  int cnt = 0;
-  for (int J = 0; J < n_atoms; ++J) {
-    for (int img = 0; img < 27; ++img) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_base = 0;
+  __syncthreads();
+  const int total = n_atoms * 27;
+  for (int b0 = 0; b0 < total; b0 += blockDim.x) {
+    const int q = b0 + threadIdx.x;
+    bool hit = false;
+    if (q < total) {
+      const int J = q / 27, img = q % 27;
       const int ni[3] = {img % 3 - 1, (img / 3) % 3 - 1, img / 9 - 1};
       float d2 = 0.f;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        float c = (float)Rw[3 * J + a] + (float)(ni[a] * L);
-        float d = fmaxf(fmaxf(lo[a] - c, c - hi[a]), 0.f);
+        const float c = (float)Rw[3 * J + a] + (float)(ni[a] * L);
+        const float d = fmaxf(fmaxf(lo[a] - c, c - hi[a]), 0.f);
         d2 += d * d;
       }
-      if (d2 < rr) {
-        if (cnt < EMD_TILE_CAND_MAX) {
-          tile_ent[t * EMD_TILE_CAND_MAX + cnt] = J * 27 + img;
-          ++cnt;
-        } else {
-          atomicOr(err, EMD_ERRBIT_TILE);
-        }
-      }
+      hit = d2 < rr;
     }
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) warp_tot[warp] = __popc(m);
+    __syncthreads();
+    int off = s_base, tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      if (w < warp) off += warp_tot[w];
+      tot += warp_tot[w];
+    }
+    if (hit) {
+      const int e = off + __popc(m & ((1u << lane) - 1u));
+      if (e < EMD_TILE_CAND_MAX)
+        tile_ent[t * EMD_TILE_CAND_MAX + e] = q;   // q = J * 27 + image
+      else
+        atomicOr(err, EMD_ERRBIT_TILE);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_base += tot;
+    __syncthreads();
   }
-  tile_cnt[t] = cnt;
+  if (threadIdx.x == 0) tile_cnt[t] = min(s_base, EMD_TILE_CAND_MAX);
 }
 
 // Point-major table: for each grid point the atoms whose projector reaches it
@@ -63,7 +82,8 @@ __global__ void k_tile_candidates(int n, double h, double L, const double *Rw,
 __global__ void __launch_bounds__(512)
 k_point_table(int n, int n3, double h, double L, const double *Rw,
               SpeciesDev sp, const int *tile_cnt, const int *tile_ent,
-              int *pt_cnt, int *pt_J, double *pt_p, double *g_ion, int *err) {
+              int *pt_cnt, int *pt_J, double *pt_p, float *pt_pf, int2 *pt4,
+              double *g_ion, int *err) {
   __shared__ int cand[EMD_TILE_CAND_MAX];
   const int nt = (n + EMD_TILE - 1) / EMD_TILE;
   const int t = blockIdx.x;
@@ -90,6 +110,7 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
         if (cnt < EMD_PT_KMAX) {
           pt_J[cnt * n3 + p] = curJ;
           pt_p[cnt * n3 + p] = psum;
+          pt_pf[cnt * n3 + p] = (float)psum;
           ++cnt;
         } else {
           atomicOr(err, EMD_ERRBIT_PT);
@@ -113,6 +134,7 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
     if (cnt < EMD_PT_KMAX) {
       pt_J[cnt * n3 + p] = curJ;
       pt_p[cnt * n3 + p] = psum;
+      pt_pf[cnt * n3 + p] = (float)psum;
       ++cnt;
     } else {
       atomicOr(err, EMD_ERRBIT_PT);
@@ -120,6 +142,12 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
   }
   pt_cnt[p] = cnt;
   g_ion[p] = gsum;
+  for (int e = 0; e < 4; ++e) {
+    int2 q = make_int2(0, 0);
+    if (e < cnt) q = make_int2(pt_J[e * n3 + p], __float_as_int(pt_pf[e * n3 + p]));
+    if (e == 0) q.x |= cnt << 16;
+    pt4[(size_t)p * 4 + e] = q;
+  }
 }
 
 // Index box of the grid points an image sphere can reach along one axis.
@@ -131,158 +159,203 @@ __device__ __forceinline__ void axis_range(double c, int nimg, double L,
   hi = min(n - 1, (int)ceil((cc + r) / h) + 1);
 }
 
+// Boxes of the 27 images of atom J's support sphere, flattened in image
+// order then box order (x fastest): the enumeration order of the atom table.
+struct ImageBoxes {
+  int lo[27][3], ext[27][3], start[28];
+};
+__device__ void image_boxes(const double *c, double L, double h, double r,
+                            int n, ImageBoxes &B) {
+  int acc = 0;
+  for (int img = 0; img < 27; ++img) {
+    const int ni[3] = {img % 3 - 1, (img / 3) % 3 - 1, img / 9 - 1};
+    int nb = 1;
+    for (int a = 0; a < 3; ++a) {
+      int lo, hi;
+      axis_range(c[a], ni[a], L, h, r, n, lo, hi);
+      B.lo[img][a] = lo;
+      B.ext[img][a] = hi >= lo ? hi - lo + 1 : 0;
+      nb *= B.ext[img][a];
+    }
+    B.start[img] = acc;
+    acc += nb;
+  }
+  B.start[27] = acc;
+}
+
 // Atom-major projector table: every (point, image) pair within r_proj of atom
 // J, in image order then box order (deterministic), with p and d = r - R_img.
+// Grid (atom, split): the flattened box space of the atom is cut into
+// `nsplit` contiguous ranges.  Pass 0 counts the hits of each range; pass 1
+// writes them at the offset given by the counts of the earlier ranges.
 __global__ void __launch_bounds__(256)
-k_atom_table(int n, double h, double L, const double *Rw, SpeciesDev sp,
-             int cap, int *at_cnt, int *at_pt, double *at_p, double *at_d,
-             int *err) {
+k_atom_table(int pass, int n, double h, double L, const double *Rw,
+             SpeciesDev sp, int cap, int *split_cnt, int *at_cnt, int *at_pt,
+             double *at_p, double *at_d, int *err) {
+  __shared__ ImageBoxes B;
   __shared__ int warp_tot[8];
   __shared__ int s_base;
-  const int J = blockIdx.x;
+  const int J = blockIdx.x, split = blockIdx.y, nsplit = gridDim.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double c[3] = {Rw[3 * J], Rw[3 * J + 1], Rw[3 * J + 2]};
   const double rp2 = __dmul_rn(sp.r_proj, sp.r_proj);
-  if (threadIdx.x == 0) s_base = 0;
-  __syncthreads();
-  for (int img = 0; img < 27; ++img) {
-    const int ni[3] = {img % 3 - 1, (img / 3) % 3 - 1, img / 9 - 1};
-    int lo[3], hi[3];
-    bool empty = false;
-    for (int a = 0; a < 3; ++a) {
-      axis_range(c[a], ni[a], L, h, sp.r_proj, n, lo[a], hi[a]);
-      if (lo[a] > hi[a]) empty = true;
-    }
-    if (empty) continue;
-    const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1,
-              ez = hi[2] - lo[2] + 1;
-    const int nbox = ex * ey * ez;
-    for (int b0 = 0; b0 < nbox; b0 += blockDim.x) {
-      const int k = b0 + threadIdx.x;
-      bool flag = false;
-      double dx = 0, dy = 0, dz = 0, d2 = 0;
-      int pidx = 0;
-      if (k < nbox) {
-        const int ix = lo[0] + k % ex, iy = lo[1] + (k / ex) % ey,
-                  iz = lo[2] + k / (ex * ey);
-        dx = emd_disp(ix, h, c[0], ni[0], L);
-        dy = emd_disp(iy, h, c[1], ni[1], L);
-        dz = emd_disp(iz, h, c[2], ni[2], L);
-        d2 = emd_norm2(dx, dy, dz);
-        flag = d2 < rp2;
-        pidx = (iz * n + iy) * n + ix;
-      }
-      const unsigned m = __ballot_sync(0xffffffffu, flag);
-      const int pre = __popc(m & ((1u << lane) - 1u));
-      if (lane == 0) warp_tot[warp] = __popc(m);
-      __syncthreads();
-      int off = s_base, tot = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        if (w < warp) off += warp_tot[w];
-        tot += warp_tot[w];
-      }
-      if (flag) {
-        const int e = off + pre;
-        if (e < cap) {
-          at_pt[(size_t)J * cap + e] = pidx;
-          at_p[(size_t)J * cap + e] = sp.c_p * exp(-d2 * sp.inv_2rc2);
-          double *dd = at_d + 3 * ((size_t)J * cap + e);
-          dd[0] = dx;
-          dd[1] = dy;
-          dd[2] = dz;
-        } else {
-          atomicOr(err, EMD_ERRBIT_AT);
-        }
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) s_base += tot;
-      __syncthreads();
-    }
+  if (threadIdx.x == 0) {
+    image_boxes(c, L, h, sp.r_proj, n, B);
+    int base = 0;
+    if (pass == 1)
+      for (int s2 = 0; s2 < split; ++s2) base += split_cnt[J * nsplit + s2];
+    s_base = base;
   }
-  if (threadIdx.x == 0) at_cnt[J] = min(s_base, cap);
+  __syncthreads();
+  const int total = B.start[27];
+  const int per = (total + nsplit - 1) / nsplit;
+  const int f0 = split * per, f1 = min(total, f0 + per);
+  int img = 0;
+  for (int b0 = f0; b0 < f1; b0 += blockDim.x) {
+    const int f = b0 + threadIdx.x;
+    bool flag = false;
+    double dx = 0, dy = 0, dz = 0, d2 = 0;
+    int pidx = 0;
+    if (f < f1) {
+      while (img < 26 && f >= B.start[img + 1]) ++img;
+      const int k = f - B.start[img];
+      const int ex = B.ext[img][0], ey = B.ext[img][1];
+      const int ix = B.lo[img][0] + k % ex, iy = B.lo[img][1] + (k / ex) % ey,
+                iz = B.lo[img][2] + k / (ex * ey);
+      const int ni[3] = {img % 3 - 1, (img / 3) % 3 - 1, img / 9 - 1};
+      dx = emd_disp(ix, h, c[0], ni[0], L);
+      dy = emd_disp(iy, h, c[1], ni[1], L);
+      dz = emd_disp(iz, h, c[2], ni[2], L);
+      d2 = emd_norm2(dx, dy, dz);
+      flag = d2 < rp2;
+      pidx = (iz * n + iy) * n + ix;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    if (lane == 0) warp_tot[warp] = __popc(m);
+    __syncthreads();
+    int off = s_base, tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      if (w < warp) off += warp_tot[w];
+      tot += warp_tot[w];
+    }
+    if (pass == 1 && flag) {
+      const int e = off + __popc(m & ((1u << lane) - 1u));
+      if (e < cap) {
+        at_pt[(size_t)J * cap + e] = pidx;
+        at_p[(size_t)J * cap + e] = sp.c_p * exp(-d2 * sp.inv_2rc2);
+        double *dd = at_d + 3 * ((size_t)J * cap + e);
+        dd[0] = dx;
+        dd[1] = dy;
+        dd[2] = dz;
+      } else {
+        atomicOr(err, EMD_ERRBIT_AT);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_base += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (pass == 0) split_cnt[J * nsplit + split] = s_base;
+    else if (split == nsplit - 1) at_cnt[J] = min(s_base, cap);
+  }
 }
 
 // F_J^loc = h^3 sum_r v_es(r) g_J(d) 2 d / a^2 over the Gaussian support
-// (-dE_es/dR_J of 1/2 h^3 sum n_tot v_es, n_tot = rho - sum g).
+// (-dE_es/dR_J of 1/2 h^3 sum n_tot v_es, n_tot = rho - sum g).  Grid
+// (atom, split) over contiguous ranges of the flattened box space; partials
+// are summed in split order by k_local_force_sum.
 __global__ void __launch_bounds__(256)
 k_local_force(int n, double h, double L, const double *Rw, SpeciesDev sp,
-              const double *va, const double *vb, double *F) {
+              const double *va, const double *vb, double *part) {
+  __shared__ ImageBoxes B;
   __shared__ double red[8 * 3];
-  const int J = blockIdx.x;
+  const int J = blockIdx.x, split = blockIdx.y, nsplit = gridDim.y;
   const double c[3] = {Rw[3 * J], Rw[3 * J + 1], Rw[3 * J + 2]};
   const double rl2 = __dmul_rn(sp.r_loc, sp.r_loc);
+  if (threadIdx.x == 0) image_boxes(c, L, h, sp.r_loc, n, B);
+  __syncthreads();
+  const int total = B.start[27];
+  const int per = (total + nsplit - 1) / nsplit;
+  const int f0 = split * per, f1 = min(total, f0 + per);
   double acc[3] = {0.0, 0.0, 0.0};
-  for (int img = 0; img < 27; ++img) {
+  int img = 0;
+  for (int f = f0 + threadIdx.x; f < f1; f += blockDim.x) {
+    while (img < 26 && f >= B.start[img + 1]) ++img;
+    const int k = f - B.start[img];
+    const int ex = B.ext[img][0], ey = B.ext[img][1];
+    const int ix = B.lo[img][0] + k % ex, iy = B.lo[img][1] + (k / ex) % ey,
+              iz = B.lo[img][2] + k / (ex * ey);
     const int ni[3] = {img % 3 - 1, (img / 3) % 3 - 1, img / 9 - 1};
-    int lo[3], hi[3];
-    bool empty = false;
-    for (int a = 0; a < 3; ++a) {
-      axis_range(c[a], ni[a], L, h, sp.r_loc, n, lo[a], hi[a]);
-      if (lo[a] > hi[a]) empty = true;
-    }
-    if (empty) continue;
-    const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1,
-              ez = hi[2] - lo[2] + 1;
-    const int nbox = ex * ey * ez;
-    for (int k = threadIdx.x; k < nbox; k += blockDim.x) {
-      const int ix = lo[0] + k % ex, iy = lo[1] + (k / ex) % ey,
-                iz = lo[2] + k / (ex * ey);
-      const double dx = emd_disp(ix, h, c[0], ni[0], L);
-      const double dy = emd_disp(iy, h, c[1], ni[1], L);
-      const double dz = emd_disp(iz, h, c[2], ni[2], L);
-      const double d2 = emd_norm2(dx, dy, dz);
-      if (d2 < rl2) {
-        const int p = (iz * n + iy) * n + ix;
-        const double g = sp.c_g * exp(-d2 * sp.inv_a2);
-        const double w = (va[p] + vb[p]) * g * (2.0 * sp.inv_a2);
-        acc[0] += w * dx;
-        acc[1] += w * dy;
-        acc[2] += w * dz;
-      }
+    const double dx = emd_disp(ix, h, c[0], ni[0], L);
+    const double dy = emd_disp(iy, h, c[1], ni[1], L);
+    const double dz = emd_disp(iz, h, c[2], ni[2], L);
+    const double d2 = emd_norm2(dx, dy, dz);
+    if (d2 < rl2) {
+      const int p = (iz * n + iy) * n + ix;
+      const double g = sp.c_g * exp(-d2 * sp.inv_a2);
+      const double w = (va[p] + vb[p]) * g * (2.0 * sp.inv_a2);
+      acc[0] += w * dx;
+      acc[1] += w * dy;
+      acc[2] += w * dz;
     }
   }
   emd_block_sum<3>(acc, red);
   if (threadIdx.x == 0) {
     const double h3 = h * h * h;
-    F[3 * J + 0] = h3 * acc[0];
-    F[3 * J + 1] = h3 * acc[1];
-    F[3 * J + 2] = h3 * acc[2];
+    for (int a = 0; a < 3; ++a) part[((size_t)J * nsplit + split) * 3 + a] = h3 * acc[a];
   }
 }
 
+__global__ void k_local_force_sum(const double *part, int n_atoms, int nsplit,
+                                  double *F) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * n_atoms) return;
+  const int J = i / 3, a = i % 3;
+  double s = 0.0;
+  for (int k = 0; k < nsplit; ++k) s += part[((size_t)J * nsplit + k) * 3 + a];
+  F[i] = s;
+}
+
 // Short-range ion-ion term E_sr = 1/2 sum' Z^2 erfc(d/s)/d (s = sqrt2 a, d <
-// 12 bohr, all images) and its force.  One thread per atom.
-__global__ void k_short_range(SpeciesDev sp, int n_atoms, const double *Rw,
-                              double L, int nmax, double *F, double *e_part) {
-  const int J = blockIdx.x * blockDim.x + threadIdx.x;
-  if (J >= n_atoms) return;
+// 12 bohr, all images) and its force.  One block per atom J, threads over
+// (atom K, image) pairs, fixed-order block sum.
+__global__ void __launch_bounds__(256)
+k_short_range(SpeciesDev sp, int n_atoms, const double *Rw, double L, int nmax,
+              double *F, double *e_part) {
+  __shared__ double red[8 * 4];
+  const int J = blockIdx.x;
   const double s = sqrt(2.0) * sp.a_loc;
   const double zz = sp.z * sp.z;
   const double rcut = 12.0;
   const double k2 = 2.0 / (s * sqrt(M_PI));
-  double e = 0.0, f[3] = {0.0, 0.0, 0.0};
-  for (int K = 0; K < n_atoms; ++K) {
-    for (int nz = -nmax; nz <= nmax; ++nz)
-      for (int ny = -nmax; ny <= nmax; ++ny)
-        for (int nx = -nmax; nx <= nmax; ++nx) {
-          if (K == J && nx == 0 && ny == 0 && nz == 0) continue;
-          const double dv0 = Rw[3 * J] - Rw[3 * K] - nx * L;
-          const double dv1 = Rw[3 * J + 1] - Rw[3 * K + 1] - ny * L;
-          const double dv2 = Rw[3 * J + 2] - Rw[3 * K + 2] - nz * L;
-          const double d = sqrt(dv0 * dv0 + dv1 * dv1 + dv2 * dv2);
-          if (d >= rcut || d <= 0.0) continue;
-          const double ef = erfc(d / s) / d;
-          e += ef;
-          const double fm = zz * (ef / d + k2 * exp(-d * d / (s * s)) / d) / d;
-          f[0] += fm * dv0;
-          f[1] += fm * dv1;
-          f[2] += fm * dv2;
-        }
+  const int side = 2 * nmax + 1, nimg = side * side * side;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int q = threadIdx.x; q < n_atoms * nimg; q += blockDim.x) {
+    const int K = q / nimg, im = q % nimg;
+    const int nx = im % side - nmax, ny = (im / side) % side - nmax,
+              nz = im / (side * side) - nmax;
+    if (K == J && nx == 0 && ny == 0 && nz == 0) continue;
+    const double dv0 = Rw[3 * J] - Rw[3 * K] - nx * L;
+    const double dv1 = Rw[3 * J + 1] - Rw[3 * K + 1] - ny * L;
+    const double dv2 = Rw[3 * J + 2] - Rw[3 * K + 2] - nz * L;
+    const double d2 = dv0 * dv0 + dv1 * dv1 + dv2 * dv2;
+    if (d2 >= rcut * rcut || d2 <= 0.0) continue;
+    const double d = sqrt(d2);
+    const double ef = erfc(d / s) / d;
+    acc[0] += ef;
+    const double fm = zz * (ef / d + k2 * exp(-d2 / (s * s)) / d) / d;
+    acc[1] += fm * dv0;
+    acc[2] += fm * dv1;
+    acc[3] += fm * dv2;
   }
-  e_part[J] = 0.5 * zz * e;
-  F[3 * J] = f[0];
-  F[3 * J + 1] = f[1];
-  F[3 * J + 2] = f[2];
+  emd_block_sum<4>(acc, red);
+  if (threadIdx.x == 0) {
+    e_part[J] = 0.5 * zz * acc[0];
+    F[3 * J] = acc[1];
+    F[3 * J + 1] = acc[2];
+    F[3 * J + 2] = acc[3];
+  }
 }
 
 // R(t+dt) = R + V dt + F dt^2 / (2M), in the reference's rounding order.
@@ -319,28 +392,38 @@ void emd_launch_wrap(const double *R, double *Rw, int n_atoms, double L,
 
 void emd_launch_tables(const GridInfo &g, const SpeciesDev &sp, int n_atoms,
                        TableSet &t, int *err, cudaStream_t st) {
-  emd_note_launches(2 + (n_atoms > 0));
+  emd_note_launches(2 + 2 * (n_atoms > 0));
   const int nt = (g.n + EMD_TILE - 1) / EMD_TILE;
   const int ntiles = nt * nt * nt;
   const float rmax = (float)fmax(sp.r_proj, sp.r_loc);
-  k_tile_candidates<<<(ntiles + 127) / 128, 128, 0, st>>>(
+  k_tile_candidates<<<ntiles, 256, 0, st>>>(
       g.n, g.h, g.L, t.Rw, n_atoms, rmax, t.tile_cnt, t.tile_ent, err);
   k_point_table<<<ntiles, 512, 0, st>>>(g.n, g.n3, g.h, g.L, t.Rw, sp,
                                         t.tile_cnt, t.tile_ent, t.pt_cnt,
-                                        t.pt_J, t.pt_p, t.g_ion, err);
-  if (n_atoms > 0)
-    k_atom_table<<<n_atoms, 256, 0, st>>>(g.n, g.h, g.L, t.Rw, sp, t.cap,
-                                          t.at_cnt, t.at_pt, t.at_p, t.at_d,
-                                          err);
+                                        t.pt_J, t.pt_p, t.pt_pf, t.pt4, t.g_ion,
+                                        err);
+  if (n_atoms > 0) {
+    dim3 grid(n_atoms, EMD_SPLIT);
+    k_atom_table<<<grid, 256, 0, st>>>(0, g.n, g.h, g.L, t.Rw, sp, t.cap,
+                                       t.split_cnt, t.at_cnt, t.at_pt, t.at_p,
+                                       t.at_d, err);
+    k_atom_table<<<grid, 256, 0, st>>>(1, g.n, g.h, g.L, t.Rw, sp, t.cap,
+                                       t.split_cnt, t.at_cnt, t.at_pt, t.at_p,
+                                       t.at_d, err);
+  }
 }
 
 void emd_launch_local_force(const GridInfo &g, const SpeciesDev &sp,
                             int n_atoms, const double *Rw, const double *v_es_a,
-                            const double *v_es_b, double *F, cudaStream_t st) {
+                            const double *v_es_b, double *part, double *F,
+                            cudaStream_t st) {
   if (n_atoms <= 0) return;
-  emd_note_launches(1);
-  k_local_force<<<n_atoms, 256, 0, st>>>(g.n, g.h, g.L, Rw, sp, v_es_a,
-                                         v_es_b, F);
+  emd_note_launches(2);
+  dim3 grid(n_atoms, EMD_SPLIT);
+  k_local_force<<<grid, 256, 0, st>>>(g.n, g.h, g.L, Rw, sp, v_es_a, v_es_b,
+                                      part);
+  const int m = 3 * n_atoms;
+  k_local_force_sum<<<(m + 127) / 128, 128, 0, st>>>(part, n_atoms, EMD_SPLIT, F);
 }
 
 void emd_launch_short_range(const SpeciesDev &sp, int n_atoms, const double *Rw,
@@ -349,8 +432,7 @@ void emd_launch_short_range(const SpeciesDev &sp, int n_atoms, const double *Rw,
   if (n_atoms <= 0) return;
   emd_note_launches(1);
   const int nmax = (int)ceil(12.0 / L) + 1;
-  k_short_range<<<(n_atoms + 63) / 64, 64, 0, st>>>(sp, n_atoms, Rw, L, nmax,
-                                                     F, e_part);
+  k_short_range<<<n_atoms, 256, 0, st>>>(sp, n_atoms, Rw, L, nmax, F, e_part);
 }
 
 void emd_launch_vv_positions(int n_atoms, const double *R, const double *V,

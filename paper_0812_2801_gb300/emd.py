@@ -19,6 +19,7 @@ EMD_OK, EMD_EINVAL, EMD_ENOMEM, EMD_ECUDA, EMD_EUNSTABLE, EMD_ESTATE, EMD_ETABLE
 EMD_FP64, EMD_FP32_ORBITALS = 0, 1
 EMD_OPT_FROZEN_IONS, EMD_OPT_PROFILE, EMD_OPT_CHECK_STABLE = 1, 2, 3
 EMD_KERNEL_HORNER, EMD_KERNEL_ALL = 0, 1
+EMD_OBS_ENERGY, EMD_OBS_DIPOLE_Z = 0, 1
 
 
 class EmdError(RuntimeError):
@@ -76,6 +77,14 @@ def load() -> ctypes.CDLL:
     lib.emd_apply_hamiltonian.argtypes = [vp, ip, _DPTR, _DPTR]
     lib.emd_set_option.argtypes = [vp, ip, dp]
     lib.emd_kernel_stats.argtypes = [vp, ip, _DPTR, ctypes.POINTER(ctypes.c_longlong)]
+    lib.emd_propagate_adjoint.argtypes = [vp, ip, dp, dp, _DPTR, ip, ip, _DPTR, _DPTR, _DPTR]
+    lib.emd_propagate_adjoint.restype = ctypes.c_int
+    lib.emd_batch_create.argtypes = [ip, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    lib.emd_batch_create.restype = ctypes.c_int
+    lib.emd_batch_propagate.argtypes = [vp, ip, dp, dp]
+    lib.emd_batch_propagate.restype = ctypes.c_int
+    lib.emd_batch_destroy.argtypes = [vp]
+    lib.emd_batch_destroy.restype = None
     lib.emd_destroy.argtypes = [vp]
     lib.emd_destroy.restype = None
     lib.emd_last_error.restype = ctypes.c_char_p
@@ -189,6 +198,38 @@ def emd_kernel_stats(h, kernel: int = EMD_KERNEL_HORNER):
 def emd_destroy(h) -> None:
     if h:
         load().emd_destroy(h)
+
+
+def emd_propagate_adjoint(h, n_steps: int, dt: float, mu: float,
+                          field: Optional[np.ndarray], ckpt_every: int,
+                          observable: int, n_atoms: int):
+    """Returns (L, dL/dR [n_atoms, 3], dL/dfield [n_steps] or None)."""
+    f = None if field is None else np.ascontiguousarray(field, dtype=np.float64)
+    L = ctypes.c_double()
+    dR = np.zeros((n_atoms, 3))
+    df = None if f is None else np.zeros(n_steps)
+    _check(load().emd_propagate_adjoint(h, int(n_steps), float(dt), float(mu), _dptr(f),
+                                        int(ckpt_every), int(observable),
+                                        ctypes.cast(ctypes.pointer(L), _DPTR),
+                                        _dptr(dR), _dptr(df)))
+    return L.value, dR, df
+
+
+def emd_batch_create(handles) -> ctypes.c_void_p:
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h
+                                              for h in handles])
+    b = ctypes.c_void_p()
+    _check(load().emd_batch_create(len(handles), arr, ctypes.byref(b)))
+    return b
+
+
+def emd_batch_propagate(b, n_steps: int, dt: float, mu: float) -> None:
+    _check(load().emd_batch_propagate(b, int(n_steps), float(dt), float(mu)))
+
+
+def emd_batch_destroy(b) -> None:
+    if b:
+        load().emd_batch_destroy(b)
 
 
 # ---- convenience -----------------------------------------------------------

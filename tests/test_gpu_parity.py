@@ -180,3 +180,19 @@ def test_precision_workload_sampled_hamiltonian():
         got = np.array([[hu[a, z, y, x] for (z, y, x) in pts] for a in orbs])
         scale = np.max(np.abs(ref))
         assert np.max(np.abs(got - ref)) < tol * scale, prec
+
+
+@pytest.mark.parametrize("order", [2, 4, 6, 8])
+@pytest.mark.parametrize("bo", [1, 2, 4])
+def test_fp32_hamiltonian_all_orders_and_blocks(order, bo):
+    """complex64 H psi (shared-memory z-marching kernel for bo = 2, 4) against
+    the FP64 oracle on a 33^3 grid (ragged against the 32-point tile)."""
+    s = inputs.small_system(n=33, h=0.32, fd_order=order, n_atoms=3, seed=9, n_orb=6)
+    g = emd.System(s, emd.EMD_FP32_ORBITALS, block_orbitals=bo)
+    st = O.init_state(s)
+    rng = np.random.default_rng(4)
+    u = rng.normal(size=(5, s.n, s.n, s.n)) + 1j * rng.normal(size=(5, s.n, s.n, s.n))
+    H = O.Hamiltonian(st.v_loc + st.v_h + st.v_xc, st.tables, s.species, s.h, s.fd_order)
+    got = emd.emd_apply_hamiltonian(g.handle, u)
+    g.close()
+    assert rel(got, H.apply(u)) < 3e-6
