@@ -229,6 +229,31 @@ int emd_batch_create(int n, emd_system *const *systems, emd_batch **out);
 int emd_batch_propagate(emd_batch *b, int n_steps, double dt, double mu);
 void emd_batch_destroy(emd_batch *b);
 
+/* Periodic Poisson solve that allocates nothing.  The paper has no
+ * counterpart: this is a convenience for callers that cannot call cudaMalloc
+ * -- code that runs while a CUDA graph is being captured, applications whose
+ * device memory belongs to another allocator or a fixed budget, and
+ * latency-critical loops where an allocation would synchronise the device.
+ *
+ * v = periodic solution of nabla^2 v = -4 pi charge on an n^3 grid of
+ * spacing h with the G = 0 component removed (the Hartree step of
+ * emd_propagate).  charge and v are DEVICE pointers to n^3 doubles in the
+ * canonical layout (x fastest), owned by the caller; they may not alias.
+ * Work is issued on cuda_stream (NULL = legacy default stream); the call
+ * returns without synchronising.
+ *
+ * Limits and sharing: the FFT work arrays live in one file-scope device
+ * array sized for n <= 64 (8 MB, held on every GPU that loads the library
+ * until the process exits); n > 64 or a prime factor of n above 13 returns
+ * EMD_EINVAL with a message.  The array keeps the last call's contents and
+ * every call uses it, so calls that overlap on the GPU (different streams,
+ * or different host threads on one device) race; serialise them.  The first
+ * call on each device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream
+ * capture.  Errors: EMD_EINVAL, EMD_ECUDA. */
+int emd_poisson_static(int n, double h, const double *charge, double *v,
+                       void *cuda_stream);
+
 /* Release all device memory and the handle.  NULL is accepted. */
 void emd_destroy(emd_system *s);
 

@@ -79,6 +79,11 @@ struct Adjoint {
   std::vector<void *> mem;
 };
 
+int emd_set_error(int code, const char *msg) {
+  g_err = msg;
+  return code;
+}
+
 struct emd_system {
   emd_config cfg;
   GridInfo g;

@@ -109,6 +109,8 @@ struct GridInfo {
 // Process-wide count of kernel launches issued by the library (for the
 // benchmark's launch count); defined in emd_api.cu.
 void emd_note_launches(int k);
+// Set the calling thread's error message (emd_last_error) and return code.
+int emd_set_error(int code, const char *msg);
 
 // tables.cu
 void emd_launch_wrap(const double *R, double *Rw, int n_atoms, double L,

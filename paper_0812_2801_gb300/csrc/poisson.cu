@@ -377,3 +377,129 @@ void emd_launch_sum(const double *partials, int n, double *out,
   emd_note_launches(1);
   k_sum<<<1, 256, 0, st>>>(partials, n, out);
 }
+
+// ===========================================================================
+// Poisson solve that allocates nothing (emd_poisson_static).
+//
+// For callers that cannot allocate device memory: code that runs while a
+// CUDA graph is being captured (cudaMalloc is not capturable), applications
+// whose device memory is owned by another allocator or a fixed budget, and
+// latency-critical loops where cudaMalloc/cudaFree would synchronise the
+// device.  The FFT work arrays and the twiddle table live in one file-scope
+// __device__ array of fixed size, present on every GPU that loads the
+// library until the process exits.
+// ===========================================================================
+namespace {
+
+constexpr int kStaticMaxN = 64;                       // largest grid edge
+constexpr size_t kStaticN3 = (size_t)kStaticMaxN * kStaticMaxN * kStaticMaxN;
+constexpr int kStaticTab = 2048;                      // twiddle entries
+// [0, N^3): work a, [N^3, 2 N^3): work b, then the twiddle table
+__device__ __align__(256) double2 g_static_scratch[2 * kStaticN3 + kStaticTab];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+double2 *g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device (set-up on the
+// first call per device).  In host code the symbol is only a stand-in.
+cudaError_t static_scratch(double2 **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[dev] = static_cast<double2 *>(p);
+  }
+  *out = g_static_ptr[dev];
+  return cudaSuccess;
+}
+
+// Plan offsets only (no table, no heap): same radix order as make_plan.
+bool plan_offsets(int n, FftPlan &p) {
+  p.n = n;
+  p.ns = 0;
+  int m = n;
+  const int order[] = {4, 2, 3, 5, 7, 11, 13};
+  for (int r : order) {
+    while (m % r == 0) {
+      if (p.ns >= kMaxStages) return false;
+      p.rad[p.ns++] = r;
+      m /= r;
+    }
+  }
+  if (m != 1) return false;
+  int off = 0, Ns = 1;
+  for (int s = 0; s < p.ns; ++s) {
+    p.tw_off[s] = off;
+    off += Ns * p.rad[s];
+    p.root_off[s] = off;
+    off += p.rad[s];
+    Ns *= p.rad[s];
+  }
+  if (off > kStaticTab) return false;
+  p.lines = n >= 1280 ? 1 : (1280 / n > 8 ? 8 : 1280 / n);
+  return true;
+}
+
+// Twiddles and roots of the plan, computed on the device with sincospi.
+__global__ void k_fill_twiddles(FftPlan p, double2 *tab) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int Ns = 1;
+  for (int s = 0; s < p.ns; ++s) {
+    const int R = p.rad[s];
+    if (i >= p.tw_off[s] && i < p.tw_off[s] + Ns * R) {
+      const int k = i - p.tw_off[s];
+      const int jm = k / R, r = k % R;
+      const long num = (long)jm * r % ((long)Ns * R);
+      double sn, cs;
+      sincospi(-2.0 * (double)num / (double)(Ns * R), &sn, &cs);
+      tab[i] = make_double2(cs, sn);
+    } else if (i >= p.root_off[s] && i < p.root_off[s] + R) {
+      const int q = i - p.root_off[s];
+      double sn, cs;
+      sincospi(-2.0 * (double)q / (double)R, &sn, &cs);
+      tab[i] = make_double2(cs, sn);
+    }
+    Ns *= R;
+  }
+}
+
+}  // namespace
+
+extern "C" int emd_poisson_static(int n, double h, const double *charge,
+                                  double *v, void *cuda_stream) {
+  if (!charge || !v || !(h > 0.0) || n < 2)
+    return emd_set_error(EMD_EINVAL, "emd_poisson_static: NULL pointer, h <= 0 or n < 2");
+  if (n > kStaticMaxN)
+    return emd_set_error(EMD_EINVAL, "emd_poisson_static: n exceeds the static "
+                                     "scratch limit of 64 points per axis");
+  FftPlan p;
+  if (!plan_offsets(n, p))
+    return emd_set_error(EMD_EINVAL, "emd_poisson_static: n has a prime factor above 13");
+  double2 *base = nullptr;
+  if (static_scratch(&base) != cudaSuccess)
+    return emd_set_error(EMD_ECUDA, "emd_poisson_static: cudaGetSymbolAddress of "
+                                    "the static scratch failed");
+  const size_t n3 = (size_t)n * n * n;
+  double2 *wa = base, *wb = base + kStaticN3, *tab = base + 2 * kStaticN3;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  k_fill_twiddles<<<(kStaticTab + 255) / 256, 256, 0, st>>>(p, tab);
+  const int blocks = (n * n + p.lines - 1) / p.lines;
+  const size_t smem = 2 * (size_t)p.lines * n * sizeof(double2);
+  const double L = n * h;
+  k_fft_pass<true, false><<<blocks, 256, smem, st>>>(charge, wa, p, tab, -1, 1.0);
+  k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wa, wb, p, tab, -1, 1.0);
+  k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wb, wa, p, tab, -1, 1.0);
+  k_poisson_kernel<<<(unsigned)((n3 + 255) / 256), 256, 0, st>>>(wa, n, L);
+  k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wa, wb, p, tab, +1, 1.0);
+  k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wb, wa, p, tab, +1, 1.0);
+  k_fft_pass<false, true><<<blocks, 256, smem, st>>>(wa, v, p, tab, +1, 1.0);
+  if (cudaGetLastError() != cudaSuccess)
+    return emd_set_error(EMD_ECUDA, "emd_poisson_static: kernel launch failed");
+  return emd_set_error(EMD_OK, "");
+}

@@ -77,6 +77,8 @@ def load() -> ctypes.CDLL:
     lib.emd_apply_hamiltonian.argtypes = [vp, ip, _DPTR, _DPTR]
     lib.emd_set_option.argtypes = [vp, ip, dp]
     lib.emd_kernel_stats.argtypes = [vp, ip, _DPTR, ctypes.POINTER(ctypes.c_longlong)]
+    lib.emd_poisson_static.argtypes = [ip, dp, vp, vp, vp]
+    lib.emd_poisson_static.restype = ctypes.c_int
     lib.emd_propagate_adjoint.argtypes = [vp, ip, dp, dp, _DPTR, ip, ip, _DPTR, _DPTR, _DPTR]
     lib.emd_propagate_adjoint.restype = ctypes.c_int
     lib.emd_batch_create.argtypes = [ip, ctypes.POINTER(vp), ctypes.POINTER(vp)]
@@ -193,6 +195,15 @@ def emd_kernel_stats(h, kernel: int = EMD_KERNEL_HORNER):
     n = ctypes.c_longlong()
     _check(load().emd_kernel_stats(h, int(kernel), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def emd_poisson_static(n: int, h: float, charge_dev: int, v_dev: int,
+                       stream: int = 0) -> None:
+    """Periodic Poisson solve on device buffers without any allocation
+    (see include/emd.h); charge_dev and v_dev are device addresses."""
+    _check(load().emd_poisson_static(int(n), float(h), ctypes.c_void_p(charge_dev),
+                                     ctypes.c_void_p(v_dev),
+                                     ctypes.c_void_p(stream) if stream else None))
 
 
 def emd_destroy(h) -> None:
