@@ -44,7 +44,7 @@ BYTES_PER_UPDATE = {"f32": 24, "f64": 48}
 # dram__bytes_read.sum + dram__bytes_write.sum of one Horner-stage launch
 # (profiles/horner_stage_c96.md), per precision, for the kernel as built;
 # None until a capture exists for it.
-TRAFFIC_PER_LAUNCH = {"f32": None, "f64": None}
+TRAFFIC_PER_LAUNCH = {"f32": 3.350e9, "f64": None}
 
 
 def dist_env():
@@ -275,6 +275,45 @@ def time_batched(emd, torch, steps, n_replicas=32):
                         "2 orbitals per atom, order 8, complex64, mu 10, dt 0.158"}
 
 
+def time_adjoint(emd, torch, n_steps=200, ckpt=20):
+    """Fixed-ion adjoint gradient of the final dipole with respect to ion
+    positions and 200 field amplitudes on the 64^3 field workload (16 atoms,
+    32 orbitals, order 6, FP64, mu 10), against the plain forward run."""
+    from paper_0812_2801_gb300 import inputs
+    s = inputs.field_c64(n_steps)
+    upd = 8.0 * s.n_orb * s.n ** 3 * n_steps
+
+    def fresh():
+        h = emd.emd_init_system(emd.config_for(s))
+        emd.emd_set_option(h, emd.EMD_OPT_FROZEN_IONS, 1)
+        emd.emd_set_ions(h, s.R, s.V * 0.0)
+        emd.emd_set_orbitals(h, s.psi)
+        return h
+
+    h = fresh()
+    emd.emd_propagate(h, 2, s.dt, s.mu, s.field[:2])
+    torch.cuda.synchronize()
+    emd.emd_destroy(h)
+    h = fresh()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    emd.emd_propagate(h, n_steps, s.dt, s.mu, s.field)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    emd.emd_destroy(h)
+    h = fresh()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    emd.emd_propagate_adjoint(h, n_steps, s.dt, s.mu, s.field, ckpt,
+                              emd.EMD_OBS_DIPOLE_Z, s.n_atoms)
+    t_adj = time.perf_counter() - t0
+    emd.emd_destroy(h)
+    return {"workload": "field-16at-64^3: 16 Si-like atoms (bcc), 32 orbitals, 64^3 at 0.3, "
+                        "order 6, FP64, mu 10, 200 steps, fixed ions, checkpoints every 20",
+            "forward_s": t_fwd, "gradient_s": t_adj, "gradient_over_forward": t_adj / t_fwd,
+            "forward_updates_per_s": upd / t_fwd, "unit": UNIT}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -286,6 +325,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--batched-steps", type=int, default=12)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -329,6 +369,7 @@ def main():
     e2e_val = ws * upd_per_step * args.e2e_steps / e2e_dt
 
     batched = None if args.no_batched else time_batched(emd, torch, args.batched_steps)
+    adjoint = None if (args.no_adjoint or ws > 1) else time_adjoint(emd, torch)
 
     peak, peak_kind = measured_peaks()
     stage_avg_s = r32["stage_ms"] * 1e-3 / max(1, r32["stage_launches"])
@@ -362,6 +403,7 @@ def main():
                 "note": "per step: set_ions + set_orbitals (pinned host, complex128), "
                         "propagate 1 MD step, get_state(psi) + get_forces + get_energy"},
         "batched": batched,
+        "adjoint": adjoint,
         "gpu_launches": r32["launches"],
         "clocks": clk.summary(),
         "energy_total": r32["energy"]["total"],

@@ -59,6 +59,15 @@ extern "C" {
 #define EMD_OPT_FROZEN_IONS  1  /* value != 0: ions fixed, no forces/VV      */
 #define EMD_OPT_PROFILE      2  /* value != 0: time Horner-stage launches     */
 #define EMD_OPT_CHECK_STABLE 3  /* value == 0: skip the stability refusal    */
+#define EMD_OPT_STAGE_VARIANT 4 /* complex64 Horner-stage kernel for bo = 2:
+                                   0 one thread per grid point (default),
+                                   1 one thread per (point, orbital); bo = 4
+                                   always uses the latter                  */
+#define EMD_OPT_PROJECTION   5  /* projections <p_J|u>: 1 atom-major (each
+                                   atom gathers its sphere, default), 0
+                                   point-major (each 8^3 tile read once,
+                                   warp-tree reductions per atom; slower on
+                                   GB300: 1.09 vs 0.41 ms, 96^3 complex64) */
 
 /* kernels that can be timed with EMD_OPT_PROFILE */
 #define EMD_KERNEL_HORNER    0  /* one Taylor/Horner stage u' = psi0 + a H u */
@@ -94,7 +103,8 @@ typedef struct {
   int n_atoms;           /* number of atoms, >= 0                        */
   emd_species species;   /* one species for all atoms                    */
   void *cuda_stream;     /* cudaStream_t to issue work on, or NULL        */
-  int block_orbitals;    /* orbitals interleaved per grid point; 0 = auto */
+  int block_orbitals;    /* orbitals interleaved per grid point: 1, 2, 4;
+                            0 = 4 for complex64, 2 for complex128      */
 } emd_config;
 
 /* Energy components (hartree), eq. E_KS and eq. E_new:

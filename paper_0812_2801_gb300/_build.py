@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libemd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["emd_api.cu", "hpsi.cu", "tables.cu", "poisson.cu", "adjoint.cu"]
+SOURCES = ["emd_api.cu", "hpsi.cu", "tables.cu", "poisson.cu", "adjoint.cu", "project_pm.cu"]
 
 
 def nvcc() -> str:

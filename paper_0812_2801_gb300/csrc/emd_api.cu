@@ -113,7 +113,8 @@ struct emd_system {
   double *scal = nullptr;
   int *err = nullptr;
   int ions_set = 0, orbs_set = 0;
-  int frozen_ions = 0, profile = 0, check_stable = 1;
+  int frozen_ions = 0, profile = 0, check_stable = 1, proj_atom_major = 1;
+  double2 *proj_part = nullptr;   // point-major projection partials
   double v_max = 0.0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending, prof_free;
   double prof_ms = 0.0;
@@ -168,6 +169,7 @@ int build_set(emd_system *s, int k) {
   TableSet &t = s->ts[k];
   emd_launch_wrap(t.R, t.Rw, s->n_atoms, s->g.L, s->st);
   emd_launch_tables(s->g, s->sp, s->n_atoms, t, s->err, s->st);
+  emd_launch_tile_atoms(s->g, s->n_atoms, t, s->err, s->st);
   // v_loc = Poisson(-g): solve for g, negate in the final pass
   emd_launch_poisson(s->g, t.g_ion, t.v_loc, s->fft_a, s->fft_b, s->st);
   return launch_check("build_set");
@@ -176,8 +178,13 @@ int build_set(emd_system *s, int k) {
 void negate_grid(double *v, int n3, cudaStream_t st);
 
 void project(emd_system *s, const void *u, int set) {
-  emd_launch_project(s->o, s->ts[set], s->n_atoms, u, s->g.h * s->g.h * s->g.h,
-                     s->sp.h_kb, s->c, s->hc, s->st);
+  if (s->proj_atom_major)
+    emd_launch_project(s->o, s->ts[set], s->n_atoms, u, s->g.h * s->g.h * s->g.h,
+                       s->sp.h_kb, s->c, s->hc, s->st);
+  else
+    emd_launch_project_pm(s->o, s->ts[set], s->n_atoms, u,
+                          s->g.h * s->g.h * s->g.h, s->sp.h_kb, s->c, s->hc,
+                          s->proj_part, s->st);
 }
 
 void stage(emd_system *s, const void *u_in, const void *psi0, void *u_out,
@@ -377,12 +384,15 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
   o.n3 = s->g.n3;
   o.h = c.h;
   o.prec = c.precision;
+  // default block width: measured fastest stage kernel on the 96^3 order-8
+  // workload (complex64: 4 orbitals, column kernel; complex128: 2)
   o.bo = c.block_orbitals ? c.block_orbitals : (c.precision == EMD_FP64 ? 2 : 4);
   o.n_orb = c.n_orb;
   o.n_blk = (c.n_orb + o.bo - 1) / o.bo;
   o.n_orb_pad = o.n_blk * o.bo;
   o.half_order = c.fd_order / 2;
   o.n_atoms = c.n_atoms;
+  o.stage_variant = 0;
   for (int k = 0; k <= EMD_MAX_HALF_ORDER; ++k) o.w[k] = 0.0;
   o.w[0] = -1.5 * fd_weight(c.fd_order, 0) / (c.h * c.h);
   for (int k = 1; k <= o.half_order; ++k)
@@ -438,9 +448,17 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
     TRY(A((void **)&t.at_pt, (size_t)na * cap * 4));
     TRY(A((void **)&t.at_p, (size_t)na * cap * 8));
     TRY(A((void **)&t.at_d, (size_t)na * cap * 24));
+    t.n_slots_cap = ntiles * EMD_TILE_ATOM_MAX;
+    TRY(A((void **)&t.tile_nat, ntiles * 4));
+    TRY(A((void **)&t.tile_atoms, (size_t)ntiles * EMD_TILE_ATOM_MAX * 4));
+    TRY(A((void **)&t.tile_off, ntiles * 4));
+    TRY(A((void **)&t.at_ntiles, na * 4));
+    TRY(A((void **)&t.at_tiles, (size_t)na * ntiles * sizeof(int2)));
     TRY(A((void **)&t.g_ion, n3 * 8));
     TRY(A((void **)&t.v_loc, n3 * 8));
   }
+  TRY(A((void **)&s->proj_part, (size_t)o.n_blk * ntiles * EMD_TILE_ATOM_MAX *
+                                     o.bo * sizeof(double2)));
   TRY(A((void **)&s->c, (size_t)na * o.n_orb_pad * sizeof(double2)));
   TRY(A(&s->hc, (size_t)na * o.n_orb_pad * esz));
   TRY(A((void **)&s->V, na * 3 * 8));
@@ -544,6 +562,14 @@ int emd_set_option(emd_system *s, int option, double value) {
     case EMD_OPT_FROZEN_IONS: s->frozen_ions = value != 0.0; return EMD_OK;
     case EMD_OPT_PROFILE: s->profile = value != 0.0; return EMD_OK;
     case EMD_OPT_CHECK_STABLE: s->check_stable = value != 0.0; return EMD_OK;
+    case EMD_OPT_PROJECTION:
+      if (value != 0.0 && value != 1.0) return fail(EMD_EINVAL, "projection form must be 0 or 1");
+      s->proj_atom_major = (int)value;
+      return EMD_OK;
+    case EMD_OPT_STAGE_VARIANT:
+      if (value != 0.0 && value != 1.0) return fail(EMD_EINVAL, "stage variant must be 0 or 1");
+      s->o.stage_variant = (int)value;
+      return EMD_OK;
   }
   return fail(EMD_EINVAL, "unknown option %d", option);
 }

@@ -7,6 +7,7 @@
 #define EMD_PT_KMAX 16          // atoms per grid point in the point-major table
 #define EMD_TILE 8              // edge of the tiles that carry atom candidates
 #define EMD_TILE_CAND_MAX 160   // (atom, image) candidates per tile
+#define EMD_TILE_ATOM_MAX 32    // distinct atoms per tile (point-major projections)
 #define EMD_MAX_HALF_ORDER 6    // fd_order / 2 <= 6
 #define EMD_SPLIT 16            // CTAs per atom for table building and local forces
 
@@ -45,6 +46,12 @@ struct TableSet {
   int *at_pt;       // [n_atoms][cap] flat grid index
   double *at_p;     // [n_atoms][cap] p value of that (point, image)
   double *at_d;     // [n_atoms][cap][3] displacement r - R_image
+  int *tile_nat;    // [n_tiles] distinct atoms per tile
+  int *tile_atoms;  // [n_tiles][EMD_TILE_ATOM_MAX] in atom order
+  int *tile_off;    // [n_tiles] exclusive prefix sum of tile_nat
+  int *at_ntiles;   // [n_atoms] tiles listing the atom
+  int2 *at_tiles;   // [n_atoms][n_tiles] (tile, slot) in tile order
+  int n_slots_cap;  // n_tiles * EMD_TILE_ATOM_MAX
   double *g_ion;    // [n3] sum of Gaussian ion charges
   double *v_loc;    // [n3] Poisson(-g_ion)
   int cap;
@@ -165,6 +172,7 @@ struct StageArgs {
 };
 struct OrbLayout {
   int n, n3, bo, n_blk, n_orb, n_orb_pad, prec, half_order, n_atoms;
+  int stage_variant;   // complex64 stage: 0 point-per-thread, 1 column-per-thread
   double h;
   double w[EMD_MAX_HALF_ORDER + 1];   // w_0 = -3 c_0 / (2 h^2), w_k = -c_k/(2 h^2)
 };
@@ -187,6 +195,14 @@ void emd_launch_unpack(const OrbLayout &o, const void *u, double2 *canon,
                        int n_vec, cudaStream_t st);
 void emd_launch_abs2_sum(const double2 *c, int n, double *out,
                          cudaStream_t st);
+
+// project_pm.cu
+void emd_launch_tile_atoms(const GridInfo &g, int n_atoms, TableSet &t, int *err,
+                           cudaStream_t st);
+// partial: [n_blk][n_slots_cap][bo] complex FP64 scratch
+void emd_launch_project_pm(const OrbLayout &o, const TableSet &t, int n_atoms,
+                           const void *u, double h3, double h_kb, double2 *c,
+                           void *hc, double2 *partial, cudaStream_t st);
 
 // adjoint.cu (FP64 orbitals)
 void emd_adj_axpy(double2 *y, const double2 *x, size_t n, cudaStream_t st);

@@ -393,6 +393,277 @@ k_stage_z(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Point-per-thread variant: each thread owns one grid point of a 32 x 16 tile
+// and all bo orbitals of the block there, so the per-point work (staging
+// offsets, v_eff, projector records, index arithmetic) is shared by the bo
+// orbitals and shared memory is read 16 bytes at a time.  Same 3-deep ring
+// and (2M+1)-slot delay line as k_stage_z.
+// ---------------------------------------------------------------------------
+template <int BO, int M> struct ZPTile {
+  static constexpr int TX = 32, TY = 16, NT = 512;
+  static constexpr int SW = TX + 2 * M, SH = TY + 2 * M;
+  static constexpr int PLANE = SH * SW * BO;
+  static constexpr int CH = BO / 2;
+  static constexpr int NCHUNK = SH * SW * CH;
+  static constexpr int CPT = (NCHUNK + NT - 1) / NT;
+  static constexpr int NV = TX * TY;                       // == NT
+  static constexpr int QPT = (2 * NV + NT - 1) / NT;
+  static constexpr int SPT = (NV * CH + NT - 1) / NT;
+  static constexpr int NS = 2 * M + 1, NB = 3;
+  static constexpr int UB = PLANE * 8, VB = NV * 4, QB = NV * 32, SB = NV * BO * 8;
+  static constexpr int SLOT = UB + VB + QB + SB;
+  static constexpr size_t SMEM_FIXED = (size_t)NB * SLOT;
+};
+
+template <int BO>
+__device__ __forceinline__ void lds_point(const float2 *p, float2 (&v)[BO]) {
+#pragma unroll
+  for (int h = 0; h < BO / 2; ++h) {
+    const float4 q = reinterpret_cast<const float4 *>(p)[h];
+    v[2 * h] = make_float2(q.x, q.y);
+    v[2 * h + 1] = make_float2(q.z, q.w);
+  }
+}
+
+template <int BO, int M>
+__global__ void __launch_bounds__(512, 1)
+k_stage_zp(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
+           float2 *__restrict__ u_out, const float *__restrict__ v_eff,
+           const int2 *__restrict__ pt4, const int *__restrict__ pt_J,
+           const float *__restrict__ pt_pf, const float2 *__restrict__ hc,
+           int n, int ntx, int zc, int n_orb_pad, int n_atoms, int hc_in_smem,
+           float a, int apply_only, Weights<float> W) {
+  typedef ZPTile<BO, M> Z;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2 *hcs = reinterpret_cast<float2 *>(smraw + Z::NB * Z::SLOT);
+  const int tid = threadIdx.x;
+  const int xl = tid % Z::TX, yl = tid / Z::TX;
+  const int tx0 = (blockIdx.x % ntx) * Z::TX, ty0 = (blockIdx.x / ntx) * Z::TY;
+  const int x = tx0 + xl, y = ty0 + yl;
+  const bool own = x < n && y < n;
+  const int z0 = blockIdx.y * zc;
+  const int zcount = min(zc, n - z0);
+  const int total = zcount + 2 * M;
+  const int blk = blockIdx.z;
+  const int n2 = n * n;
+  const size_t n3 = (size_t)n2 * n;
+  const float2 *ub = u_in + (size_t)blk * n3 * BO;
+  const float2 *pb = psi0 + (size_t)blk * n3 * BO;
+  float2 *ob = u_out + (size_t)blk * n3 * BO;
+
+  int src_off[Z::CPT], dst_off[Z::CPT];
+#pragma unroll
+  for (int i = 0; i < Z::CPT; ++i) {
+    const int q = tid + i * Z::NT;
+    src_off[i] = -1;
+    dst_off[i] = 0;
+    if (q < Z::NCHUNK) {
+      const int hh = q % Z::CH, pnt = q / Z::CH;
+      const int c = pnt % Z::SW, rr = pnt / Z::SW;
+      const int xx = (tx0 - M + c + 2 * n) % n;
+      const int yy = (ty0 - M + rr + 2 * n) % n;
+      src_off[i] = (yy * n + xx) * BO + 2 * hh;
+      dst_off[i] = (rr * Z::SW + c) * BO + 2 * hh;
+    }
+  }
+  const int own_off = (min(y, n - 1) * n + min(x, n - 1));   // in-plane point index
+  const int v_src = (y % n) * n + x % n;
+  int q_src[Z::QPT], q_dst[Z::QPT];
+#pragma unroll
+  for (int i = 0; i < Z::QPT; ++i) {
+    const int q = tid + i * Z::NT;
+    q_src[i] = -1;
+    q_dst[i] = 0;
+    if (q < 2 * Z::NV) {
+      const int pnt = q >> 1, half = q & 1;
+      const int xx = min(tx0 + pnt % Z::TX, n - 1), yy = min(ty0 + pnt / Z::TX, n - 1);
+      q_src[i] = (yy * n + xx) * 4 + 2 * half;
+      q_dst[i] = pnt * 4 + 2 * half;
+    }
+  }
+  int s_src[Z::SPT], s_dst[Z::SPT];
+#pragma unroll
+  for (int i = 0; i < Z::SPT; ++i) {
+    const int q = tid + i * Z::NT;
+    s_src[i] = -1;
+    s_dst[i] = 0;
+    if (q < Z::NV * Z::CH) {
+      const int pnt = q / Z::CH, hh = q % Z::CH;
+      const int xx = min(tx0 + pnt % Z::TX, n - 1), yy = min(ty0 + pnt / Z::TX, n - 1);
+      s_src[i] = (yy * n + xx) * BO + 2 * hh;
+      s_dst[i] = pnt * BO + 2 * hh;
+    }
+  }
+  if (hc_in_smem) {
+    for (int i = tid; i < n_atoms * BO; i += Z::NT)
+      hcs[i] = hc[(size_t)(i / BO) * n_orb_pad + (size_t)blk * BO + i % BO];
+  }
+
+  auto issue = [&](int zi, int slot) {
+    unsigned char *base = smraw + slot * Z::SLOT;
+    float2 *U = reinterpret_cast<float2 *>(base);
+    float *V = reinterpret_cast<float *>(base + Z::UB);
+    int2 *Q = reinterpret_cast<int2 *>(base + Z::UB + Z::VB);
+    float2 *S = reinterpret_cast<float2 *>(base + Z::UB + Z::VB + Z::QB);
+    int zz = z0 - M + zi;
+    if (zz < 0) zz += n;
+    if (zz >= n) zz -= n;
+    const float2 *src = ub + (size_t)zz * n2 * BO;
+#pragma unroll
+    for (int i = 0; i < Z::CPT; ++i)
+      if (src_off[i] >= 0) cp_async16(U + dst_off[i], src + src_off[i]);
+    cp_async4(V + tid, v_eff + (size_t)zz * n2 + v_src);
+    if (zi >= 2 * M) {
+      const int zo = z0 + zi - 2 * M;
+      const int2 *qs = pt4 + (size_t)zo * n2 * 4;
+#pragma unroll
+      for (int i = 0; i < Z::QPT; ++i)
+        if (q_src[i] >= 0) cp_async16(Q + q_dst[i], qs + q_src[i]);
+      if (!apply_only) {
+        const float2 *ss = pb + (size_t)zo * n2 * BO;
+#pragma unroll
+        for (int i = 0; i < Z::SPT; ++i)
+          if (s_src[i] >= 0) cp_async16(S + s_dst[i], ss + s_src[i]);
+      }
+    }
+    cp_async_commit();
+  };
+
+  float2 w2[M + 1];
+#pragma unroll
+  for (int k = 0; k <= M; ++k) w2[k] = make_float2(W.w[k], W.w[k]);
+  const float2 a2 = make_float2(a, -a);
+
+  float2 acc[BO][Z::NS];
+#pragma unroll
+  for (int j = 0; j < BO; ++j)
+#pragma unroll
+    for (int q = 0; q < Z::NS; ++q) acc[j][q] = make_float2(0.f, 0.f);
+
+  const int cidx = ((yl + M) * Z::SW + xl + M) * BO;   // own point in a staged plane
+  issue(0, 0);
+  if (total > 1) issue(1, 1);
+  int sb = 0;
+  for (int g = 0; g * Z::NS < total; ++g) {
+#pragma unroll
+    for (int ph = 0; ph < Z::NS; ++ph) {
+      const int zi = g * Z::NS + ph;
+      if (zi >= total) break;
+      if (zi + 2 < total) {
+        issue(zi + 2, sb == 0 ? 2 : sb - 1);
+        cp_async_wait<2>();
+      } else if (zi + 1 < total) {
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      const unsigned char *base = smraw + sb * Z::SLOT;
+      const float2 *P = reinterpret_cast<const float2 *>(base) + cidx;
+      const float ve = reinterpret_cast<const float *>(base + Z::UB)[tid];
+      float2 c[BO], s2[BO];
+      lds_point<BO>(P, c);
+#pragma unroll
+      for (int j = 0; j < BO; ++j) s2[j] = __fmul2_rn(w2[0], c[j]);
+#pragma unroll
+      for (int k = 1; k <= M; ++k) {
+#pragma unroll
+        for (int h = 0; h < BO / 2; ++h) {
+          // two orbitals at a time: at most four 16-byte neighbour loads live
+          const float4 xp = reinterpret_cast<const float4 *>(P + k * BO)[h];
+          const float4 xm = reinterpret_cast<const float4 *>(P - k * BO)[h];
+          const float4 yp = reinterpret_cast<const float4 *>(P + k * Z::SW * BO)[h];
+          const float4 ym = reinterpret_cast<const float4 *>(P - k * Z::SW * BO)[h];
+          const float2 t0 = __fadd2_rn(__fadd2_rn(make_float2(xp.x, xp.y), make_float2(xm.x, xm.y)),
+                                       __fadd2_rn(make_float2(yp.x, yp.y), make_float2(ym.x, ym.y)));
+          const float2 t1 = __fadd2_rn(__fadd2_rn(make_float2(xp.z, xp.w), make_float2(xm.z, xm.w)),
+                                       __fadd2_rn(make_float2(yp.z, yp.w), make_float2(ym.z, ym.w)));
+          s2[2 * h] = __ffma2_rn(w2[k], t0, s2[2 * h]);
+          s2[2 * h + 1] = __ffma2_rn(w2[k], t1, s2[2 * h + 1]);
+        }
+      }
+      const float2 ve2 = make_float2(ve, ve);
+#pragma unroll
+      for (int j = 0; j < BO; ++j) {
+        s2[j] = __ffma2_rn(ve2, c[j], s2[j]);
+        acc[j][ph] = __fadd2_rn(acc[j][ph], s2[j]);
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+          acc[j][(ph + k) % Z::NS] = __ffma2_rn(w2[k], c[j], acc[j][(ph + k) % Z::NS]);
+          if (g > 0 || ph - k >= 0)
+            acc[j][(ph - k + Z::NS) % Z::NS] =
+                __ffma2_rn(w2[k], c[j], acc[j][(ph - k + Z::NS) % Z::NS]);
+        }
+      }
+      if (zi >= M) {
+        const int slot = (ph - M + Z::NS) % Z::NS;
+        if (zi >= 2 * M && own) {
+          const int zo = z0 + zi - 2 * M;
+          const int4 *Q4 = reinterpret_cast<const int4 *>(base + Z::UB + Z::VB);
+          const int4 q01 = Q4[2 * tid], q23 = Q4[2 * tid + 1];
+          const int cnt = q01.x >> 16;
+          const int J[4] = {q01.x & 0xffff, q01.z, q23.x, q23.z};
+          const float pv[4] = {__int_as_float(q01.y), __int_as_float(q01.w),
+                               __int_as_float(q23.y), __int_as_float(q23.w)};
+          float2 hv[BO];
+#pragma unroll
+          for (int j = 0; j < BO; ++j) hv[j] = acc[j][slot];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float2 hcv[BO];
+            if (hc_in_smem) {
+              lds_point<BO>(hcs + J[e] * BO, hcv);
+            } else {
+#pragma unroll
+              for (int j = 0; j < BO; ++j)
+                hcv[j] = __ldg(hc + (size_t)J[e] * n_orb_pad + (size_t)blk * BO + j);
+            }
+            const float2 p2 = make_float2(pv[e], pv[e]);
+#pragma unroll
+            for (int j = 0; j < BO; ++j) hv[j] = __ffma2_rn(p2, hcv[j], hv[j]);
+          }
+          const size_t p = (size_t)zo * n2 + own_off;
+          for (int e = 4; e < cnt; ++e) {
+            const int Je = __ldg(pt_J + (size_t)e * n3 + p);
+            const float pe = __ldg(pt_pf + (size_t)e * n3 + p);
+            const float2 p2 = make_float2(pe, pe);
+#pragma unroll
+            for (int j = 0; j < BO; ++j) {
+              const float2 hcv = hc_in_smem ? hcs[Je * BO + j]
+                  : __ldg(hc + (size_t)Je * n_orb_pad + (size_t)blk * BO + j);
+              hv[j] = __ffma2_rn(p2, hcv, hv[j]);
+            }
+          }
+          float2 out[BO];
+          if (apply_only) {
+#pragma unroll
+            for (int j = 0; j < BO; ++j) out[j] = hv[j];
+          } else {
+            float2 s0[BO];
+            lds_point<BO>(reinterpret_cast<const float2 *>(base + Z::UB + Z::VB + Z::QB) + tid * BO, s0);
+#pragma unroll
+            for (int j = 0; j < BO; ++j)
+              out[j] = __ffma2_rn(a2, make_float2(hv[j].y, hv[j].x), s0[j]);
+          }
+          float4 *dst = reinterpret_cast<float4 *>(ob + p * BO);
+#pragma unroll
+          for (int h = 0; h < BO / 2; ++h)
+            dst[h] = make_float4(out[2 * h].x, out[2 * h].y, out[2 * h + 1].x, out[2 * h + 1].y);
+        }
+#pragma unroll
+        for (int j = 0; j < BO; ++j) {
+#pragma unroll
+          for (int q = 0; q < Z::NS; ++q)
+            if (q == slot) acc[j][q] = make_float2(0.f, 0.f);
+        }
+      }
+      __syncthreads();
+      sb = sb == 2 ? 0 : sb + 1;
+    }
+  }
+}
+
 // c[J][A] = h^3 sum_e p_e u_A(pt_e) over atom J's (point, image) entries;
 // hc = h_kb c in orbital precision.  One block per (atom, orbital block).
 // Each thread accumulates its strided share of the entries in T (FP32 for
@@ -457,6 +728,38 @@ __global__ void k_density(const typename cplx<T>::type *__restrict__ u,
     }
   }
   rho[p] = occ * acc;
+}
+
+// complex64 orbitals: sum |u|^2 in double-float arithmetic on the FP32
+// pipes.  Each square is split exactly into p + e (e = fma(v, v, -p)); the
+// running sum is a (hi, lo) pair updated with Knuth's TwoSum, and converted to
+// FP64 once per point (~1e-13 relative, without FP64 instructions per term).
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float t) {
+  // rounded-to-nearest intrinsics: never contracted into FMAs
+  const float s = __fadd_rn(hi, t);
+  const float bb = __fsub_rn(s, hi);
+  lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(t, bb)));
+  hi = s;
+}
+
+template <int BO>
+__global__ void k_density_c64(const float2 *__restrict__ u, size_t n3, int n_blk,
+                              double occ, double *rho) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n3) return;
+  float hi = 0.f, lo = 0.f;
+  for (int b = 0; b < n_blk; ++b) {
+    const float2 *ub = u + ((size_t)b * n3 + p) * BO;
+#pragma unroll
+    for (int j = 0; j < BO; ++j) {
+      const float2 v = ub[j];
+      const float px = __fmul_rn(v.x, v.x), py = __fmul_rn(v.y, v.y);
+      lo = __fadd_rn(lo, __fadd_rn(__fmaf_rn(v.x, v.x, -px), __fmaf_rn(v.y, v.y, -py)));
+      two_sum_acc(hi, lo, px);
+      two_sum_acc(hi, lo, py);
+    }
+  }
+  rho[p] = occ * ((double)hi + (double)lo);
 }
 
 // partial[b] = sum over the points of block b and all orbitals of
@@ -648,6 +951,39 @@ void stage_z_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
       (float)a.a, a.apply_only, weights_of<float>(o));
 }
 
+template <int BO, int M>
+void stage_zp_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
+  typedef ZPTile<BO, M> Z;
+  const int hc_bytes = o.n_atoms * BO * (int)sizeof(float2);
+  const int hc_in_smem = hc_bytes <= 16384;
+  const size_t smem = Z::SMEM_FIXED + (hc_in_smem ? hc_bytes : 0);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_stage_zp<BO, M>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(Z::SMEM_FIXED + 16384));
+    attr_done = true;
+  }
+  const int ntx = (o.n + Z::TX - 1) / Z::TX, nty = (o.n + Z::TY - 1) / Z::TY;
+  const int zc = o.n <= 64 ? o.n : (o.n + 1) / 2 <= 64 ? (o.n + 1) / 2 : 48;
+  dim3 grid(ntx * nty, (o.n + zc - 1) / zc, o.n_blk);
+  k_stage_zp<BO, M><<<grid, Z::NT, smem, st>>>(
+      (const float2 *)a.u_in, (const float2 *)a.psi0, (float2 *)a.u_out,
+      (const float *)a.v_eff, a.tab->pt4, a.tab->pt_J, a.tab->pt_pf,
+      (const float2 *)a.hc, o.n, ntx, zc, o.n_orb_pad, o.n_atoms, hc_in_smem,
+      (float)a.a, a.apply_only, weights_of<float>(o));
+}
+
+template <int BO>
+void stage_zp_m(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
+  switch (o.half_order) {
+    case 1: stage_zp_t<BO, 1>(o, a, st); break;
+    case 2: stage_zp_t<BO, 2>(o, a, st); break;
+    case 3: stage_zp_t<BO, 3>(o, a, st); break;
+    case 4: stage_zp_t<BO, 4>(o, a, st); break;
+  }
+}
+
 template <int BO>
 void stage_z_m(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
   switch (o.half_order) {
@@ -690,9 +1026,13 @@ template <typename T, int BO>
 void density_t(const OrbLayout &o, const void *u, double occ, double *rho,
                cudaStream_t st) {
   typedef typename cplx<T>::type V;
-  k_density<T, BO><<<(o.n3 + 255) / 256, 256, 0, st>>>((const V *)u,
-                                                       (size_t)o.n3, o.n_blk,
-                                                       occ, rho);
+  if (sizeof(T) == 4)
+    k_density_c64<BO><<<(o.n3 + 255) / 256, 256, 0, st>>>(
+        (const float2 *)u, (size_t)o.n3, o.n_blk, occ, rho);
+  else
+    k_density<T, BO><<<(o.n3 + 255) / 256, 256, 0, st>>>((const V *)u,
+                                                         (size_t)o.n3, o.n_blk,
+                                                         occ, rho);
 }
 
 template <typename T, int BO, int M>
@@ -757,8 +1097,8 @@ void emd_launch_stage(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
   } else {
     switch (o.bo) {
       case 1: stage_m<float, 1>(o, a, st); break;
-      case 2: stage_z_m<2>(o, a, st); break;
-      case 4: stage_z_m<4>(o, a, st); break;
+      case 2: if (o.stage_variant == 1) stage_z_m<2>(o, a, st); else stage_zp_m<2>(o, a, st); break;
+      case 4: stage_z_m<4>(o, a, st); break;   // point-per-thread needs > 128 registers
     }
   }
 }

@@ -196,3 +196,30 @@ def test_fp32_hamiltonian_all_orders_and_blocks(order, bo):
     got = emd.emd_apply_hamiltonian(g.handle, u)
     g.close()
     assert rel(got, H.apply(u)) < 3e-6
+
+
+def test_fp32_density_is_fp64_accurate():
+    """complex64 orbitals: the density (compensated FP32 sums) equals the FP64
+    density of the same complex64 values to ~1e-13."""
+    s = inputs.small_system(n=24, h=0.3, fd_order=4, n_atoms=4, seed=17)
+    g = emd.System(s, emd.EMD_FP32_ORBITALS)
+    _, _, psi, rho = g.state()
+    g.close()
+    ref = s.occ * np.sum(psi.real.astype(np.float64) ** 2 + psi.imag.astype(np.float64) ** 2, axis=0)
+    assert np.max(np.abs(rho - ref)) <= 1e-12 * np.max(ref)
+
+
+@pytest.mark.parametrize("prec,tol", [(emd.EMD_FP64, 1e-13), (emd.EMD_FP32_ORBITALS, 1e-6)])
+def test_point_major_projections_equal_atom_major(prec, tol):
+    """The two projection forms (each 8^3 tile read once vs each atom
+    gathering its sphere) agree, on the tiny workload whose spheres overlap
+    their own periodic images."""
+    s = inputs.tiny_fp64()
+    out = []
+    for form in (0, 1):
+        g = emd.System(s, prec)
+        emd.emd_set_option(g.handle, emd.EMD_OPT_PROJECTION, form)
+        g.propagate(2)
+        out.append(emd.emd_get_projections(g.handle, s.n_atoms, s.n_orb))
+        g.close()
+    assert np.max(np.abs(out[0] - out[1])) <= tol * np.max(np.abs(out[1]))
