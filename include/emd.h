@@ -60,9 +60,10 @@ extern "C" {
 #define EMD_OPT_PROFILE      2  /* value != 0: time Horner-stage launches     */
 #define EMD_OPT_CHECK_STABLE 3  /* value == 0: skip the stability refusal    */
 #define EMD_OPT_STAGE_VARIANT 4 /* complex64 Horner-stage kernel for bo = 2:
-                                   0 one thread per grid point (default),
-                                   1 one thread per (point, orbital); bo = 4
-                                   always uses the latter                  */
+                                   0 one thread per (column, 2 rows), both
+                                   orbitals (default); 1 one thread per
+                                   (point, orbital) column; 2 one thread per
+                                   point.  bo = 4 always uses 1            */
 #define EMD_OPT_PROJECTION   5  /* projections <p_J|u>: 1 atom-major (each
                                    atom gathers its sphere, default), 0
                                    point-major (each 8^3 tile read once,

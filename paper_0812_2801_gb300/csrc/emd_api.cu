@@ -567,7 +567,8 @@ int emd_set_option(emd_system *s, int option, double value) {
       s->proj_atom_major = (int)value;
       return EMD_OK;
     case EMD_OPT_STAGE_VARIANT:
-      if (value != 0.0 && value != 1.0) return fail(EMD_EINVAL, "stage variant must be 0 or 1");
+      if (value != 0.0 && value != 1.0 && value != 2.0)
+        return fail(EMD_EINVAL, "stage variant must be 0, 1 or 2");
       s->o.stage_variant = (int)value;
       return EMD_OK;
   }

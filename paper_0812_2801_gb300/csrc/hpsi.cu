@@ -400,14 +400,18 @@ k_stage_z(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
 // orbitals and shared memory is read 16 bytes at a time.  Same 3-deep ring
 // and (2M+1)-slot delay line as k_stage_z.
 // ---------------------------------------------------------------------------
-template <int BO, int M> struct ZPTile {
-  static constexpr int TX = 32, TY = 16, NT = 512;
+template <int BO, int M, int RY> struct ZPTile {
+  static constexpr int TX = 32;                      // points per tile row
+  static constexpr int NT = RY == 1 ? 512 : 256;     // threads per CTA
+  static constexpr int TYT = NT / TX;                // thread rows
+  static constexpr int TY = TYT * RY;                // grid rows per tile
   static constexpr int SW = TX + 2 * M, SH = TY + 2 * M;
   static constexpr int PLANE = SH * SW * BO;
   static constexpr int CH = BO / 2;
   static constexpr int NCHUNK = SH * SW * CH;
   static constexpr int CPT = (NCHUNK + NT - 1) / NT;
-  static constexpr int NV = TX * TY;                       // == NT
+  static constexpr int NV = TX * TY;
+  static constexpr int VPT = (NV + NT - 1) / NT;             // v_eff values / thread
   static constexpr int QPT = (2 * NV + NT - 1) / NT;
   static constexpr int SPT = (NV * CH + NT - 1) / NT;
   static constexpr int NS = 2 * M + 1, NB = 3;
@@ -426,22 +430,24 @@ __device__ __forceinline__ void lds_point(const float2 *p, float2 (&v)[BO]) {
   }
 }
 
-template <int BO, int M>
-__global__ void __launch_bounds__(512, 1)
+// Each thread owns the bo orbitals of one grid column over RY consecutive
+// rows: y-neighbours come from a register window of RY + 2M points, x
+// neighbours from shared memory, 16 bytes at a time.
+template <int BO, int M, int RY>
+__global__ void __launch_bounds__(ZPTile<BO, M, RY>::NT, 1)
 k_stage_zp(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
            float2 *__restrict__ u_out, const float *__restrict__ v_eff,
            const int2 *__restrict__ pt4, const int *__restrict__ pt_J,
            const float *__restrict__ pt_pf, const float2 *__restrict__ hc,
            int n, int ntx, int zc, int n_orb_pad, int n_atoms, int hc_in_smem,
            float a, int apply_only, Weights<float> W) {
-  typedef ZPTile<BO, M> Z;
+  typedef ZPTile<BO, M, RY> Z;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2 *hcs = reinterpret_cast<float2 *>(smraw + Z::NB * Z::SLOT);
   const int tid = threadIdx.x;
-  const int xl = tid % Z::TX, yl = tid / Z::TX;
+  const int xl = tid % Z::TX, tyr = tid / Z::TX;
   const int tx0 = (blockIdx.x % ntx) * Z::TX, ty0 = (blockIdx.x / ntx) * Z::TY;
-  const int x = tx0 + xl, y = ty0 + yl;
-  const bool own = x < n && y < n;
+  const int x = tx0 + xl;
   const int z0 = blockIdx.y * zc;
   const int zcount = min(zc, n - z0);
   const int total = zcount + 2 * M;
@@ -467,8 +473,16 @@ k_stage_zp(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
       dst_off[i] = (rr * Z::SW + c) * BO + 2 * hh;
     }
   }
-  const int own_off = (min(y, n - 1) * n + min(x, n - 1));   // in-plane point index
-  const int v_src = (y % n) * n + x % n;
+  int v_src[Z::VPT];
+#pragma unroll
+  for (int i = 0; i < Z::VPT; ++i) {
+    const int q = tid + i * Z::NT;
+    v_src[i] = -1;
+    if (q < Z::NV) {
+      const int vx = q % Z::TX, vy = q / Z::TX;
+      v_src[i] = ((ty0 + vy) % n) * n + (tx0 + vx) % n;
+    }
+  }
   int q_src[Z::QPT], q_dst[Z::QPT];
 #pragma unroll
   for (int i = 0; i < Z::QPT; ++i) {
@@ -513,7 +527,10 @@ k_stage_zp(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
 #pragma unroll
     for (int i = 0; i < Z::CPT; ++i)
       if (src_off[i] >= 0) cp_async16(U + dst_off[i], src + src_off[i]);
-    cp_async4(V + tid, v_eff + (size_t)zz * n2 + v_src);
+    const float *vsrc = v_eff + (size_t)zz * n2;
+#pragma unroll
+    for (int i = 0; i < Z::VPT; ++i)
+      if (v_src[i] >= 0) cp_async4(V + tid + i * Z::NT, vsrc + v_src[i]);
     if (zi >= 2 * M) {
       const int zo = z0 + zi - 2 * M;
       const int2 *qs = pt4 + (size_t)zo * n2 * 4;
@@ -535,13 +552,15 @@ k_stage_zp(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
   for (int k = 0; k <= M; ++k) w2[k] = make_float2(W.w[k], W.w[k]);
   const float2 a2 = make_float2(a, -a);
 
-  float2 acc[BO][Z::NS];
+  float2 acc[RY][BO][Z::NS];
 #pragma unroll
-  for (int j = 0; j < BO; ++j)
+  for (int r = 0; r < RY; ++r)
 #pragma unroll
-    for (int q = 0; q < Z::NS; ++q) acc[j][q] = make_float2(0.f, 0.f);
+    for (int j = 0; j < BO; ++j)
+#pragma unroll
+      for (int q = 0; q < Z::NS; ++q) acc[r][j][q] = make_float2(0.f, 0.f);
 
-  const int cidx = ((yl + M) * Z::SW + xl + M) * BO;   // own point in a staged plane
+  const int cidx = ((tyr * RY + M) * Z::SW + xl + M) * BO;   // own row 0
   issue(0, 0);
   if (total > 1) issue(1, 1);
   int sb = 0;
@@ -561,102 +580,116 @@ k_stage_zp(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
       __syncthreads();
       const unsigned char *base = smraw + sb * Z::SLOT;
       const float2 *P = reinterpret_cast<const float2 *>(base) + cidx;
-      const float ve = reinterpret_cast<const float *>(base + Z::UB)[tid];
-      float2 c[BO], s2[BO];
-      lds_point<BO>(P, c);
+      const float *VP = reinterpret_cast<const float *>(base + Z::UB);
+      float2 win[RY + 2 * M][BO];
 #pragma unroll
-      for (int j = 0; j < BO; ++j) s2[j] = __fmul2_rn(w2[0], c[j]);
+      for (int w = 0; w < RY + 2 * M; ++w) lds_point<BO>(P + (w - M) * Z::SW * BO, win[w]);
 #pragma unroll
-      for (int k = 1; k <= M; ++k) {
+      for (int r = 0; r < RY; ++r) {
+        const float2 *Pr = P + r * Z::SW * BO;
+        float2 s2[BO];
 #pragma unroll
-        for (int h = 0; h < BO / 2; ++h) {
-          // two orbitals at a time: at most four 16-byte neighbour loads live
-          const float4 xp = reinterpret_cast<const float4 *>(P + k * BO)[h];
-          const float4 xm = reinterpret_cast<const float4 *>(P - k * BO)[h];
-          const float4 yp = reinterpret_cast<const float4 *>(P + k * Z::SW * BO)[h];
-          const float4 ym = reinterpret_cast<const float4 *>(P - k * Z::SW * BO)[h];
-          const float2 t0 = __fadd2_rn(__fadd2_rn(make_float2(xp.x, xp.y), make_float2(xm.x, xm.y)),
-                                       __fadd2_rn(make_float2(yp.x, yp.y), make_float2(ym.x, ym.y)));
-          const float2 t1 = __fadd2_rn(__fadd2_rn(make_float2(xp.z, xp.w), make_float2(xm.z, xm.w)),
-                                       __fadd2_rn(make_float2(yp.z, yp.w), make_float2(ym.z, ym.w)));
-          s2[2 * h] = __ffma2_rn(w2[k], t0, s2[2 * h]);
-          s2[2 * h + 1] = __ffma2_rn(w2[k], t1, s2[2 * h + 1]);
-        }
-      }
-      const float2 ve2 = make_float2(ve, ve);
-#pragma unroll
-      for (int j = 0; j < BO; ++j) {
-        s2[j] = __ffma2_rn(ve2, c[j], s2[j]);
-        acc[j][ph] = __fadd2_rn(acc[j][ph], s2[j]);
+        for (int j = 0; j < BO; ++j) s2[j] = __fmul2_rn(w2[0], win[r + M][j]);
 #pragma unroll
         for (int k = 1; k <= M; ++k) {
-          acc[j][(ph + k) % Z::NS] = __ffma2_rn(w2[k], c[j], acc[j][(ph + k) % Z::NS]);
-          if (g > 0 || ph - k >= 0)
-            acc[j][(ph - k + Z::NS) % Z::NS] =
-                __ffma2_rn(w2[k], c[j], acc[j][(ph - k + Z::NS) % Z::NS]);
+#pragma unroll
+          for (int h = 0; h < BO / 2; ++h) {
+            const float4 xp = reinterpret_cast<const float4 *>(Pr + k * BO)[h];
+            const float4 xm = reinterpret_cast<const float4 *>(Pr - k * BO)[h];
+            const float2 t0 = __fadd2_rn(__fadd2_rn(make_float2(xp.x, xp.y), make_float2(xm.x, xm.y)),
+                                         __fadd2_rn(win[r + M + k][2 * h], win[r + M - k][2 * h]));
+            const float2 t1 = __fadd2_rn(__fadd2_rn(make_float2(xp.z, xp.w), make_float2(xm.z, xm.w)),
+                                         __fadd2_rn(win[r + M + k][2 * h + 1], win[r + M - k][2 * h + 1]));
+            s2[2 * h] = __ffma2_rn(w2[k], t0, s2[2 * h]);
+            s2[2 * h + 1] = __ffma2_rn(w2[k], t1, s2[2 * h + 1]);
+          }
+        }
+        const float ve = VP[(tyr * RY + r) * Z::TX + xl];
+        const float2 ve2 = make_float2(ve, ve);
+#pragma unroll
+        for (int j = 0; j < BO; ++j) {
+          const float2 c = win[r + M][j];
+          s2[j] = __ffma2_rn(ve2, c, s2[j]);
+          acc[r][j][ph] = __fadd2_rn(acc[r][j][ph], s2[j]);
+#pragma unroll
+          for (int k = 1; k <= M; ++k) {
+            acc[r][j][(ph + k) % Z::NS] = __ffma2_rn(w2[k], c, acc[r][j][(ph + k) % Z::NS]);
+            if (g > 0 || ph - k >= 0)
+              acc[r][j][(ph - k + Z::NS) % Z::NS] =
+                  __ffma2_rn(w2[k], c, acc[r][j][(ph - k + Z::NS) % Z::NS]);
+          }
         }
       }
       if (zi >= M) {
         const int slot = (ph - M + Z::NS) % Z::NS;
-        if (zi >= 2 * M && own) {
+        if (zi >= 2 * M) {
           const int zo = z0 + zi - 2 * M;
           const int4 *Q4 = reinterpret_cast<const int4 *>(base + Z::UB + Z::VB);
-          const int4 q01 = Q4[2 * tid], q23 = Q4[2 * tid + 1];
-          const int cnt = q01.x >> 16;
-          const int J[4] = {q01.x & 0xffff, q01.z, q23.x, q23.z};
-          const float pv[4] = {__int_as_float(q01.y), __int_as_float(q01.w),
-                               __int_as_float(q23.y), __int_as_float(q23.w)};
-          float2 hv[BO];
+          const float2 *Sb = reinterpret_cast<const float2 *>(base + Z::UB + Z::VB + Z::QB);
 #pragma unroll
-          for (int j = 0; j < BO; ++j) hv[j] = acc[j][slot];
+          for (int r = 0; r < RY; ++r) {
+            const int vy = tyr * RY + r, y = ty0 + vy;
+            if (x < n && y < n) {
+              const int pnt = vy * Z::TX + xl;
+              const int4 q01 = Q4[2 * pnt], q23 = Q4[2 * pnt + 1];
+              const int cnt = q01.x >> 16;
+              const int J[4] = {q01.x & 0xffff, q01.z, q23.x, q23.z};
+              const float pv[4] = {__int_as_float(q01.y), __int_as_float(q01.w),
+                                   __int_as_float(q23.y), __int_as_float(q23.w)};
+              float2 hv[BO];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            float2 hcv[BO];
-            if (hc_in_smem) {
-              lds_point<BO>(hcs + J[e] * BO, hcv);
-            } else {
+              for (int j = 0; j < BO; ++j) hv[j] = acc[r][j][slot];
 #pragma unroll
-              for (int j = 0; j < BO; ++j)
-                hcv[j] = __ldg(hc + (size_t)J[e] * n_orb_pad + (size_t)blk * BO + j);
+              for (int e = 0; e < 4; ++e) {
+                float2 hcv[BO];
+                if (hc_in_smem) {
+                  lds_point<BO>(hcs + J[e] * BO, hcv);
+                } else {
+#pragma unroll
+                  for (int j = 0; j < BO; ++j)
+                    hcv[j] = __ldg(hc + (size_t)J[e] * n_orb_pad + (size_t)blk * BO + j);
+                }
+                const float2 p2 = make_float2(pv[e], pv[e]);
+#pragma unroll
+                for (int j = 0; j < BO; ++j) hv[j] = __ffma2_rn(p2, hcv[j], hv[j]);
+              }
+              const size_t p = (size_t)zo * n2 + (size_t)y * n + x;
+              for (int e = 4; e < cnt; ++e) {
+                const int Je = __ldg(pt_J + (size_t)e * n3 + p);
+                const float pe = __ldg(pt_pf + (size_t)e * n3 + p);
+                const float2 p2 = make_float2(pe, pe);
+#pragma unroll
+                for (int j = 0; j < BO; ++j) {
+                  const float2 hcv = hc_in_smem ? hcs[Je * BO + j]
+                      : __ldg(hc + (size_t)Je * n_orb_pad + (size_t)blk * BO + j);
+                  hv[j] = __ffma2_rn(p2, hcv, hv[j]);
+                }
+              }
+              float2 out[BO];
+              if (apply_only) {
+#pragma unroll
+                for (int j = 0; j < BO; ++j) out[j] = hv[j];
+              } else {
+                float2 s0[BO];
+                lds_point<BO>(Sb + pnt * BO, s0);
+#pragma unroll
+                for (int j = 0; j < BO; ++j)
+                  out[j] = __ffma2_rn(a2, make_float2(hv[j].y, hv[j].x), s0[j]);
+              }
+              float4 *dst = reinterpret_cast<float4 *>(ob + p * BO);
+#pragma unroll
+              for (int h = 0; h < BO / 2; ++h)
+                dst[h] = make_float4(out[2 * h].x, out[2 * h].y, out[2 * h + 1].x, out[2 * h + 1].y);
             }
-            const float2 p2 = make_float2(pv[e], pv[e]);
-#pragma unroll
-            for (int j = 0; j < BO; ++j) hv[j] = __ffma2_rn(p2, hcv[j], hv[j]);
           }
-          const size_t p = (size_t)zo * n2 + own_off;
-          for (int e = 4; e < cnt; ++e) {
-            const int Je = __ldg(pt_J + (size_t)e * n3 + p);
-            const float pe = __ldg(pt_pf + (size_t)e * n3 + p);
-            const float2 p2 = make_float2(pe, pe);
-#pragma unroll
-            for (int j = 0; j < BO; ++j) {
-              const float2 hcv = hc_in_smem ? hcs[Je * BO + j]
-                  : __ldg(hc + (size_t)Je * n_orb_pad + (size_t)blk * BO + j);
-              hv[j] = __ffma2_rn(p2, hcv, hv[j]);
-            }
-          }
-          float2 out[BO];
-          if (apply_only) {
-#pragma unroll
-            for (int j = 0; j < BO; ++j) out[j] = hv[j];
-          } else {
-            float2 s0[BO];
-            lds_point<BO>(reinterpret_cast<const float2 *>(base + Z::UB + Z::VB + Z::QB) + tid * BO, s0);
-#pragma unroll
-            for (int j = 0; j < BO; ++j)
-              out[j] = __ffma2_rn(a2, make_float2(hv[j].y, hv[j].x), s0[j]);
-          }
-          float4 *dst = reinterpret_cast<float4 *>(ob + p * BO);
-#pragma unroll
-          for (int h = 0; h < BO / 2; ++h)
-            dst[h] = make_float4(out[2 * h].x, out[2 * h].y, out[2 * h + 1].x, out[2 * h + 1].y);
         }
 #pragma unroll
-        for (int j = 0; j < BO; ++j) {
+        for (int r = 0; r < RY; ++r)
 #pragma unroll
-          for (int q = 0; q < Z::NS; ++q)
-            if (q == slot) acc[j][q] = make_float2(0.f, 0.f);
-        }
+          for (int j = 0; j < BO; ++j)
+#pragma unroll
+            for (int q = 0; q < Z::NS; ++q)
+              if (q == slot) acc[r][j][q] = make_float2(0.f, 0.f);
       }
       __syncthreads();
       sb = sb == 2 ? 0 : sb + 1;
@@ -951,15 +984,15 @@ void stage_z_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
       (float)a.a, a.apply_only, weights_of<float>(o));
 }
 
-template <int BO, int M>
+template <int BO, int M, int RY>
 void stage_zp_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
-  typedef ZPTile<BO, M> Z;
+  typedef ZPTile<BO, M, RY> Z;
   const int hc_bytes = o.n_atoms * BO * (int)sizeof(float2);
   const int hc_in_smem = hc_bytes <= 16384;
   const size_t smem = Z::SMEM_FIXED + (hc_in_smem ? hc_bytes : 0);
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(k_stage_zp<BO, M>,
+    cudaFuncSetAttribute(k_stage_zp<BO, M, RY>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(Z::SMEM_FIXED + 16384));
     attr_done = true;
@@ -967,20 +1000,20 @@ void stage_zp_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
   const int ntx = (o.n + Z::TX - 1) / Z::TX, nty = (o.n + Z::TY - 1) / Z::TY;
   const int zc = o.n <= 64 ? o.n : (o.n + 1) / 2 <= 64 ? (o.n + 1) / 2 : 48;
   dim3 grid(ntx * nty, (o.n + zc - 1) / zc, o.n_blk);
-  k_stage_zp<BO, M><<<grid, Z::NT, smem, st>>>(
+  k_stage_zp<BO, M, RY><<<grid, Z::NT, smem, st>>>(
       (const float2 *)a.u_in, (const float2 *)a.psi0, (float2 *)a.u_out,
       (const float *)a.v_eff, a.tab->pt4, a.tab->pt_J, a.tab->pt_pf,
       (const float2 *)a.hc, o.n, ntx, zc, o.n_orb_pad, o.n_atoms, hc_in_smem,
       (float)a.a, a.apply_only, weights_of<float>(o));
 }
 
-template <int BO>
+template <int BO, int RY>
 void stage_zp_m(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
   switch (o.half_order) {
-    case 1: stage_zp_t<BO, 1>(o, a, st); break;
-    case 2: stage_zp_t<BO, 2>(o, a, st); break;
-    case 3: stage_zp_t<BO, 3>(o, a, st); break;
-    case 4: stage_zp_t<BO, 4>(o, a, st); break;
+    case 1: stage_zp_t<BO, 1, RY>(o, a, st); break;
+    case 2: stage_zp_t<BO, 2, RY>(o, a, st); break;
+    case 3: stage_zp_t<BO, 3, RY>(o, a, st); break;
+    case 4: stage_zp_t<BO, 4, RY>(o, a, st); break;
   }
 }
 
@@ -1097,7 +1130,11 @@ void emd_launch_stage(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
   } else {
     switch (o.bo) {
       case 1: stage_m<float, 1>(o, a, st); break;
-      case 2: if (o.stage_variant == 1) stage_z_m<2>(o, a, st); else stage_zp_m<2>(o, a, st); break;
+      case 2:
+        if (o.stage_variant == 1) stage_z_m<2>(o, a, st);
+        else if (o.stage_variant == 2) stage_zp_m<2, 1>(o, a, st);
+        else stage_zp_m<2, 2>(o, a, st);
+        break;
       case 4: stage_z_m<4>(o, a, st); break;   // point-per-thread needs > 128 registers
     }
   }
