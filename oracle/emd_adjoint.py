@@ -222,3 +222,132 @@ def gradients(sysin, field, n_steps, dt, mu, kind: str):
     L = observable(sysin, R, f, n_steps, dt, mu, kind)
     gR, gf = torch.autograd.grad(L, [R, f])
     return float(L.detach()), gR.numpy(), gf.numpy()
+
+
+# --------------------------------------------------------------------------
+# Moving ions: the full MD step (velocity Verlet, forces = -dE_KS/dR at fixed
+# orbitals, Sec. 5.1 and eq. new_EoM_b) restated in PyTorch.  The supports at
+# each step's positions are taken from the numpy oracle's own trajectory (the
+# integer decisions), the values on them are differentiable.
+# --------------------------------------------------------------------------
+
+class TorchMD(TorchStep):
+    def __init__(self, sysin, n_steps, dt, mu, field):
+        super().__init__(sysin)
+        self.n_steps, self.dt, self.mu = n_steps, dt, mu
+        self.field_np = np.zeros(n_steps) if field is None else np.array(field, dtype=np.float64)
+        # trajectory of the numpy oracle -> supports at every step
+        self.sup = []
+        st = O.init_state(sysin)
+        self.sup.append(_support_tensors(st.tables) + (torch.as_tensor(np.array(st.R)),))
+        for i in range(n_steps):
+            st = O.md_step(st, dt, mu, float(self.field_np[i]))
+            self.sup.append(_support_tensors(st.tables) + (torch.as_tensor(np.array(st.R)),))
+
+    def _use(self, k):
+        self.loc, self.proj, self.R0 = self.sup[k]
+
+    def forces(self, R, psi, v_es, pvals):
+        sp, h3 = self.sp, self.h ** 3
+        na = R.shape[0]
+        F = []
+        vflat = v_es.reshape(-1)
+        cs = self.projections(psi, pvals)
+        flat = psi.reshape(psi.shape[0], -1)
+        rc2 = sp.r_c ** 2
+        for J in range(na):
+            idx, d0 = self.loc[J]
+            d = self._disp(d0, R, J)
+            d2 = (d * d).sum(1)
+            g = sp.z * math.pi ** -1.5 * sp.a_loc ** -3 * torch.exp(-d2 / sp.a_loc ** 2)
+            floc = h3 * ((vflat[idx] * g * (2.0 / sp.a_loc ** 2))[:, None] * d).sum(0)
+            pidx, pd0 = self.proj[J]
+            pdd = self._disp(pd0, R, J)
+            pp = math.pi ** -0.75 * sp.r_c ** -1.5 * torch.exp(-(pdd * pdd).sum(1) / (2 * rc2))
+            u = flat[:, pidx]
+            dc = h3 * (u[:, :, None] * (pp[:, None] * pdd / rc2)[None].to(u.dtype)).sum(1)
+            fnl = -2.0 * sp.h_kb * self.s.occ * (cs[J].conj()[:, None] * dc).real.sum(0)
+            F.append(floc + fnl)
+        F = torch.stack(F)
+        return F + self.short_range_force(R)
+
+    def short_range_force(self, R, r_cut=12.0):
+        sp = self.sp
+        L = self.L
+        s = math.sqrt(2.0) * sp.a_loc
+        nmax = int(math.ceil(r_cut / L)) + 1
+        Rw = R - L * torch.floor(R / L).detach()
+        rng = torch.arange(-nmax, nmax + 1, dtype=torch.float64)
+        img = torch.stack(torch.meshgrid(rng, rng, rng, indexing="ij"), -1).reshape(-1, 3) * L
+        out = []
+        zz = sp.z ** 2
+        for j in range(R.shape[0]):
+            dv = (Rw[j][None, None, :] - Rw[:, None, :] - img[None, :, :]).reshape(-1, 3)
+            d2 = (dv * dv).sum(1)
+            keep = (d2.detach() < r_cut * r_cut) & (d2.detach() > 0.0)
+            dk = torch.sqrt(d2[keep])
+            dvk = dv[keep]
+            ef = torch.special.erfc(dk / s) / dk
+            fm = zz * (ef / dk + 2.0 / (s * math.sqrt(math.pi)) * torch.exp(-dk * dk / (s * s)) / dk)
+            out.append(((fm / dk)[:, None] * dvk).sum(0))
+        return torch.stack(out)
+
+    def run_md(self, R, V, field):
+        sp, dt, mu = self.sp, self.dt, self.mu
+        M = sp.mass
+        tau = 0.5 * (dt / mu)
+        psi = torch.as_tensor(np.array(self.s.psi))
+        self._use(0)
+        g = self.ion_charge(R)
+        v_loc = self.poisson(-g)
+        pv = self.projector_values(R)
+        rho = self.density(psi)
+        _, vxc = self.lda(rho)
+        vh = self.poisson(rho)
+        hist = [vh + vxc]
+        F = self.forces(R, psi, vh + v_loc, pv)
+        for i in range(self.n_steps):
+            e = field[i]
+            R_new = R + V * dt + F * (dt * dt / (2.0 * M))
+            self._use(i + 1)
+            g_new = self.ion_charge(R_new)
+            v_loc_new = self.poisson(-g_new)
+            pv_new = self.projector_values(R_new)
+            if len(hist) == 1:
+                x = hist[0]
+            elif len(hist) == 2:
+                x = 2.0 * hist[0] - hist[1]
+            else:
+                x = 3.0 * hist[0] - 3.0 * hist[1] + hist[2]
+            self._use(i)
+            psi1 = self.taylor4(psi, tau, v_loc + hist[0] + e * self.saw, pv)
+            self._use(i + 1)
+            psi = self.taylor4(psi1, tau, v_loc_new + x + e * self.saw, pv_new)
+            rho = self.density(psi)
+            _, vxc = self.lda(rho)
+            vh = self.poisson(rho)
+            hist = [vh + vxc] + hist[:2]
+            F_new = self.forces(R_new, psi, vh + v_loc_new, pv_new)
+            F_new = F_new + torch.stack([torch.zeros_like(e), torch.zeros_like(e), sp.z * e])[None, :]
+            V = V + (F + F_new) * (dt / (2.0 * M))
+            R, F, g, v_loc, pv = R_new, F_new, g_new, v_loc_new, pv_new
+        return psi, rho, g, v_loc, pv, R, V
+
+    def total_energy(self, psi, rho, g, v_loc, pv, R, V):
+        return self.energy_ks(R, psi, rho, g, v_loc, pv) + 0.5 * self.sp.mass * (V * V).sum()
+
+
+def gradients_md(sysin, field, n_steps, dt, mu, kind: str):
+    """(L, dL/dR(0), dL/dfield) for the moving-ion dynamics; kind 'dipole'
+    (final D_z) or 'energy' (final E_KS + sum M V^2 / 2)."""
+    T = TorchMD(sysin, n_steps, dt, mu, field)
+    R = torch.as_tensor(np.array(sysin.R)).clone().requires_grad_(True)
+    V = torch.as_tensor(np.array(sysin.V))
+    f = torch.as_tensor(np.array(T.field_np)).clone().requires_grad_(True)
+    psi, rho, g, v_loc, pv, Rn, Vn = T.run_md(R, V, f)
+    if kind == "dipole":
+        L = T.dipole(Rn, rho)
+    else:
+        L = T.total_energy(psi, rho, g, v_loc, pv, Rn, Vn)
+    gR, gf = torch.autograd.grad(L, [R, f])
+    return float(L.detach()), gR.numpy(), gf.numpy()
