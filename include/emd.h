@@ -196,21 +196,26 @@ int emd_kernel_stats(emd_system *s, int kernel, double *ms_total,
 /* Adjoint (backward-in-time) propagation.  The paper gives the forward
  * dynamics only (Sec. 4.1, eq. new_EoM; Sec. 5.1, eq. aetrs); this is the
  * exact discrete adjoint of the implemented step, for gradient-based uses of
- * the trajectory (field optimisation, sensitivities).  Built for fixed ions
- * (EMD_OPT_FROZEN_IONS set) and FP64 orbitals: the electrons evolve
- * self-consistently (density -> Hartree + LDA -> extrapolated H(t+dt)) under
- * the field e_n; the gradient is taken with respect to the static ion
- * positions and every e_n.
+ * the trajectory (field optimisation, sensitivities).  FP64 orbitals only.
+ * The electrons evolve self-consistently (density -> Hartree + LDA ->
+ * extrapolated H(t+dt)) under the field e_n.  With EMD_OPT_FROZEN_IONS set
+ * the ions stay at their positions; otherwise they move by velocity Verlet
+ * under the forces of eq. new_EoM_b plus Z e_n along z, and the reverse
+ * sweep also runs through the forces (their orbital, potential and position
+ * dependence) and the Verlet updates.  The gradient is taken with respect to
+ * the initial ion positions R(0) (velocities held) and every e_n.
  *   observable EMD_OBS_DIPOLE_Z: L = -h^3 sum rho (z - L/2) + sum_J Z (Z_J - L/2)
- *   observable EMD_OBS_ENERGY:   L = E_KS of the final state (eq. E_KS)
- * Runs n_steps forward from the current state (storing orbitals and the
- * v_Hxc history every ckpt_every steps), then backward segment by segment,
- * recomputing each segment's steps from its checkpoint.  On return the
- * system is at the final state; *L_out = L, dL_dR[n_atoms][3],
+ *   observable EMD_OBS_ENERGY:   L = E_KS of the final state (eq. E_KS), plus
+ *                                sum_J M V_J^2 / 2 when the ions move
+ * Runs n_steps forward from the current state (storing orbitals, the v_Hxc
+ * history and the ions' R, V, F every ckpt_every steps), then backward
+ * segment by segment, recomputing each segment's steps from its checkpoint.
+ * On return the system is at the final state; *L_out = L, dL_dR[n_atoms][3],
  * dL_dfield[n_steps] (may be NULL if field is NULL).  Device workspace
  * (about (n_steps/ckpt_every + ckpt_every + 13) orbital sets) is allocated
- * on first use and kept until emd_destroy.  Synchronises.
- * Errors: EMD_EINVAL, EMD_ESTATE (ions not fixed), EMD_ENOMEM, EMD_ECUDA. */
+ * on first use and kept until emd_destroy.  Synchronises (once per reverse
+ * step with moving ions).
+ * Errors: EMD_EINVAL, EMD_ESTATE, EMD_ENOMEM, EMD_ECUDA, EMD_ETABLE. */
 #define EMD_OBS_ENERGY   0
 #define EMD_OBS_DIPOLE_Z 1
 int emd_propagate_adjoint(emd_system *s, int n_steps, double dt, double mu,

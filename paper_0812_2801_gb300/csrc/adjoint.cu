@@ -230,3 +230,273 @@ void emd_adj_lincomb(int n, double *out, double a0, const double *x0, double a1,
   emd_note_launches(1);
   k_lincomb<<<(n + 255) / 256, 256, 0, st>>>(n, out, a0, x0, a1, x1, a2, x2, a3, x3);
 }
+
+// ===========================================================================
+// Moving ions: reverse of the force F(psi, R, v_es) (eq. new_EoM_b) used by
+// velocity Verlet.  With lam_F the adjoint of the forces:
+//   splat   w(r)   = h^3 sum_J lam_J . g_J(r) 2 d / a^2      (dL/dv_es)
+//   loc HVP dL/dR_J += h^3 sum_r v_es g_J (-2/a^2) [lam_J - 2 d (d.lam_J)/a^2]
+//   nl orb  Lam(r) += -2 h_kb f h^3 sum_J [p_J alpha_J + (lam_J . dp_J) c_J]
+//           alpha_J = lam_J . dc_J,  dp_J = p_J d / r_c^2
+//   nl R    second moments m_b = h^3 sum p [(lam.d) d_b / r_c^4 - lam_b / r_c^2] u
+//   sr HVP  dL/dR_m += sum_{K,n} Jac(D_mKn) (lam_m - lam_K)
+// ===========================================================================
+namespace {
+
+// w(r) for every grid point from the (atom, image) candidates of its tile.
+__global__ void __launch_bounds__(512)
+k_force_splat(int n, double h, double L, const double *Rw, SpeciesDev sp,
+              const int *tile_cnt, const int *tile_ent, const double *lamF,
+              double *w) {
+  __shared__ int cand[EMD_TILE_CAND_MAX];
+  const int nt = (n + EMD_TILE - 1) / EMD_TILE;
+  const int t = blockIdx.x;
+  const int tx = t % nt, ty = (t / nt) % nt, tz = t / (nt * nt);
+  const int nc = tile_cnt[t];
+  for (int i = threadIdx.x; i < nc; i += blockDim.x)
+    cand[i] = tile_ent[t * EMD_TILE_CAND_MAX + i];
+  __syncthreads();
+  const int x = tx * EMD_TILE + (threadIdx.x & 7);
+  const int y = ty * EMD_TILE + ((threadIdx.x >> 3) & 7);
+  const int z = tz * EMD_TILE + (threadIdx.x >> 6);
+  if (x >= n || y >= n || z >= n) return;
+  const double rl2 = __dmul_rn(sp.r_loc, sp.r_loc);
+  const double h3 = h * h * h;
+  double acc = 0.0;
+  for (int e = 0; e < nc; ++e) {
+    const int J = cand[e] / 27, img = cand[e] % 27;
+    const double dx = emd_disp(x, h, Rw[3 * J + 0], img % 3 - 1, L);
+    const double dy = emd_disp(y, h, Rw[3 * J + 1], (img / 3) % 3 - 1, L);
+    const double dz = emd_disp(z, h, Rw[3 * J + 2], img / 9 - 1, L);
+    const double d2 = emd_norm2(dx, dy, dz);
+    if (d2 < rl2) {
+      const double g = sp.c_g * exp(-d2 * sp.inv_a2) * (2.0 * sp.inv_a2);
+      acc += g * (lamF[3 * J] * dx + lamF[3 * J + 1] * dy + lamF[3 * J + 2] * dz);
+    }
+  }
+  w[((size_t)z * n + y) * n + x] = h3 * acc;
+}
+
+// Orbital term of the nonlocal-force adjoint, added to lam (orbital layout).
+// coef = -2 h_kb f h^3; cc[J][A] = c_JA, dc[J][A][b] = dc_JA,b, and
+// alpha_JA = lam_J . dc_JA is formed on the fly.
+template <int BO>
+__global__ void __launch_bounds__(512)
+k_nl_force_adj_orb(int n, double h, double L, const double *Rw, SpeciesDev sp,
+                   const int *tile_cnt, const int *tile_ent, const double *lamF,
+                   const double2 *dc, const double2 *cc, int n_orb_pad,
+                   double coef, double2 *lam) {
+  __shared__ int cand[EMD_TILE_CAND_MAX];
+  const int nt = (n + EMD_TILE - 1) / EMD_TILE;
+  const int t = blockIdx.x, blk = blockIdx.y;
+  const int tx = t % nt, ty = (t / nt) % nt, tz = t / (nt * nt);
+  const int nc = tile_cnt[t];
+  for (int i = threadIdx.x; i < nc; i += blockDim.x)
+    cand[i] = tile_ent[t * EMD_TILE_CAND_MAX + i];
+  __syncthreads();
+  const int x = tx * EMD_TILE + (threadIdx.x & 7);
+  const int y = ty * EMD_TILE + ((threadIdx.x >> 3) & 7);
+  const int z = tz * EMD_TILE + (threadIdx.x >> 6);
+  if (x >= n || y >= n || z >= n) return;
+  const double rp2 = __dmul_rn(sp.r_proj, sp.r_proj);
+  double2 acc[BO];
+#pragma unroll
+  for (int j = 0; j < BO; ++j) acc[j] = make_double2(0.0, 0.0);
+  for (int e = 0; e < nc; ++e) {
+    const int J = cand[e] / 27, img = cand[e] % 27;
+    const double dx = emd_disp(x, h, Rw[3 * J + 0], img % 3 - 1, L);
+    const double dy = emd_disp(y, h, Rw[3 * J + 1], (img / 3) % 3 - 1, L);
+    const double dz = emd_disp(z, h, Rw[3 * J + 2], img / 9 - 1, L);
+    const double d2 = emd_norm2(dx, dy, dz);
+    if (d2 < rp2) {
+      const double p = sp.c_p * exp(-d2 * sp.inv_2rc2);
+      const double ld = p * sp.inv_rc2 *
+                        (lamF[3 * J] * dx + lamF[3 * J + 1] * dy + lamF[3 * J + 2] * dz);
+#pragma unroll
+      for (int j = 0; j < BO; ++j) {
+        const size_t o = (size_t)J * n_orb_pad + (size_t)blk * BO + j;
+        const double2 d0 = dc[3 * o], d1 = dc[3 * o + 1], d2v = dc[3 * o + 2];
+        const double2 a = make_double2(
+            lamF[3 * J] * d0.x + lamF[3 * J + 1] * d1.x + lamF[3 * J + 2] * d2v.x,
+            lamF[3 * J] * d0.y + lamF[3 * J + 1] * d1.y + lamF[3 * J + 2] * d2v.y);
+        const double2 c = cc[o];
+        acc[j].x += p * a.x + ld * c.x;
+        acc[j].y += p * a.y + ld * c.y;
+      }
+    }
+  }
+  const size_t n3 = (size_t)n * n * n;
+  const size_t pidx = ((size_t)z * n + y) * n + x;
+  double2 *lb = lam + ((size_t)blk * n3 + pidx) * BO;
+#pragma unroll
+  for (int j = 0; j < BO; ++j) {
+    lb[j].x += coef * acc[j].x;
+    lb[j].y += coef * acc[j].y;
+  }
+}
+
+// m[J][A][b] = h^3 sum_e p_e [(lam_J . d) d_b / r_c^4 - lam_J,b / r_c^2] u_A
+template <int BO>
+__global__ void __launch_bounds__(256)
+k_nl_second_moment(const double2 *__restrict__ u, size_t n3, const int *at_cnt,
+                   const int *at_pt, const double *at_p, const double *at_d,
+                   int cap, double h3, double inv_rc2, const double *lamF,
+                   int n_orb_pad, double2 *m) {
+  __shared__ double red[8 * 6 * BO];
+  const int J = blockIdx.x, blk = blockIdx.y;
+  const int cnt = at_cnt[J];
+  const double2 *ub = u + (size_t)blk * n3 * BO;
+  const double l0 = lamF[3 * J], l1 = lamF[3 * J + 1], l2 = lamF[3 * J + 2];
+  double acc[6 * BO];
+#pragma unroll
+  for (int k = 0; k < 6 * BO; ++k) acc[k] = 0.0;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const size_t idx = (size_t)J * cap + e;
+    const int pt = at_pt[idx];
+    const double pv = at_p[idx];
+    const double d0 = at_d[3 * idx], d1 = at_d[3 * idx + 1], d2 = at_d[3 * idx + 2];
+    const double ld = (l0 * d0 + l1 * d1 + l2 * d2) * inv_rc2 * inv_rc2;
+    const double w0 = pv * (ld * d0 - l0 * inv_rc2);
+    const double w1 = pv * (ld * d1 - l1 * inv_rc2);
+    const double w2 = pv * (ld * d2 - l2 * inv_rc2);
+#pragma unroll
+    for (int j = 0; j < BO; ++j) {
+      const double2 v = ub[(size_t)pt * BO + j];
+      acc[6 * j + 0] += w0 * v.x;
+      acc[6 * j + 1] += w0 * v.y;
+      acc[6 * j + 2] += w1 * v.x;
+      acc[6 * j + 3] += w1 * v.y;
+      acc[6 * j + 4] += w2 * v.x;
+      acc[6 * j + 5] += w2 * v.y;
+    }
+  }
+  emd_block_sum<6 * BO>(acc, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < BO; ++j) {
+      const size_t o = (size_t)J * n_orb_pad + (size_t)blk * BO + j;
+      for (int b = 0; b < 3; ++b)
+        m[3 * o + b] = make_double2(h3 * acc[6 * j + 2 * b], h3 * acc[6 * j + 2 * b + 1]);
+    }
+  }
+}
+
+// Position term of the nonlocal-force adjoint:
+// out[J][b] = coef Re sum_A [conj(dc_JA,b) alpha_JA + conj(c_JA) m_JA,b],
+// coef = -2 h_kb f, alpha_JA = lam_J . dc_JA.  One thread per (J, b), the
+// orbital sum in fixed order.
+__global__ void k_nl_force_adj_r(const double2 *cc, const double2 *dc,
+                                 const double2 *m, const double *lamF,
+                                 int n_atoms, int n_orb, int n_orb_pad,
+                                 double coef, double *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * n_atoms) return;
+  const int J = i / 3, b = i % 3;
+  const double l0 = lamF[3 * J], l1 = lamF[3 * J + 1], l2 = lamF[3 * J + 2];
+  double s = 0.0;
+  for (int A = 0; A < n_orb; ++A) {
+    const size_t o = (size_t)J * n_orb_pad + A;
+    const double2 d0 = dc[3 * o], d1 = dc[3 * o + 1], d2 = dc[3 * o + 2];
+    const double ax = l0 * d0.x + l1 * d1.x + l2 * d2.x;
+    const double ay = l0 * d0.y + l1 * d1.y + l2 * d2.y;
+    const double2 db = dc[3 * o + b], c = cc[o], mb = m[3 * o + b];
+    s += (db.x * ax + db.y * ay) + (c.x * mb.x + c.y * mb.y);
+  }
+  out[i] = coef * s;
+}
+
+// sum_{K,n} Jac(D)(lam_m - lam_K), Jac = Z^2 [psi(d) I + psi'(d) D D^T / d],
+// psi = phi / d, phi(d) = erfc(d/s)/d^2 + 2/(s sqrt(pi)) exp(-d^2/s^2)/d.
+__global__ void __launch_bounds__(256)
+k_sr_hvp(SpeciesDev sp, int n_atoms, const double *Rw, double L, int nmax,
+         const double *lamF, double *out) {
+  __shared__ double red[8 * 3];
+  const int m = blockIdx.x;
+  const double s = sqrt(2.0) * sp.a_loc;
+  const double zz = sp.z * sp.z;
+  const double k2 = 2.0 / (s * sqrt(M_PI));
+  const int side = 2 * nmax + 1, nimg = side * side * side;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int q = threadIdx.x; q < n_atoms * nimg; q += blockDim.x) {
+    const int K = q / nimg, im = q % nimg;
+    const int nx = im % side - nmax, ny = (im / side) % side - nmax,
+              nz = im / (side * side) - nmax;
+    if (K == m && nx == 0 && ny == 0 && nz == 0) continue;
+    const double D0 = Rw[3 * m] - Rw[3 * K] - nx * L;
+    const double D1 = Rw[3 * m + 1] - Rw[3 * K + 1] - ny * L;
+    const double D2 = Rw[3 * m + 2] - Rw[3 * K + 2] - nz * L;
+    const double d2 = D0 * D0 + D1 * D1 + D2 * D2;
+    if (d2 >= 144.0 || d2 <= 0.0) continue;
+    const double d = sqrt(d2);
+    const double ex = exp(-d2 / (s * s));
+    const double ef = erfc(d / s);
+    const double phi = ef / d2 + k2 * ex / d;
+    const double dphi = -k2 * ex / d2 - 2.0 * ef / (d2 * d) + k2 * ex * (-2.0 / (s * s) - 1.0 / d2);
+    const double psi = phi / d;
+    const double dpsi = (dphi * d - phi) / d2;
+    const double l0 = lamF[3 * m] - lamF[3 * K], l1 = lamF[3 * m + 1] - lamF[3 * K + 1],
+                 l2 = lamF[3 * m + 2] - lamF[3 * K + 2];
+    const double Dl = (D0 * l0 + D1 * l1 + D2 * l2) * dpsi / d;
+    acc[0] += zz * (psi * l0 + Dl * D0);
+    acc[1] += zz * (psi * l1 + Dl * D1);
+    acc[2] += zz * (psi * l2 + Dl * D2);
+  }
+  emd_block_sum<3>(acc, red);
+  if (threadIdx.x == 0)
+    for (int a = 0; a < 3; ++a) out[3 * m + a] = acc[a];
+}
+
+}  // namespace
+
+void emd_adj_force_splat(const GridInfo &g, const SpeciesDev &sp, const TableSet &t,
+                         const double *lamF, double *w, cudaStream_t st) {
+  const int nt = (g.n + EMD_TILE - 1) / EMD_TILE;
+  emd_note_launches(1);
+  k_force_splat<<<nt * nt * nt, 512, 0, st>>>(g.n, g.h, g.L, t.Rw, sp, t.tile_cnt,
+                                              t.tile_ent, lamF, w);
+}
+
+void emd_adj_nl_force_orb(const OrbLayout &o, const GridInfo &g, const SpeciesDev &sp,
+                          const TableSet &t, const double *lamF, const double2 *dc,
+                          const double2 *cc, double coef, double2 *lam,
+                          cudaStream_t st) {
+  const int nt = (g.n + EMD_TILE - 1) / EMD_TILE;
+  dim3 grid(nt * nt * nt, o.n_blk);
+  emd_note_launches(1);
+  switch (o.bo) {
+    case 1: k_nl_force_adj_orb<1><<<grid, 512, 0, st>>>(g.n, g.h, g.L, t.Rw, sp, t.tile_cnt, t.tile_ent, lamF, dc, cc, o.n_orb_pad, coef, lam); break;
+    case 2: k_nl_force_adj_orb<2><<<grid, 512, 0, st>>>(g.n, g.h, g.L, t.Rw, sp, t.tile_cnt, t.tile_ent, lamF, dc, cc, o.n_orb_pad, coef, lam); break;
+    case 4: k_nl_force_adj_orb<4><<<grid, 512, 0, st>>>(g.n, g.h, g.L, t.Rw, sp, t.tile_cnt, t.tile_ent, lamF, dc, cc, o.n_orb_pad, coef, lam); break;
+  }
+}
+
+void emd_adj_nl_second_moment(const OrbLayout &o, const TableSet &t, int n_atoms,
+                              const double2 *u, double h3, double inv_rc2,
+                              const double *lamF, double2 *m, cudaStream_t st) {
+  if (n_atoms <= 0) return;
+  dim3 grid(n_atoms, o.n_blk);
+  emd_note_launches(1);
+  switch (o.bo) {
+    case 1: k_nl_second_moment<1><<<grid, 256, 0, st>>>(u, (size_t)o.n3, t.at_cnt, t.at_pt, t.at_p, t.at_d, t.cap, h3, inv_rc2, lamF, o.n_orb_pad, m); break;
+    case 2: k_nl_second_moment<2><<<grid, 256, 0, st>>>(u, (size_t)o.n3, t.at_cnt, t.at_pt, t.at_p, t.at_d, t.cap, h3, inv_rc2, lamF, o.n_orb_pad, m); break;
+    case 4: k_nl_second_moment<4><<<grid, 256, 0, st>>>(u, (size_t)o.n3, t.at_cnt, t.at_pt, t.at_p, t.at_d, t.cap, h3, inv_rc2, lamF, o.n_orb_pad, m); break;
+  }
+}
+
+void emd_adj_sr_hvp(const SpeciesDev &sp, int n_atoms, const double *Rw, double L,
+                    const double *lamF, double *out, cudaStream_t st) {
+  if (n_atoms <= 0) return;
+  emd_note_launches(1);
+  const int nmax = (int)ceil(12.0 / L) + 1;
+  k_sr_hvp<<<n_atoms, 256, 0, st>>>(sp, n_atoms, Rw, L, nmax, lamF, out);
+}
+
+void emd_adj_nl_force_r(const double2 *cc, const double2 *dc, const double2 *m,
+                        const double *lamF, int n_atoms, int n_orb, int n_orb_pad,
+                        double coef, double *out, cudaStream_t st) {
+  if (n_atoms <= 0) return;
+  emd_note_launches(1);
+  const int k = 3 * n_atoms;
+  k_nl_force_adj_r<<<(k + 127) / 128, 128, 0, st>>>(cc, dc, m, lamF, n_atoms, n_orb,
+                                                     n_orb_pad, coef, out);
+}

@@ -75,6 +75,12 @@ struct Adjoint {
          *scal = nullptr;
   double2 *cm = nullptr, *dcm = nullptr, *cu = nullptr, *dcu = nullptr,
           *hcu = nullptr;
+  // moving ions: (R, V, F) per checkpoint and per segment step, the force
+  // adjoint lam_F, its products and the extra grids
+  double *ck_ion = nullptr, *seg_ion = nullptr, *lamF = nullptr, *fl = nullptr,
+         *fr = nullptr, *fs = nullptr, *gR1 = nullptr, *fconv = nullptr,
+         *vh = nullptr, *w = nullptr, *tmp3 = nullptr;
+  double2 *m2 = nullptr;
   int n_field = 0;
   std::vector<void *> mem;
 };
@@ -849,7 +855,9 @@ namespace {
 
 int adj_alloc(emd_system *s, int n_ck, int K, int n_steps) {
   Adjoint *&A = s->adj;
-  if (A && A->n_ck >= n_ck && A->K >= K && A->n_field >= n_steps) return EMD_OK;
+  if (A && A->n_ck >= n_ck && A->K >= K && A->n_field >= n_steps &&
+      (s->frozen_ions || A->ck_ion))
+    return EMD_OK;
   if (A) {
     for (void *p : A->mem) cudaFree(p);
     delete A;
@@ -903,6 +911,22 @@ int adj_alloc(emd_system *s, int n_ck, int K, int n_steps) {
   AG(A->hcu, cb);
   AG(A->dcm, 3 * cb);
   AG(A->dcu, 3 * cb);
+  if (!s->frozen_ions) {
+    const size_t ib = 9 * (size_t)std::max(1, s->n_atoms) * sizeof(double);
+    const size_t ab = 3 * (size_t)std::max(1, s->n_atoms) * sizeof(double);
+    AG(A->ck_ion, (n_ck + 1) * ib);
+    AG(A->seg_ion, K * ib);
+    AG(A->lamF, ab);
+    AG(A->fl, ab);
+    AG(A->fr, ab);
+    AG(A->fs, ab);
+    AG(A->gR1, ab);
+    AG(A->fconv, ab);
+    AG(A->vh, gb);
+    AG(A->w, gb);
+    AG(A->tmp3, gb);
+    AG(A->m2, 3 * cb);
+  }
 #undef AG
   CK(cudaMemsetAsync(A->zero, 0, ob, s->st));
   CK(cudaMemsetAsync(A->zgrid, 0, gb, s->st));
@@ -939,7 +963,7 @@ void grid_dot(emd_system *s, const double *a, const double *b, double *dst) {
 // on return acc holds the adjoint of psi0; gv += dL/dv_eff; gR += dL/dR.
 void reverse_exponential(emd_system *s, const double2 *mu_in, double2 *acc,
                          double2 *const u[4], int which_veff, double tau,
-                         double *gv) {
+                         double *gv, int set, double *gR) {
   Adjoint *A = s->adj;
   const OrbLayout &o = s->o;
   const size_t nel = (size_t)o.n_blk * o.n3 * o.bo;
@@ -947,7 +971,7 @@ void reverse_exponential(emd_system *s, const double2 *mu_in, double2 *acc,
   double2 *mu = A->mu, *mu2 = A->mu + nel;
   cudaMemcpyAsync(mu, mu_in, s->orb_bytes, cudaMemcpyDeviceToDevice, s->st);
   cudaMemsetAsync(acc, 0, s->orb_bytes, s->st);
-  const TableSet &t = s->ts[s->cur];
+  const TableSet &t = s->ts[set];
   for (int k = 1; k <= 4; ++k) {
     const double b = tau / k;
     emd_adj_axpy(acc, mu, nel, s->st);
@@ -957,12 +981,318 @@ void reverse_exponential(emd_system *s, const double2 *mu_in, double2 *acc,
     emd_adj_project_grad(o, t, s->n_atoms, u[k - 1], h3, s->sp.h_kb,
                          s->sp.inv_rc2, A->cu, A->hcu, A->dcu, s->st);
     emd_adj_proj_sens(A->cm, A->dcm, A->cu, A->dcu, s->n_atoms, o.n_orb,
-                      o.n_orb_pad, s->sp.h_kb * b / h3, A->gR, s->st);
+                      o.n_orb_pad, s->sp.h_kb * b / h3, gR, s->st);
     // mu <- conj(a_k) H mu = (+i b) H mu
-    stage(s, mu, A->zero, mu2, s->cur, which_veff, -b);
+    stage(s, mu, A->zero, mu2, set, which_veff, -b);
     std::swap(mu, mu2);
   }
   emd_adj_axpy(acc, mu, nel, s->st);
+}
+
+// (R, V, F) of the current state to dst[0..9 na) / back; positions into
+// table set k with every table rebuilt.
+void save_ions(emd_system *s, double *dst) {
+  const size_t b = 3 * (size_t)s->n_atoms * sizeof(double);
+  cudaMemcpyAsync(dst, s->ts[s->cur].R, b, cudaMemcpyDeviceToDevice, s->st);
+  cudaMemcpyAsync(dst + 3 * s->n_atoms, s->V, b, cudaMemcpyDeviceToDevice, s->st);
+  cudaMemcpyAsync(dst + 6 * s->n_atoms, s->F, b, cudaMemcpyDeviceToDevice, s->st);
+}
+int load_positions(emd_system *s, int k, const double *src) {
+  const size_t b = 3 * (size_t)s->n_atoms * sizeof(double);
+  cudaMemcpyAsync(s->ts[k].R, src, b, cudaMemcpyDeviceToDevice, s->st);
+  int r = build_set(s, k);
+  if (r) return r;
+  negate_grid(s->ts[k].v_loc, s->g.n3, s->st);
+  return EMD_OK;
+}
+int load_ions(emd_system *s, const double *src) {
+  const size_t b = 3 * (size_t)s->n_atoms * sizeof(double);
+  cudaMemcpyAsync(s->V, src + 3 * s->n_atoms, b, cudaMemcpyDeviceToDevice, s->st);
+  cudaMemcpyAsync(s->F, src + 6 * s->n_atoms, b, cudaMemcpyDeviceToDevice, s->st);
+  return load_positions(s, s->cur, src);
+}
+
+// Reverse of the forces F(R, psi, v_es) at table set k for the direction
+// lam_F (already in A->lamF): fl, fr, fs = position terms (local, nonlocal,
+// short range); w = adjoint of v_es; lam += orbital term (if lam != NULL).
+// vh must hold Poisson(rho(psi)).
+void reverse_forces(emd_system *s, int k, const double2 *psi, double2 *lam) {
+  Adjoint *A = s->adj;
+  const OrbLayout &o = s->o;
+  const TableSet &t = s->ts[k];
+  const double h3 = s->g.h * s->g.h * s->g.h;
+  const double coef = -2.0 * s->sp.h_kb * s->cfg.occ;
+  emd_adj_project_grad(o, t, s->n_atoms, psi, h3, s->sp.h_kb, s->sp.inv_rc2,
+                       A->cu, A->hcu, A->dcu, s->st);
+  emd_adj_force_splat(s->g, s->sp, t, A->lamF, A->w, s->st);
+  if (lam)
+    emd_adj_nl_force_orb(o, s->g, s->sp, t, A->lamF, A->dcu, A->cu, coef * h3,
+                         lam, s->st);
+  emd_adj_nl_second_moment(o, t, s->n_atoms, psi, h3, s->sp.inv_rc2, A->lamF,
+                           A->m2, s->st);
+  emd_adj_nl_force_r(A->cu, A->dcu, A->m2, A->lamF, s->n_atoms, o.n_orb,
+                     o.n_orb_pad, coef, A->fr, s->st);
+  emd_launch_local_force_hvp(s->g, s->sp, s->n_atoms, t.Rw, A->vh, t.v_loc,
+                             A->lamF, s->lf_part, A->fl, s->st);
+  emd_adj_sr_hvp(s->sp, s->n_atoms, t.Rw, s->g.L, A->lamF, A->fs, s->st);
+}
+
+// The adjoint with moving ions.  Forward map of step n (Sec. 5.1):
+//   R' = R + dt V + c2 F;  tables at R';  psi' = T4(H(R', v2)) T4(H(R, v1)) psi;
+//   F' = F(R', psi', v_H(rho') + v_loc(R')) + Z e_n z;  V' = V + c1 (F + F'),
+// c1 = dt / (2M), c2 = dt^2 / (2M).  The reverse of step n, from the adjoints
+// (lam_psi, Lam_0..2, lam_R, lam_V, lam_F) of state n+1, first takes
+// mu_F = lam_F + c1 lam_V through the forces at R' (orbital, potential and
+// position terms), then the electrons as for fixed ions (the two
+// exponentials at their own table sets), converts the adjoint of v_loc(R')
+// into positions, and ends with the reverse of the position update:
+//   lam_R <- lam_R' (+ exponential-1 terms at R), lam_V = lam_V' + dt lam_R',
+//   lam_F = c1 lam_V' + c2 lam_R'.
+// The small per-atom vectors live on the host; one synchronisation per step.
+int adjoint_moving(emd_system *s, int n_steps, double dt, double mu,
+                   const std::vector<double> &fe, int K, int observable,
+                   double *L_out, double *dL_dR, double *dL_dfield) {
+  const int n_ck = (n_steps + K - 1) / K;
+  int r = adj_alloc(s, n_ck, K, n_steps);
+  if (r) return r;
+  Adjoint *A = s->adj;
+  const OrbLayout &o = s->o;
+  const int n3 = s->g.n3;
+  const size_t gb = (size_t)n3 * sizeof(double);
+  const double h3 = s->g.h * s->g.h * s->g.h;
+  const double tau = 0.5 * (dt / mu);
+  const double occ = s->cfg.occ;
+  const int na = s->n_atoms;
+  const size_t ionw = 9 * (size_t)na;
+  const double M = s->sp.mass;
+  const double c1 = dt / (2.0 * M), c2 = (dt * dt) / (2.0 * M);
+
+  // ---- forward sweep: orbitals, history and (R, V, F) every K steps
+  for (int n = 0; n < n_steps; ++n) {
+    if (n % K == 0) {
+      const int ck = n / K;
+      CK(cudaMemcpyAsync(A->ck_psi[ck], s->psi, s->orb_bytes, cudaMemcpyDeviceToDevice, s->st));
+      copy_hist_out(s, A->ck_hist[ck]);
+      A->ck_len[ck] = s->hist_len;
+      save_ions(s, A->ck_ion + ck * ionw);
+    }
+    r = step_once(s, dt, mu, fe[n]);
+    if (r) return r;
+  }
+  CK(cudaMemcpyAsync(A->ck_psi[n_ck], s->psi, s->orb_bytes, cudaMemcpyDeviceToDevice, s->st));
+  copy_hist_out(s, A->ck_hist[n_ck]);
+  A->ck_len[n_ck] = s->hist_len;
+  save_ions(s, A->ck_ion + n_ck * ionw);
+
+  // ---- observable and the adjoint of the final state
+  std::vector<double> lR(3 * std::max(1, na), 0.0), lV(lR), lF(lR), mF(lR);
+  std::vector<double> fl(lR), fr(lR), fs(lR), g2(lR), g1(lR), fc(lR);
+  std::vector<double> dfi(n_steps, 0.0);
+  CK(cudaMemsetAsync(A->lam, 0, s->orb_bytes, s->st));
+  double L = 0.0;
+  if (observable == EMD_OBS_DIPOLE_Z) {
+    grid_dot(s, s->rho, A->saw, A->scal);
+    double dot = 0.0;
+    std::vector<double> Rw(3 * std::max(1, na));
+    CK(cudaMemcpyAsync(&dot, A->scal, sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    if (na) CK(cudaMemcpyAsync(Rw.data(), s->ts[s->cur].Rw, 3 * na * 8, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    L = -h3 * dot;
+    for (int J = 0; J < na; ++J) {
+      L += s->sp.z * (Rw[3 * J + 2] - 0.5 * s->g.L);
+      lR[3 * J + 2] += s->sp.z;
+    }
+    emd_adj_scale_add(o, A->lam, (const double2 *)s->psi, A->saw, -2.0 * occ * h3, s->st);
+  } else {
+    // L = E_KS + sum M V^2 / 2: lam_psi = 2 f h^3 H psi, lam_R = -F_KS,
+    // lam_V = M V
+    emd_energy e;
+    r = emd_get_energy(s, &e);
+    if (r) return r;
+    L = e.ks + e.kin_ion;
+    emd_launch_veff(s->g, s->ts[s->cur].v_loc, s->hist, 1, 0.0, s->veff1, s->veff1f, s->st);
+    project(s, s->psi, s->cur);
+    StageArgs a_;
+    a_.u_in = s->psi;
+    a_.psi0 = s->psi;
+    a_.u_out = A->acc;
+    a_.v_eff = s->veff1;
+    a_.tab = &s->ts[s->cur];
+    a_.hc = s->hc;
+    a_.a = 0.0;
+    a_.apply_only = 1;
+    emd_launch_stage(o, a_, s->st);
+    std::vector<double> ones(n3, 1.0);
+    CK(cudaMemcpyAsync(A->tmp, ones.data(), gb, cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    emd_adj_scale_add(o, A->lam, A->acc, A->tmp, 2.0 * occ * h3, s->st);
+    forces(s, s->cur, 0.0, 0.0, 0);
+    std::vector<double> F(3 * std::max(1, na)), V(3 * std::max(1, na));
+    if (na) {
+      CK(cudaMemcpyAsync(F.data(), s->F, 3 * na * 8, cudaMemcpyDeviceToHost, s->st));
+      CK(cudaMemcpyAsync(V.data(), s->V, 3 * na * 8, cudaMemcpyDeviceToHost, s->st));
+    }
+    CK(cudaStreamSynchronize(s->st));
+    for (int i = 0; i < 3 * na; ++i) {
+      lR[i] -= F[i];
+      lV[i] = M * V[i];
+    }
+  }
+  CK(cudaMemsetAsync(A->L0, 0, gb, s->st));
+  CK(cudaMemsetAsync(A->L1, 0, gb, s->st));
+  CK(cudaMemsetAsync(A->L2, 0, gb, s->st));
+  CK(cudaMemsetAsync(A->gvloc, 0, gb, s->st));
+  CK(cudaMemsetAsync(A->dfield, 0, n_steps * 8, s->st));
+  const size_t ab = 3 * (size_t)na * sizeof(double);
+
+  // ---- reverse sweep, last segment first
+  int setA = 0;
+  for (int ck = n_ck - 1; ck >= 0; --ck) {
+    const int n0 = ck * K, n1 = std::min(n_steps, n0 + K);
+    CK(cudaMemcpyAsync(s->psi, A->ck_psi[ck], s->orb_bytes, cudaMemcpyDeviceToDevice, s->st));
+    copy_hist_in(s, A->ck_hist[ck]);
+    s->hist_len = A->ck_len[ck];
+    r = load_ions(s, A->ck_ion + ck * ionw);
+    if (r) return r;
+    s->c_valid = 0;
+    for (int n = n0; n < n1; ++n) {
+      CK(cudaMemcpyAsync(A->seg_psi[n - n0], s->psi, s->orb_bytes, cudaMemcpyDeviceToDevice, s->st));
+      copy_hist_out(s, A->seg_hist[n - n0]);
+      A->seg_len[n - n0] = s->hist_len;
+      save_ions(s, A->seg_ion + (n - n0) * ionw);
+      r = step_once(s, dt, mu, fe[n]);
+      if (r) return r;
+    }
+    // positions R_{n1} in set cur, R_{n1 - 1} in the other
+    int setB = s->cur;
+    setA = 1 - s->cur;
+    for (int n = n1 - 1; n >= n0; --n) {
+      const double2 *psi_next = n == n1 - 1 ? (const double2 *)s->psi : A->seg_psi[n + 1 - n0];
+      // adjoint of F_{n+1}
+      for (int i = 0; i < 3 * na; ++i) {
+        mF[i] = lF[i] + c1 * lV[i];
+        lF[i] = c1 * lV[i];
+      }
+      for (int J = 0; J < na; ++J) dfi[n] += s->sp.z * mF[3 * J + 2];
+      if (na) CK(cudaMemcpyAsync(A->lamF, mF.data(), ab, cudaMemcpyHostToDevice, s->st));
+      emd_launch_density(o, psi_next, occ, A->tmp2, s->st);
+      emd_launch_poisson(s->g, A->tmp2, A->vh, s->fft_a, s->fft_b, s->st);
+      reverse_forces(s, setB, psi_next, A->lam);
+      emd_adj_lincomb(n3, A->gvloc, 1.0, A->gvloc, 1.0, A->w, 0.0, nullptr, 0.0, nullptr, s->st);
+      // adjoint of rho_{n+1}: through v_Hxc (history slot 0) and v_H in v_es
+      emd_adj_lincomb(n3, A->tmp3, 1.0, A->L0, 1.0, A->w, 0.0, nullptr, 0.0, nullptr, s->st);
+      emd_launch_poisson(s->g, A->tmp3, A->tmp, s->fft_a, s->fft_b, s->st);
+      emd_adj_rho(n3, A->tmp2, A->L0, A->tmp, s->st);
+      emd_adj_scale_add(o, A->lam, psi_next, A->tmp, 2.0 * occ, s->st);
+      // recompute the stage inputs of step n: exponential 1 at R_n (set A),
+      // exponential 2 at R_{n+1} (set B)
+      const double2 *psi_n = A->seg_psi[n - n0];
+      const double *hn = A->seg_hist[n - n0];
+      const double *hp[3] = {hn, hn + n3, hn + 2 * (size_t)n3};
+      const int len = A->seg_len[n - n0];
+      emd_launch_veff(s->g, s->ts[setA].v_loc, hp, 1, fe[n], s->veff1, s->veff1f, s->st);
+      emd_launch_veff(s->g, s->ts[setB].v_loc, hp, len, fe[n], s->veff2, s->veff2f, s->st);
+      double2 *const *U = A->st_u.data();
+      project(s, psi_n, setA);
+      stage(s, psi_n, psi_n, U[0], setA, 1, tau / 4.0);
+      project(s, U[0], setA);
+      stage(s, U[0], psi_n, U[1], setA, 1, tau / 3.0);
+      project(s, U[1], setA);
+      stage(s, U[1], psi_n, U[2], setA, 1, tau / 2.0);
+      project(s, U[2], setA);
+      stage(s, U[2], psi_n, U[3], setA, 1, tau);
+      project(s, U[3], setB);
+      stage(s, U[3], U[3], U[4], setB, 2, tau / 4.0);
+      project(s, U[4], setB);
+      stage(s, U[4], U[3], U[5], setB, 2, tau / 3.0);
+      project(s, U[5], setB);
+      stage(s, U[5], U[3], U[6], setB, 2, tau / 2.0);
+      CK(cudaMemsetAsync(A->gv2, 0, gb, s->st));
+      CK(cudaMemsetAsync(A->gv1, 0, gb, s->st));
+      if (na) {
+        CK(cudaMemsetAsync(A->gR, 0, ab, s->st));
+        CK(cudaMemsetAsync(A->gR1, 0, ab, s->st));
+      }
+      double2 *const in2[4] = {U[6], U[5], U[4], U[3]};
+      reverse_exponential(s, A->lam, A->acc, in2, 2, tau, A->gv2, setB, A->gR);
+      double2 *const in1[4] = {U[2], U[1], U[0], (double2 *)psi_n};
+      reverse_exponential(s, A->acc, A->lam, in1, 1, tau, A->gv1, setA, A->gR1);
+      // v_loc(R_{n+1}) adjoint complete: to positions, then restart with gv1
+      emd_adj_lincomb(n3, A->gvloc, 1.0, A->gvloc, 1.0, A->gv2, 0.0, nullptr, 0.0, nullptr, s->st);
+      emd_launch_poisson(s->g, A->gvloc, A->tmp, s->fft_a, s->fft_b, s->st);
+      emd_launch_local_force(s->g, s->sp, na, s->ts[setB].Rw, A->tmp, A->zgrid,
+                             s->lf_part, A->fconv, s->st);
+      emd_adj_lincomb(n3, A->tmp, 1.0, A->gv1, 1.0, A->gv2, 0.0, nullptr, 0.0, nullptr, s->st);
+      grid_dot(s, A->tmp, A->saw, A->dfield + n);
+      emd_adj_lincomb(n3, A->gvloc, 1.0, A->gv1, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr, s->st);
+      const double x0 = len <= 1 ? 1.0 : len == 2 ? 2.0 : 3.0;
+      const double x1 = len <= 1 ? 0.0 : len == 2 ? -1.0 : -3.0;
+      const double x2 = len <= 2 ? 0.0 : 1.0;
+      emd_adj_lincomb(n3, A->tmp, 1.0, A->L1, 1.0, A->gv1, x0, A->gv2, 0.0, nullptr, s->st);
+      emd_adj_lincomb(n3, A->L1, 1.0, A->L2, x1, A->gv2, 0.0, nullptr, 0.0, nullptr, s->st);
+      emd_adj_lincomb(n3, A->L2, x2, A->gv2, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr, s->st);
+      std::swap(A->L0, A->tmp);
+      r = launch_check("emd_propagate_adjoint");
+      if (r) return r;
+      if (na) {
+        CK(cudaMemcpyAsync(fl.data(), A->fl, ab, cudaMemcpyDeviceToHost, s->st));
+        CK(cudaMemcpyAsync(fr.data(), A->fr, ab, cudaMemcpyDeviceToHost, s->st));
+        CK(cudaMemcpyAsync(fs.data(), A->fs, ab, cudaMemcpyDeviceToHost, s->st));
+        CK(cudaMemcpyAsync(g2.data(), A->gR, ab, cudaMemcpyDeviceToHost, s->st));
+        CK(cudaMemcpyAsync(g1.data(), A->gR1, ab, cudaMemcpyDeviceToHost, s->st));
+        CK(cudaMemcpyAsync(fc.data(), A->fconv, ab, cudaMemcpyDeviceToHost, s->st));
+      }
+      CK(cudaStreamSynchronize(s->st));
+      for (int i = 0; i < 3 * na; ++i) {
+        const double lr1 = lR[i] + fl[i] + fr[i] + fs[i] + g2[i] - fc[i] / h3;
+        lR[i] = lr1 + g1[i];
+        lV[i] += dt * lr1;
+        lF[i] += c2 * lr1;
+      }
+      if (n > n0) {
+        // set B now takes R_{n-1}; set A (R_n) becomes the next step's B
+        r = load_positions(s, setB, A->seg_ion + (n - 1 - n0) * ionw);
+        if (r) return r;
+        std::swap(setA, setB);
+      }
+    }
+  }
+
+  // ---- the initial forces F(R_0, psi_0, v_es_0) and v_loc(R_0)
+  for (int i = 0; i < 3 * na; ++i) mF[i] = lF[i];
+  if (na) CK(cudaMemcpyAsync(A->lamF, mF.data(), ab, cudaMemcpyHostToDevice, s->st));
+  emd_launch_density(o, A->seg_psi[0], occ, A->tmp2, s->st);
+  emd_launch_poisson(s->g, A->tmp2, A->vh, s->fft_a, s->fft_b, s->st);
+  reverse_forces(s, setA, A->seg_psi[0], nullptr);
+  emd_adj_lincomb(n3, A->gvloc, 1.0, A->gvloc, 1.0, A->w, 0.0, nullptr, 0.0, nullptr, s->st);
+  emd_launch_poisson(s->g, A->gvloc, A->tmp, s->fft_a, s->fft_b, s->st);
+  emd_launch_local_force(s->g, s->sp, na, s->ts[setA].Rw, A->tmp, A->zgrid,
+                         s->lf_part, A->fconv, s->st);
+  if (na) {
+    CK(cudaMemcpyAsync(fl.data(), A->fl, ab, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(fr.data(), A->fr, ab, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(fs.data(), A->fs, ab, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(fc.data(), A->fconv, ab, cudaMemcpyDeviceToHost, s->st));
+  }
+  std::vector<double> df(n_steps);
+  CK(cudaMemcpyAsync(df.data(), A->dfield, n_steps * 8, cudaMemcpyDeviceToHost, s->st));
+  // leave the system at the final state
+  CK(cudaMemcpyAsync(s->psi, A->ck_psi[n_ck], s->orb_bytes, cudaMemcpyDeviceToDevice, s->st));
+  copy_hist_in(s, A->ck_hist[n_ck]);
+  s->hist_len = A->ck_len[n_ck];
+  r = load_ions(s, A->ck_ion + n_ck * ionw);
+  if (r) return r;
+  s->c_valid = 0;
+  electrons(s, 0);
+  CK(cudaStreamSynchronize(s->st));
+  for (int i = 0; i < 3 * na; ++i)
+    dL_dR[i] = lR[i] + fl[i] + fr[i] + fs[i] - fc[i] / h3;
+  if (dL_dfield)
+    for (int i = 0; i < n_steps; ++i) dL_dfield[i] = df[i] + dfi[i];
+  *L_out = L;
+  r = launch_check("emd_propagate_adjoint");
+  if (r) return r;
+  return read_err_flag(s);
 }
 
 }  // namespace
@@ -977,9 +1307,6 @@ int emd_propagate_adjoint(emd_system *s, int n_steps, double dt, double mu,
   if (r) return r;
   if (s->o.prec != EMD_FP64)
     return fail(EMD_EINVAL, "adjoint propagation needs FP64 orbitals");
-  if (!s->frozen_ions)
-    return fail(EMD_ESTATE, "adjoint propagation is built for fixed ions: set "
-                            "EMD_OPT_FROZEN_IONS (moving-ion adjoint not built)");
   if (n_steps < 1 || ckpt_every < 1)
     return fail(EMD_EINVAL, "n_steps and ckpt_every must be >= 1");
   if (observable != EMD_OBS_ENERGY && observable != EMD_OBS_DIPOLE_Z)
@@ -993,6 +1320,9 @@ int emd_propagate_adjoint(emd_system *s, int n_steps, double dt, double mu,
       fe[i] = field[i];
     }
   const int K = std::min(ckpt_every, n_steps);
+  if (!s->frozen_ions)
+    return adjoint_moving(s, n_steps, dt, mu, fe, K, observable, L_out, dL_dR,
+                          dL_dfield);
   const int n_ck = (n_steps + K - 1) / K;
   r = adj_alloc(s, n_ck, K, n_steps);
   if (r) return r;
@@ -1123,9 +1453,9 @@ int emd_propagate_adjoint(emd_system *s, int n_steps, double dt, double mu,
       CK(cudaMemsetAsync(A->gv2, 0, gb, s->st));
       CK(cudaMemsetAsync(A->gv1, 0, gb, s->st));
       double2 *const in2[4] = {U[6], U[5], U[4], U[3]};
-      reverse_exponential(s, A->lam, A->acc, in2, 2, tau, A->gv2);
+      reverse_exponential(s, A->lam, A->acc, in2, 2, tau, A->gv2, s->cur, A->gR);
       double2 *const in1[4] = {U[2], U[1], U[0], (double2 *)psi_n};
-      reverse_exponential(s, A->acc, A->lam, in1, 1, tau, A->gv1);
+      reverse_exponential(s, A->acc, A->lam, in1, 1, tau, A->gv1, s->cur, A->gR);
       // field, ionic potential and history adjoints
       emd_adj_lincomb(n3, A->tmp, 1.0, A->gv1, 1.0, A->gv2, 0.0, nullptr, 0.0, nullptr, s->st);
       grid_dot(s, A->tmp, A->saw, A->dfield + n);

@@ -222,3 +222,22 @@ void emd_adj_scale_add(const OrbLayout &o, double2 *lam, const double2 *psi,
 void emd_adj_lincomb(int n, double *out, double a0, const double *x0, double a1,
                      const double *x1, double a2, const double *x2, double a3,
                      const double *x3, cudaStream_t st);
+void emd_adj_force_splat(const GridInfo &g, const SpeciesDev &sp, const TableSet &t,
+                         const double *lamF, double *w, cudaStream_t st);
+void emd_adj_nl_force_orb(const OrbLayout &o, const GridInfo &g, const SpeciesDev &sp,
+                          const TableSet &t, const double *lamF, const double2 *dc,
+                          const double2 *cc, double coef, double2 *lam,
+                          cudaStream_t st);
+void emd_adj_nl_second_moment(const OrbLayout &o, const TableSet &t, int n_atoms,
+                              const double2 *u, double h3, double inv_rc2,
+                              const double *lamF, double2 *m, cudaStream_t st);
+void emd_launch_local_force_hvp(const GridInfo &g, const SpeciesDev &sp,
+                                int n_atoms, const double *Rw,
+                                const double *v_es_a, const double *v_es_b,
+                                const double *lam, double *part, double *out,
+                                cudaStream_t st);
+void emd_adj_sr_hvp(const SpeciesDev &sp, int n_atoms, const double *Rw, double L,
+                    const double *lamF, double *out, cudaStream_t st);
+void emd_adj_nl_force_r(const double2 *cc, const double2 *dc, const double2 *m,
+                        const double *lamF, int n_atoms, int n_orb, int n_orb_pad,
+                        double coef, double *out, cudaStream_t st);

@@ -265,9 +265,14 @@ k_atom_table(int pass, int n, double h, double L, const double *Rw,
 // (-dE_es/dR_J of 1/2 h^3 sum n_tot v_es, n_tot = rho - sum g).  Grid
 // (atom, split) over contiguous ranges of the flattened box space; partials
 // are summed in split order by k_local_force_sum.
+// HVP = true gives instead, for a direction lam per atom, the derivative
+// d/dR_J of lam_J . F_loc,J at fixed potential:
+//   h^3 sum v_es g_J (-2/a^2) [lam_J - 2 d (d . lam_J) / a^2].
+template <bool HVP>
 __global__ void __launch_bounds__(256)
 k_local_force(int n, double h, double L, const double *Rw, SpeciesDev sp,
-              const double *va, const double *vb, double *part) {
+              const double *va, const double *vb, const double *lam,
+              double *part) {
   __shared__ ImageBoxes B;
   __shared__ double red[8 * 3];
   const int J = blockIdx.x, split = blockIdx.y, nsplit = gridDim.y;
@@ -294,10 +299,19 @@ k_local_force(int n, double h, double L, const double *Rw, SpeciesDev sp,
     if (d2 < rl2) {
       const int p = (iz * n + iy) * n + ix;
       const double g = sp.c_g * exp(-d2 * sp.inv_a2);
-      const double w = (va[p] + vb[p]) * g * (2.0 * sp.inv_a2);
-      acc[0] += w * dx;
-      acc[1] += w * dy;
-      acc[2] += w * dz;
+      if (HVP) {
+        const double l0 = lam[3 * J], l1 = lam[3 * J + 1], l2 = lam[3 * J + 2];
+        const double w = (va[p] + vb[p]) * g * (-2.0 * sp.inv_a2);
+        const double dl = (dx * l0 + dy * l1 + dz * l2) * (2.0 * sp.inv_a2);
+        acc[0] += w * (l0 - dx * dl);
+        acc[1] += w * (l1 - dy * dl);
+        acc[2] += w * (l2 - dz * dl);
+      } else {
+        const double w = (va[p] + vb[p]) * g * (2.0 * sp.inv_a2);
+        acc[0] += w * dx;
+        acc[1] += w * dy;
+        acc[2] += w * dz;
+      }
     }
   }
   emd_block_sum<3>(acc, red);
@@ -420,10 +434,24 @@ void emd_launch_local_force(const GridInfo &g, const SpeciesDev &sp,
   if (n_atoms <= 0) return;
   emd_note_launches(2);
   dim3 grid(n_atoms, EMD_SPLIT);
-  k_local_force<<<grid, 256, 0, st>>>(g.n, g.h, g.L, Rw, sp, v_es_a, v_es_b,
-                                      part);
+  k_local_force<false><<<grid, 256, 0, st>>>(g.n, g.h, g.L, Rw, sp, v_es_a,
+                                             v_es_b, nullptr, part);
   const int m = 3 * n_atoms;
   k_local_force_sum<<<(m + 127) / 128, 128, 0, st>>>(part, n_atoms, EMD_SPLIT, F);
+}
+
+void emd_launch_local_force_hvp(const GridInfo &g, const SpeciesDev &sp,
+                                int n_atoms, const double *Rw,
+                                const double *v_es_a, const double *v_es_b,
+                                const double *lam, double *part, double *out,
+                                cudaStream_t st) {
+  if (n_atoms <= 0) return;
+  emd_note_launches(2);
+  dim3 grid(n_atoms, EMD_SPLIT);
+  k_local_force<true><<<grid, 256, 0, st>>>(g.n, g.h, g.L, Rw, sp, v_es_a,
+                                            v_es_b, lam, part);
+  const int m = 3 * n_atoms;
+  k_local_force_sum<<<(m + 127) / 128, 128, 0, st>>>(part, n_atoms, EMD_SPLIT, out);
 }
 
 void emd_launch_short_range(const SpeciesDev &sp, int n_atoms, const double *Rw,

@@ -13,6 +13,7 @@ import pytest
 import torch
 
 from oracle import emd_adjoint as A
+from oracle import emd_oracle as O
 from paper_0812_2801_gb300 import adjoint as gadj
 from paper_0812_2801_gb300 import emd, inputs
 
@@ -108,3 +109,55 @@ def test_short_field_run_gradient_vs_central_difference_h1e4():
         fd = (forward_dipole(s, s.R, fp, 25, s.dt, s.mu)
               - forward_dipole(s, s.R, fm, 25, s.dt, s.mu)) / 2e-4
         assert abs(fd - df[i]) <= 1e-6 * max(abs(df[i]), 1e-3 * np.max(np.abs(df))), (i, fd, df[i])
+
+
+def gpu_grad_md(s, field, n_steps, dt, mu, K, kind):
+    h = emd.emd_init_system(emd.config_for(s))
+    emd.emd_set_ions(h, s.R, s.V)
+    emd.emd_set_orbitals(h, s.psi)
+    out = emd.emd_propagate_adjoint(h, n_steps, dt, mu, field, K, gadj.KINDS[kind], s.n_atoms)
+    R, V, _, _ = emd.emd_get_state(h, s.n_atoms, s.n_orb, s.n, want_psi=False)
+    emd.emd_destroy(h)
+    return out + (R, V)
+
+
+@pytest.mark.parametrize("kind", ["dipole", "energy"])
+def test_gpu_moving_ion_adjoint_matches_reference_adjoint(kind):
+    """Moving ions (velocities x200 so positions change measurably), 7 steps,
+    checkpoints every 3 (ragged last segment)."""
+    s = small()
+    s.V = s.V * 200.0
+    rng = np.random.default_rng(6)
+    field = rng.uniform(-0.02, 0.02, size=7)
+    L, dR, df, Rf, Vf = gpu_grad_md(s, field, 7, 0.05, 1.0, 3, kind)
+    Lr, dRr, dfr = A.gradients_md(s, field, 7, 0.05, 1.0, kind)
+    assert abs(L - Lr) <= 1e-10 * max(1.0, abs(Lr))
+    assert np.max(np.abs(df - dfr)) <= 1e-9 * np.max(np.abs(dfr))
+    assert np.max(np.abs(dR - dRr)) <= 1e-9 * np.max(np.abs(dRr))
+    # the system is left at the final state of the forward run
+    st = O.run(s, 7, dt=0.05, mu=1.0, field=field)
+    assert np.max(np.abs(Rf - st.R)) < 1e-12 and np.max(np.abs(Vf - st.V)) < 1e-12
+
+
+def test_gpu_moving_ion_adjoint_continues_dynamics():
+    """After the adjoint call the system continues exactly like a plain
+    propagation of the same length."""
+    s = small()
+    s.V = s.V * 200.0
+    field = np.linspace(-0.01, 0.01, 4)
+    h = emd.emd_init_system(emd.config_for(s))
+    emd.emd_set_ions(h, s.R, s.V)
+    emd.emd_set_orbitals(h, s.psi)
+    emd.emd_propagate_adjoint(h, 4, 0.05, 1.0, field, 2, emd.EMD_OBS_DIPOLE_Z, s.n_atoms)
+    emd.emd_propagate(h, 2, 0.05, 1.0, None)
+    a = emd.emd_get_state(h, s.n_atoms, s.n_orb, s.n)
+    emd.emd_destroy(h)
+    h = emd.emd_init_system(emd.config_for(s))
+    emd.emd_set_ions(h, s.R, s.V)
+    emd.emd_set_orbitals(h, s.psi)
+    emd.emd_propagate(h, 4, 0.05, 1.0, field)
+    emd.emd_propagate(h, 2, 0.05, 1.0, None)
+    b = emd.emd_get_state(h, s.n_atoms, s.n_orb, s.n)
+    emd.emd_destroy(h)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
