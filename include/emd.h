@@ -59,16 +59,20 @@ extern "C" {
 #define EMD_OPT_FROZEN_IONS  1  /* value != 0: ions fixed, no forces/VV      */
 #define EMD_OPT_PROFILE      2  /* value != 0: time Horner-stage launches     */
 #define EMD_OPT_CHECK_STABLE 3  /* value == 0: skip the stability refusal    */
-#define EMD_OPT_STAGE_VARIANT 4 /* complex64 Horner-stage kernel for bo = 2:
-                                   0 one thread per (column, 2 rows), both
-                                   orbitals (default); 1 one thread per
-                                   (point, orbital) column; 2 one thread per
-                                   point.  bo = 4 always uses 1            */
-#define EMD_OPT_PROJECTION   5  /* projections <p_J|u>: 1 atom-major (each
-                                   atom gathers its sphere, default), 0
-                                   point-major (each 8^3 tile read once,
-                                   warp-tree reductions per atom; slower on
-                                   GB300: 1.09 vs 0.41 ms, 96^3 complex64) */
+#define EMD_OPT_STAGE_VARIANT 4 /* complex64 Horner-stage kernel: 0 one
+                                   thread per (orbital column, 2 rows) with
+                                   compile-time ring slots (default); 1 the
+                                   same tiling, earlier form; bo = 2 only:
+                                   2 one thread per point, 3 one thread per
+                                   (point column, 2 rows).  bo = 4 uses 0
+                                   unless 1 is asked for                  */
+#define EMD_OPT_PROJECTION   5  /* complex128 projections <p_J|u>: 1
+                                   atom-major (each atom gathers its sphere,
+                                   default), 0 point-major (each 8^3 tile
+                                   read once, one warp-tree reduction per
+                                   atom and warp).  complex64 orbitals always
+                                   use per-tile entry lists grouped by atom
+                                   (each tile read once, one warp per atom) */
 
 /* kernels that can be timed with EMD_OPT_PROFILE */
 #define EMD_KERNEL_HORNER    0  /* one Taylor/Horner stage u' = psi0 + a H u */

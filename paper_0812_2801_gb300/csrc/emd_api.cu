@@ -184,7 +184,11 @@ int build_set(emd_system *s, int k) {
 void negate_grid(double *v, int n3, cudaStream_t st);
 
 void project(emd_system *s, const void *u, int set) {
-  if (s->proj_atom_major)
+  if (s->o.prec == EMD_FP32_ORBITALS)
+    emd_launch_project_tile(s->o, s->ts[set], s->n_atoms, u,
+                            s->g.h * s->g.h * s->g.h, s->sp.h_kb, s->c, s->hc,
+                            s->proj_part, s->st);
+  else if (s->proj_atom_major)
     emd_launch_project(s->o, s->ts[set], s->n_atoms, u, s->g.h * s->g.h * s->g.h,
                        s->sp.h_kb, s->c, s->hc, s->st);
   else
@@ -250,10 +254,16 @@ void electrons(emd_system *s, int slot) {
 void forces(emd_system *s, int k, double field, double dt, int update_v) {
   emd_launch_local_force(s->g, s->sp, s->n_atoms, s->ts[k].Rw, s->v_h,
                          s->ts[k].v_loc, s->lf_part, s->F_loc, s->st);
-  emd_launch_nl_force(s->o, s->ts[k], s->n_atoms, s->psi, s->c,
-                      s->g.h * s->g.h * s->g.h,
-                      -2.0 * s->sp.h_kb * s->cfg.occ, s->sp.inv_rc2,
-                      s->nl_part, s->F_nl, s->st);
+  if (s->o.prec == EMD_FP32_ORBITALS)
+    emd_launch_nl_force_tile(s->o, s->ts[k], s->n_atoms, s->psi, s->c,
+                             s->g.h * s->g.h * s->g.h,
+                             -2.0 * s->sp.h_kb * s->cfg.occ, s->proj_part, s->F_nl,
+                             s->st);
+  else
+    emd_launch_nl_force(s->o, s->ts[k], s->n_atoms, s->psi, s->c,
+                        s->g.h * s->g.h * s->g.h,
+                        -2.0 * s->sp.h_kb * s->cfg.occ, s->sp.inv_rc2,
+                        s->nl_part, s->F_nl, s->st);
   emd_launch_short_range(s->sp, s->n_atoms, s->ts[k].Rw, s->g.L, s->F_sr,
                          s->e_sr, s->st);
   emd_launch_vv_velocities(s->n_atoms, s->F_loc, s->F_nl, s->F_sr, field,
@@ -436,7 +446,8 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
   const long cube = (long)ext * ext * ext;
   long cap = (L > 2.0 * p.r_proj) ? std::min<long>((long)n3, cube)
                                   : std::min<long>(8L * (long)n3, 27L * cube);
-  if (c.n_atoms == 0) cap = 1;
+  // the complex64 path reads the per-tile entries instead of the atom table
+  if (c.n_atoms == 0 || c.precision == EMD_FP32_ORBITALS) cap = 1;
   for (int k = 0; k < 2; ++k) {
     TableSet &t = s->ts[k];
     t.cap = (int)cap;
@@ -454,6 +465,16 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
     TRY(A((void **)&t.at_pt, (size_t)na * cap * 4));
     TRY(A((void **)&t.at_p, (size_t)na * cap * 8));
     TRY(A((void **)&t.at_d, (size_t)na * cap * 24));
+    t.te_off = nullptr;
+    t.te_pt = nullptr;
+    t.te_p = nullptr;
+    t.te_q = nullptr;
+    if (c.precision == EMD_FP32_ORBITALS) {
+      TRY(A((void **)&t.te_off, (size_t)ntiles * (EMD_TILE_ATOM_MAX + 1) * 4));
+      TRY(A((void **)&t.te_pt, (size_t)ntiles * EMD_TE_CAP * 2));
+      TRY(A((void **)&t.te_p, (size_t)ntiles * EMD_TE_CAP * 4));
+      TRY(A((void **)&t.te_q, (size_t)ntiles * EMD_TE_CAP * 16));
+    }
     t.n_slots_cap = ntiles * EMD_TILE_ATOM_MAX;
     TRY(A((void **)&t.tile_nat, ntiles * 4));
     TRY(A((void **)&t.tile_atoms, (size_t)ntiles * EMD_TILE_ATOM_MAX * 4));
@@ -464,7 +485,8 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
     TRY(A((void **)&t.v_loc, n3 * 8));
   }
   TRY(A((void **)&s->proj_part, (size_t)o.n_blk * ntiles * EMD_TILE_ATOM_MAX *
-                                     o.bo * sizeof(double2)));
+                                     o.bo * (c.precision == EMD_FP32_ORBITALS ? 3 : 1) *
+                                     sizeof(double2)));
   TRY(A((void **)&s->c, (size_t)na * o.n_orb_pad * sizeof(double2)));
   TRY(A(&s->hc, (size_t)na * o.n_orb_pad * esz));
   TRY(A((void **)&s->V, na * 3 * 8));
@@ -573,8 +595,8 @@ int emd_set_option(emd_system *s, int option, double value) {
       s->proj_atom_major = (int)value;
       return EMD_OK;
     case EMD_OPT_STAGE_VARIANT:
-      if (value != 0.0 && value != 1.0 && value != 2.0)
-        return fail(EMD_EINVAL, "stage variant must be 0, 1 or 2");
+      if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
+        return fail(EMD_EINVAL, "stage variant must be 0, 1, 2 or 3");
       s->o.stage_variant = (int)value;
       return EMD_OK;
   }
@@ -1633,8 +1655,13 @@ int emd_apply_hamiltonian(emd_system *s, int n_vec, const double *psi,
   o.n_blk = (n_vec + o.bo - 1) / o.bo;
   emd_launch_veff(s->g, s->ts[s->cur].v_loc, s->hist, 1, 0.0, s->veff1,
                   s->veff1f, s->st);
-  emd_launch_project(o, s->ts[s->cur], s->n_atoms, s->ua,
-                     s->g.h * s->g.h * s->g.h, s->sp.h_kb, s->c, s->hc, s->st);
+  if (o.prec == EMD_FP32_ORBITALS)
+    emd_launch_project_tile(o, s->ts[s->cur], s->n_atoms, s->ua,
+                            s->g.h * s->g.h * s->g.h, s->sp.h_kb, s->c, s->hc,
+                            s->proj_part, s->st);
+  else
+    emd_launch_project(o, s->ts[s->cur], s->n_atoms, s->ua,
+                       s->g.h * s->g.h * s->g.h, s->sp.h_kb, s->c, s->hc, s->st);
   s->c_valid = 0;
   StageArgs a;
   a.u_in = s->ua;

@@ -9,6 +9,7 @@
 #define EMD_TILE_CAND_MAX 160   // (atom, image) candidates per tile
 #define EMD_TILE_ATOM_MAX 32    // distinct atoms per tile (point-major projections)
 #define EMD_MAX_HALF_ORDER 6    // fd_order / 2 <= 6
+#define EMD_TE_CAP (EMD_TILE * EMD_TILE * EMD_TILE * EMD_PT_KMAX)
 #define EMD_SPLIT 16            // CTAs per atom for table building and local forces
 
 // error bits raised by kernels (device flag, read by emd_get_*)
@@ -46,6 +47,14 @@ struct TableSet {
   int *at_pt;       // [n_atoms][cap] flat grid index
   double *at_p;     // [n_atoms][cap] p value of that (point, image)
   double *at_d;     // [n_atoms][cap][3] displacement r - R_image
+  // complex64 path: per 8^3 tile, the (point, atom) pairs of the projectors
+  // grouped by the tile's atoms (slots, in tile_atoms order): te_off[t][s]
+  // is the first entry of slot s (te_off[t][S] the end), an entry holds the
+  // point's index in the tile, p summed over images, and sum p d / r_c^2
+  int *te_off;             // [n_tiles][EMD_TILE_ATOM_MAX + 1]
+  unsigned short *te_pt;   // [n_tiles][EMD_TE_CAP]
+  float *te_p;             // [n_tiles][EMD_TE_CAP]
+  float4 *te_q;            // [n_tiles][EMD_TE_CAP] (sum p d / r_c^2, p)
   int *tile_nat;    // [n_tiles] distinct atoms per tile
   int *tile_atoms;  // [n_tiles][EMD_TILE_ATOM_MAX] in atom order
   int *tile_off;    // [n_tiles] exclusive prefix sum of tile_nat
@@ -172,7 +181,7 @@ struct StageArgs {
 };
 struct OrbLayout {
   int n, n3, bo, n_blk, n_orb, n_orb_pad, prec, half_order, n_atoms;
-  int stage_variant;   // complex64 stage: 0 point-per-thread, 1 column-per-thread
+  int stage_variant;   // complex64 stage kernel (EMD_OPT_STAGE_VARIANT)
   double h;
   double w[EMD_MAX_HALF_ORDER + 1];   // w_0 = -3 c_0 / (2 h^2), w_k = -c_k/(2 h^2)
 };
@@ -241,3 +250,10 @@ void emd_adj_sr_hvp(const SpeciesDev &sp, int n_atoms, const double *Rw, double 
 void emd_adj_nl_force_r(const double2 *cc, const double2 *dc, const double2 *m,
                         const double *lamF, int n_atoms, int n_orb, int n_orb_pad,
                         double coef, double *out, cudaStream_t st);
+float emd_fp32_d2_margin(double L, double r);
+void emd_launch_project_tile(const OrbLayout &o, const TableSet &t, int n_atoms,
+                             const void *u, double h3, double h_kb, double2 *c,
+                             void *hc, double2 *partial, cudaStream_t st);
+void emd_launch_nl_force_tile(const OrbLayout &o, const TableSet &t, int n_atoms,
+                              const void *u, const double2 *c, double h3, double coef,
+                              double2 *partial, double *F_nl, cudaStream_t st);

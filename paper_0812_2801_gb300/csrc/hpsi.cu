@@ -394,6 +394,252 @@ k_stage_z(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
 }
 
 // ---------------------------------------------------------------------------
+// Lean column kernel: the tile, ring and delay line of k_stage_z, arranged so
+// that the per-update work is the arithmetic itself.  The ring depth (3)
+// divides the delay-line length (2M+1 = 9 for M = 4, 7 for M = 3 ...) only
+// for M = 1 and M = 4, so the group of planes unrolled at once is lcm-sized:
+// the ring slot of every plane is a compile-time constant.  Weight pairs are
+// kernel parameters, the shared-memory hc path is a template flag, output
+// and staging addresses are per-thread constants plus one plane offset, and
+// the centre term starts from the delay-line accumulator.
+// ---------------------------------------------------------------------------
+template <typename T> struct WPairs { float2 w[EMD_MAX_HALF_ORDER + 1]; };
+inline WPairs<float> wpairs_of(const OrbLayout &o) {
+  WPairs<float> r;
+  for (int k = 0; k <= EMD_MAX_HALF_ORDER; ++k) r.w[k] = make_float2((float)o.w[k], (float)o.w[k]);
+  return r;
+}
+
+template <int M> struct LeanGroup {
+  // planes unrolled per group: a multiple of both the ring depth 3 and 2M+1
+  static constexpr int NS = 2 * M + 1;
+  static constexpr int G = NS % 3 == 0 ? NS : 3 * NS;
+};
+
+template <int BO, int M, bool HCS>
+__global__ void __launch_bounds__(512, 1)
+k_stage_c(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
+          float2 *__restrict__ u_out, const float *__restrict__ v_eff,
+          const int2 *__restrict__ pt4, const int *__restrict__ pt_J,
+          const float *__restrict__ pt_pf, const float2 *__restrict__ hc,
+          int n, int ntx, int zc, int n_orb_pad, int n_atoms, float a,
+          int apply_only, WPairs<float> W) {
+  typedef ZTile<BO, M> Z;
+  constexpr int RY = Z::RY;
+  constexpr int NS = Z::NS;
+  constexpr int G = LeanGroup<M>::G;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2 *hcs = reinterpret_cast<float2 *>(smraw + Z::NB * Z::SLOT);
+  const int tid = threadIdx.x;
+  const int col = tid % Z::NC, tyr = tid / Z::NC;
+  const int xl = col / BO, j = col % BO;
+  const int tx0 = (blockIdx.x % ntx) * Z::TX, ty0 = (blockIdx.x / ntx) * Z::TY;
+  const int z0 = blockIdx.y * zc;
+  const int zcount = min(zc, n - z0);
+  const int total = zcount + 2 * M;
+  const int n2 = n * n;
+  const size_t n3 = (size_t)n2 * n;
+  const size_t boff = (size_t)blockIdx.z * n3 * BO;
+  const float2 *ub = u_in + boff;
+  const float2 *pb = psi0 + boff;
+  float2 *ob = u_out + boff;
+  const int x = tx0 + xl;
+
+  // staging: per-thread (global element offset within a plane, shared byte
+  // offset within a ring slot); -1 = nothing to copy
+  int src_off[Z::CPT];
+  unsigned dst_b[Z::CPT];
+#pragma unroll
+  for (int i = 0; i < Z::CPT; ++i) {
+    const int q = tid + i * Z::NT;
+    src_off[i] = -1;
+    dst_b[i] = 0;
+    if (q < Z::NCHUNK) {
+      const int hh = q % Z::CH, pnt = q / Z::CH;
+      const int c = pnt % Z::SW, rr = pnt / Z::SW;
+      const int xx = (tx0 - M + c + 2 * n) % n;
+      const int yy = (ty0 - M + rr + 2 * n) % n;
+      src_off[i] = (yy * n + xx) * BO + 2 * hh;
+      dst_b[i] = ((rr * Z::SW + c) * BO + 2 * hh) * 8;
+    }
+  }
+  int v_src = -1, s_src = -1, q_src[Z::QPT];
+  unsigned s_dst = 0, q_dst[Z::QPT];
+  if (tid < Z::NV) {
+    const int vx = tid % Z::TX, vy = tid / Z::TX;
+    v_src = ((ty0 + vy) % n) * n + (tx0 + vx) % n;
+  }
+  static_assert(Z::SPT <= 1, "one psi0 chunk per thread");
+#pragma unroll
+  for (int i = 0; i < Z::QPT; ++i) {
+    const int q = tid + i * Z::NT;
+    q_src[i] = -1;
+    q_dst[i] = 0;
+    if (q < 2 * Z::NV) {
+      const int pnt = q >> 1, half = q & 1;
+      const int xx = min(tx0 + pnt % Z::TX, n - 1), yy = min(ty0 + pnt / Z::TX, n - 1);
+      q_src[i] = (yy * n + xx) * 4 + 2 * half;
+      q_dst[i] = (pnt * 4 + 2 * half) * 8;
+    }
+  }
+  if (tid < Z::NV * Z::CH) {
+    const int pnt = tid / Z::CH, hh = tid % Z::CH;
+    const int xx = min(tx0 + pnt % Z::TX, n - 1), yy = min(ty0 + pnt / Z::TX, n - 1);
+    s_src = (yy * n + xx) * BO + 2 * hh;
+    s_dst = (pnt * BO + 2 * hh) * 8;
+  }
+  if (HCS) {
+    for (int i = tid; i < n_atoms * BO; i += Z::NT)
+      hcs[i] = hc[(size_t)(i / BO) * n_orb_pad + (size_t)blockIdx.z * BO + i % BO];
+  }
+  const unsigned sm0 = (unsigned)__cvta_generic_to_shared(smraw);
+
+  auto issue = [&](int zi, int slot) {
+    const unsigned base = sm0 + slot * Z::SLOT;
+    int zz = z0 - M + zi;
+    zz += zz < 0 ? n : 0;
+    zz -= zz >= n ? n : 0;
+    const size_t poff = (size_t)zz * n2;
+    const float2 *src = ub + poff * BO;
+#pragma unroll
+    for (int i = 0; i < Z::CPT; ++i)
+      if (src_off[i] >= 0)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + dst_b[i]),
+                     "l"(src + src_off[i]) : "memory");
+    if (v_src >= 0)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(base + Z::UB + tid * 4),
+                   "l"(v_eff + poff + v_src) : "memory");
+    if (zi >= 2 * M) {
+      const size_t zo = (size_t)(z0 + zi - 2 * M) * n2;
+#pragma unroll
+      for (int i = 0; i < Z::QPT; ++i)
+        if (q_src[i] >= 0)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + Z::UB + Z::VB + q_dst[i]),
+                       "l"(pt4 + zo * 4 + q_src[i]) : "memory");
+      if (!apply_only && s_src >= 0)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + Z::UB + Z::VB + Z::QB + s_dst),
+                     "l"(pb + zo * BO + s_src) : "memory");
+    }
+    cp_async_commit();
+  };
+
+  // per-thread output constants
+  int orow[RY];
+  bool oval[RY];
+#pragma unroll
+  for (int r = 0; r < RY; ++r) {
+    const int y = ty0 + tyr * RY + r;
+    oval[r] = x < n && y < n;
+    orow[r] = (y * n + x) * BO + j;
+  }
+  const int win0 = ((tyr * RY) * Z::SW + xl + M) * BO + j;     // float2 index
+  const int vp0 = (tyr * RY) * Z::TX + xl;
+  const int pnt0 = (tyr * RY) * Z::TX + xl;
+
+  float2 acc[RY][NS];
+#pragma unroll
+  for (int r = 0; r < RY; ++r)
+#pragma unroll
+    for (int q = 0; q < NS; ++q) acc[r][q] = make_float2(0.f, 0.f);
+
+  issue(0, 0);
+  if (total > 1) issue(1, 1);
+  for (int g = 0; g * G < total; ++g) {
+#pragma unroll
+    for (int ph = 0; ph < G; ++ph) {
+      const int zi = g * G + ph;
+      if (zi >= total) break;
+      const int sb = ph % 3;
+      const int dl = ph % NS;             // delay-line slot of this plane
+      if (zi + 2 < total) {
+        issue(zi + 2, (ph + 2) % 3);
+        cp_async_wait<2>();
+      } else if (zi + 1 < total) {
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      const unsigned char *base = smraw + sb * Z::SLOT;
+      const float2 *P = reinterpret_cast<const float2 *>(base);
+      const float *VP = reinterpret_cast<const float *>(base + Z::UB);
+      float2 win[RY + 2 * M];
+#pragma unroll
+      for (int w = 0; w < RY + 2 * M; ++w) win[w] = P[win0 + w * Z::SW * BO];
+#pragma unroll
+      for (int r = 0; r < RY; ++r) {
+        const float2 c = win[r + M];
+        const float2 *row = P + win0 + (r + M) * Z::SW * BO;
+        float2 s2 = __ffma2_rn(W.w[0], c, acc[r][dl]);
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+          const float2 t = __fadd2_rn(__fadd2_rn(row[k * BO], row[-k * BO]),
+                                      __fadd2_rn(win[r + M + k], win[r + M - k]));
+          s2 = __ffma2_rn(W.w[k], t, s2);
+        }
+        const float ve = VP[vp0 + r * Z::TX];
+        acc[r][dl] = __ffma2_rn(make_float2(ve, ve), c, s2);
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+          acc[r][(ph + k) % NS] = __ffma2_rn(W.w[k], c, acc[r][(ph + k) % NS]);
+          if (g > 0 || ph - k >= 0)
+            acc[r][(ph - k + G) % NS] = __ffma2_rn(W.w[k], c, acc[r][(ph - k + G) % NS]);
+        }
+      }
+      if (zi >= M) {
+        const int slot = (ph - M + G) % NS;
+        if (zi >= 2 * M) {
+          const size_t zo = (size_t)(z0 + zi - 2 * M) * n2;
+          const int4 *Q4 = reinterpret_cast<const int4 *>(base + Z::UB + Z::VB);
+          const float2 *S = reinterpret_cast<const float2 *>(base + Z::UB + Z::VB + Z::QB);
+          float2 *obz = ob + zo * BO;
+#pragma unroll
+          for (int r = 0; r < RY; ++r) {
+            if (oval[r]) {
+              const int pnt = pnt0 + r * Z::TX;
+              const int4 q01 = Q4[2 * pnt], q23 = Q4[2 * pnt + 1];
+              const int cnt = q01.x >> 16;
+              const int J[4] = {q01.x & 0xffff, q01.z, q23.x, q23.z};
+              const float pv[4] = {__int_as_float(q01.y), __int_as_float(q01.w),
+                                   __int_as_float(q23.y), __int_as_float(q23.w)};
+              float2 hv = acc[r][slot];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float2 hcv = HCS ? hcs[J[e] * BO + j]
+                                       : __ldg(hc + (size_t)J[e] * n_orb_pad +
+                                               (size_t)blockIdx.z * BO + j);
+                hv = __ffma2_rn(make_float2(pv[e], pv[e]), hcv, hv);
+              }
+              if (cnt > 4) {
+                const size_t p = zo + (size_t)(orow[r] - j) / BO;
+                for (int e = 4; e < cnt; ++e) {
+                  const int Je = __ldg(pt_J + (size_t)e * n3 + p);
+                  const float pe = __ldg(pt_pf + (size_t)e * n3 + p);
+                  const float2 hcv = HCS ? hcs[Je * BO + j]
+                                         : __ldg(hc + (size_t)Je * n_orb_pad +
+                                                 (size_t)blockIdx.z * BO + j);
+                  hv = __ffma2_rn(make_float2(pe, pe), hcv, hv);
+                }
+              }
+              float2 out = hv;
+              if (!apply_only) {
+                const float2 sv = S[pnt * BO + j];
+                out.x = __fmaf_rn(a, hv.y, sv.x);
+                out.y = __fmaf_rn(-a, hv.x, sv.y);
+              }
+              obz[orow[r]] = out;
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < RY; ++r) acc[r][slot] = make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Point-per-thread variant: each thread owns one grid point of a 32 x 16 tile
 // and all bo orbitals of the block there, so the per-point work (staging
 // offsets, v_eff, projector records, index arithmetic) is shared by the bo
@@ -984,6 +1230,46 @@ void stage_z_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
       (float)a.a, a.apply_only, weights_of<float>(o));
 }
 
+template <int BO, int M, bool HCS>
+void stage_c_tt(const OrbLayout &o, const StageArgs &a, size_t smem, cudaStream_t st) {
+  typedef ZTile<BO, M> Z;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_stage_c<BO, M, HCS>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(Z::SMEM_FIXED + 16384));
+    attr_done = true;
+  }
+  const int ntx = (o.n + Z::TX - 1) / Z::TX, nty = (o.n + Z::TY - 1) / Z::TY;
+  const int zc = o.n <= 64 ? o.n : (o.n + 1) / 2 <= 64 ? (o.n + 1) / 2 : 48;
+  dim3 grid(ntx * nty, (o.n + zc - 1) / zc, o.n_blk);
+  k_stage_c<BO, M, HCS><<<grid, Z::NT, smem, st>>>(
+      (const float2 *)a.u_in, (const float2 *)a.psi0, (float2 *)a.u_out,
+      (const float *)a.v_eff, a.tab->pt4, a.tab->pt_J, a.tab->pt_pf,
+      (const float2 *)a.hc, o.n, ntx, zc, o.n_orb_pad, o.n_atoms, (float)a.a,
+      a.apply_only, wpairs_of(o));
+}
+
+template <int BO, int M>
+void stage_c_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
+  typedef ZTile<BO, M> Z;
+  const int hc_bytes = o.n_atoms * BO * (int)sizeof(float2);
+  if (hc_bytes <= 16384)
+    stage_c_tt<BO, M, true>(o, a, Z::SMEM_FIXED + hc_bytes, st);
+  else
+    stage_c_tt<BO, M, false>(o, a, Z::SMEM_FIXED, st);
+}
+
+template <int BO>
+void stage_c_m(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
+  switch (o.half_order) {
+    case 1: stage_c_t<BO, 1>(o, a, st); break;
+    case 2: stage_c_t<BO, 2>(o, a, st); break;
+    case 3: stage_c_t<BO, 3>(o, a, st); break;
+    case 4: stage_c_t<BO, 4>(o, a, st); break;
+  }
+}
+
 template <int BO, int M, int RY>
 void stage_zp_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
   typedef ZPTile<BO, M, RY> Z;
@@ -1050,9 +1336,9 @@ void project_t(const OrbLayout &o, const TableSet &t, int n_atoms,
                cudaStream_t st) {
   typedef typename cplx<T>::type V;
   dim3 grid(n_atoms, o.n_blk);
-  k_project<T, BO><<<grid, 256, 0, st>>>((const V *)u, (size_t)o.n3, t.at_cnt,
-                                         t.at_pt, t.at_p, t.cap, h3, h_kb,
-                                         o.n_orb_pad, c, (V *)hc);
+    k_project<T, BO><<<grid, 256, 0, st>>>((const V *)u, (size_t)o.n3, t.at_cnt,
+                                           t.at_pt, t.at_p, t.cap, h3, h_kb,
+                                           o.n_orb_pad, c, (V *)hc);
 }
 
 template <typename T, int BO>
@@ -1092,10 +1378,10 @@ void nlf_t(const OrbLayout &o, const TableSet &t, int n_atoms, const void *u,
            double *part, cudaStream_t st) {
   typedef typename cplx<T>::type V;
   dim3 grid(n_atoms, o.n_blk);
-  k_nl_force<T, BO><<<grid, 256, 0, st>>>((const V *)u, (size_t)o.n3, o.n_blk,
-                                          t.at_cnt, t.at_pt, t.at_p, t.at_d,
-                                          t.cap, c, o.n_orb_pad, o.n_orb, h3,
-                                          coef, inv_rc2, part);
+    k_nl_force<T, BO><<<grid, 256, 0, st>>>((const V *)u, (size_t)o.n3, o.n_blk,
+                                            t.at_cnt, t.at_pt, t.at_p, t.at_d,
+                                            t.cap, c, o.n_orb_pad, o.n_orb, h3,
+                                            coef, inv_rc2, part);
 }
 
 template <typename T, int BO>
@@ -1133,9 +1419,13 @@ void emd_launch_stage(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
       case 2:
         if (o.stage_variant == 1) stage_z_m<2>(o, a, st);
         else if (o.stage_variant == 2) stage_zp_m<2, 1>(o, a, st);
-        else stage_zp_m<2, 2>(o, a, st);
+        else if (o.stage_variant == 3) stage_zp_m<2, 2>(o, a, st);
+        else stage_c_m<2>(o, a, st);
         break;
-      case 4: stage_z_m<4>(o, a, st); break;   // point-per-thread needs > 128 registers
+      case 4:   // point-per-thread needs > 128 registers
+        if (o.stage_variant == 1) stage_z_m<4>(o, a, st);
+        else stage_c_m<4>(o, a, st);
+        break;
     }
   }
 }

@@ -222,6 +222,199 @@ void project_pm_t(const OrbLayout &o, const TableSet &t, int n_atoms, const void
                                                 o.n_orb_pad, h3, h_kb, c, (V *)hc);
 }
 
+// ---------------------------------------------------------------------------
+// complex64 path: projections and nonlocal forces from the per-tile entry
+// lists of the point table.  A small CTA (4 warps) owns one 8^3 tile of one
+// orbital block: it stages the tile in shared memory (each point read once
+// from HBM), then warp w handles the tile's slots w, w + 4, ...: its lanes
+// stride over the slot's entries with FP32 per-lane sums, a fixed shuffle
+// tree reduces the warp, and lane 0 writes the slot's FP64 partial, orbital
+// index fastest.  Many such CTAs share an SM (16 KB of shared memory each),
+// so one CTA's latency chains overlap the others' loads.  A second kernel
+// adds each atom's partials over its tiles in a fixed order.
+// ---------------------------------------------------------------------------
+#define EMD_TG_WARPS 4
+
+__device__ __forceinline__ void cp16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp8(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+template <int NV>
+__device__ __forceinline__ void warp_sum(float (&v)[NV]) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    float a = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    v[k] = a;
+  }
+}
+
+// FORCE = false: partial[(tile_off[t] + s) * n_orb_pad + A] = sum p u_A
+// FORCE = true:  partial[((tile_off[t] + s) * n_orb_pad + A) * 3 + a]
+//                = sum (p d_a / r_c^2) u_A
+template <int BO, bool FORCE>
+__global__ void __launch_bounds__(EMD_TG_WARPS * 32)
+k_tile_gather(const float2 *__restrict__ u, int n, int nt, int n_orb_pad,
+              const int *__restrict__ tile_nat, const int *__restrict__ tile_off,
+              const int *__restrict__ te_off, const unsigned short *__restrict__ te_pt,
+              const float *__restrict__ te_p, const float4 *__restrict__ te_q,
+              double2 *__restrict__ partial) {
+  constexpr int NT = EMD_TG_WARPS * 32;
+  constexpr int NA = FORCE ? 6 * BO : 2 * BO;
+  __shared__ __align__(16) float2 us[512 * BO];
+  const int t = blockIdx.x, blk = blockIdx.y;
+  const int tx = t % nt, ty = (t / nt) % nt, tz = t / (nt * nt);
+  const size_t n3 = (size_t)n * n * n;
+  const float2 *ub = u + (size_t)blk * n3 * BO;
+  // stage: 512 points, BO float2 each, in 16-byte (8-byte for BO = 1) pieces
+  constexpr int PER = BO == 1 ? 1 : BO / 2;          // pieces per point
+  for (int q = threadIdx.x; q < 512 * PER; q += NT) {
+    const int pt = q / PER, h = q % PER;
+    const int x = tx * EMD_TILE + (pt & 7), y = ty * EMD_TILE + ((pt >> 3) & 7),
+              z = tz * EMD_TILE + (pt >> 6);
+    float2 *dst = us + pt * BO + 2 * h;
+    if (x < n && y < n && z < n) {
+      const float2 *src = ub + (((size_t)z * n + y) * n + x) * BO + 2 * h;
+      if (BO == 1) cp8(dst, src);
+      else cp16(dst, src);
+    } else {
+      dst[0] = make_float2(0.f, 0.f);
+      if (BO > 1) dst[1] = make_float2(0.f, 0.f);
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  const int S = tile_nat[t];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int *off = te_off + (size_t)t * (EMD_TILE_ATOM_MAX + 1);
+  const size_t tb = (size_t)t * EMD_TE_CAP;
+  const size_t row0 = (size_t)tile_off[t];
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  for (int sl = warp; sl < S; sl += EMD_TG_WARPS) {
+    float acc[NA];
+#pragma unroll
+    for (int k = 0; k < NA; ++k) acc[k] = 0.f;
+    const int e1 = off[sl + 1];
+    for (int e = off[sl] + lane; e < e1; e += 32) {
+      const int q = __ldg(te_pt + tb + e);
+      if (FORCE) {
+        const float4 w = __ldg(te_q + tb + e);
+#pragma unroll
+        for (int j = 0; j < BO; ++j) {
+          const float2 v = us[q * BO + j];
+          acc[6 * j + 0] += w.x * v.x;
+          acc[6 * j + 1] += w.x * v.y;
+          acc[6 * j + 2] += w.y * v.x;
+          acc[6 * j + 3] += w.y * v.y;
+          acc[6 * j + 4] += w.z * v.x;
+          acc[6 * j + 5] += w.z * v.y;
+        }
+      } else {
+        const float pv = __ldg(te_p + tb + e);
+#pragma unroll
+        for (int j = 0; j < BO; ++j) {
+          const float2 v = us[q * BO + j];
+          acc[2 * j] += pv * v.x;
+          acc[2 * j + 1] += pv * v.y;
+        }
+      }
+    }
+    warp_sum<NA>(acc);
+    if (lane == 0) {
+      double2 *dst = partial + ((row0 + sl) * n_orb_pad + (size_t)blk * BO) * (FORCE ? 3 : 1);
+#pragma unroll
+      for (int k = 0; k < NA / 2; ++k)
+        dst[k] = make_double2((double)acc[2 * k], (double)acc[2 * k + 1]);
+    }
+  }
+}
+
+// c[J][A] = h^3 sum over J's (tile, slot) list; hc = h_kb c.  Block
+// (atom, 32 orbitals), 8 warps: warp w adds the list entries i = w mod 8 in
+// increasing order (lane = orbital), then the 8 warp sums are added in warp
+// order (deterministic).
+__global__ void __launch_bounds__(256)
+k_project_tile_reduce(const double2 *__restrict__ partial, const int *__restrict__ at_ntiles,
+                      const int2 *__restrict__ at_tiles, int cap,
+                      const int *__restrict__ tile_off, int n_orb_pad, int n_orb_used,
+                      double h3, double h_kb, double2 *c, float2 *hc) {
+  __shared__ double2 ws[8][32];
+  const int J = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int A = blockIdx.y * 32 + lane;
+  const int m = at_ntiles[J];
+  double re = 0.0, im = 0.0;
+  if (A < n_orb_used) {
+#pragma unroll 4
+    for (int i = warp; i < m; i += 8) {
+      const int2 ts = __ldg(at_tiles + (size_t)J * cap + i);
+      const double2 v = partial[((size_t)__ldg(tile_off + ts.x) + ts.y) * n_orb_pad + A];
+      re += v.x;
+      im += v.y;
+    }
+  }
+  ws[warp][lane] = make_double2(re, im);
+  __syncthreads();
+  if (warp == 0 && A < n_orb_used) {
+    re = 0.0;
+    im = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      re += ws[w][lane].x;
+      im += ws[w][lane].y;
+    }
+    const size_t o = (size_t)J * n_orb_pad + A;
+    c[o] = make_double2(h3 * re, h3 * im);
+    hc[o] = make_float2((float)(h_kb * h3 * re), (float)(h_kb * h3 * im));
+  }
+}
+
+// F_J = coef sum_A Re(conj(c_JA) h^3 dc_JA), dc summed over J's tiles in
+// tile order; one block per atom, orbitals over threads, fixed-tree sum.
+__global__ void __launch_bounds__(128)
+k_nl_force_tile_reduce(const double2 *__restrict__ partial, const int *__restrict__ at_ntiles,
+                       const int2 *__restrict__ at_tiles, int cap,
+                       const int *__restrict__ tile_off, const double2 *__restrict__ c,
+                       int n_orb, int n_orb_pad, double h3, double coef, double *F) {
+  __shared__ double red[4 * 3];
+  const int J = blockIdx.x;
+  const int m = at_ntiles[J];
+  double f[3] = {0.0, 0.0, 0.0};
+  for (int A = threadIdx.x; A < n_orb; A += blockDim.x) {
+    double dr[3] = {0.0, 0.0, 0.0}, di[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < m; ++i) {
+      const int2 ts = at_tiles[(size_t)J * cap + i];
+      const double2 *v = partial + (((size_t)tile_off[ts.x] + ts.y) * n_orb_pad + A) * 3;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        dr[a] += v[a].x;
+        di[a] += v[a].y;
+      }
+    }
+    const double2 cj = c[(size_t)J * n_orb_pad + A];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) f[a] += cj.x * (h3 * dr[a]) + cj.y * (h3 * di[a]);
+  }
+  emd_block_sum<3>(f, red);
+  if (threadIdx.x == 0)
+    for (int a = 0; a < 3; ++a) F[3 * J + a] = coef * f[a];
+}
+
+template <int BO, bool FORCE>
+void tile_gather_t(const OrbLayout &o, const TableSet &t, const void *u, double2 *partial,
+                   cudaStream_t st) {
+  const int nt = (o.n + EMD_TILE - 1) / EMD_TILE;
+  dim3 grid(nt * nt * nt, o.n_blk);
+  k_tile_gather<BO, FORCE><<<grid, EMD_TG_WARPS * 32, 0, st>>>(
+      (const float2 *)u, o.n, nt, o.n_orb_pad, t.tile_nat, t.tile_off, t.te_off, t.te_pt,
+      t.te_p, t.te_q, partial);
+}
+
 }  // namespace
 
 void emd_launch_tile_atoms(const GridInfo &g, int n_atoms, TableSet &t, int *err,
@@ -255,4 +448,38 @@ void emd_launch_project_pm(const OrbLayout &o, const TableSet &t, int n_atoms,
       case 4: project_pm_t<float, 4>(o, t, n_atoms, u, h3, h_kb, c, hc, partial, st); break;
     }
   }
+}
+
+void emd_launch_project_tile(const OrbLayout &o, const TableSet &t, int n_atoms,
+                             const void *u, double h3, double h_kb, double2 *c,
+                             void *hc, double2 *partial, cudaStream_t st) {
+  if (n_atoms <= 0) return;
+  emd_note_launches(2);
+  switch (o.bo) {
+    case 1: tile_gather_t<1, false>(o, t, u, partial, st); break;
+    case 2: tile_gather_t<2, false>(o, t, u, partial, st); break;
+    case 4: tile_gather_t<4, false>(o, t, u, partial, st); break;
+  }
+  const int nt = (o.n + EMD_TILE - 1) / EMD_TILE;
+  const int used = o.n_blk * o.bo;
+  dim3 g2(n_atoms, (used + 31) / 32);
+  k_project_tile_reduce<<<g2, 256, 0, st>>>(partial, t.at_ntiles, t.at_tiles, nt * nt * nt,
+                                           t.tile_off, o.n_orb_pad, used, h3, h_kb, c,
+                                           (float2 *)hc);
+}
+
+void emd_launch_nl_force_tile(const OrbLayout &o, const TableSet &t, int n_atoms,
+                              const void *u, const double2 *c, double h3, double coef,
+                              double2 *partial, double *F_nl, cudaStream_t st) {
+  if (n_atoms <= 0) return;
+  emd_note_launches(2);
+  switch (o.bo) {
+    case 1: tile_gather_t<1, true>(o, t, u, partial, st); break;
+    case 2: tile_gather_t<2, true>(o, t, u, partial, st); break;
+    case 4: tile_gather_t<4, true>(o, t, u, partial, st); break;
+  }
+  const int nt = (o.n + EMD_TILE - 1) / EMD_TILE;
+  k_nl_force_tile_reduce<<<n_atoms, 128, 0, st>>>(partial, t.at_ntiles, t.at_tiles,
+                                                 nt * nt * nt, t.tile_off, c, o.n_orb,
+                                                 o.n_orb_pad, h3, coef, F_nl);
 }

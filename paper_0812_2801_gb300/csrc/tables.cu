@@ -10,6 +10,18 @@
 // ions (Sec. 5.1).
 #include "emd_internal.cuh"
 
+#include <cmath>
+
+// Bound on |d^2_FP32 - d^2| for a point of the image boxes of a sphere of
+// radius r in a box of side L: each coordinate difference (i h - (R + n L),
+// all terms below 2L + r in size) is off by at most ~4 FP32 roundings of
+// 2L + r, and d^2 near r^2 amplifies that by 2 sqrt(3) r, plus the roundings
+// of the squares and sums; a factor 8 on top.
+float emd_fp32_d2_margin(double L, double r) {
+  const double ex = 4.0 * 5.97e-8 * (2.0 * L + r + 1.0);
+  return (float)(8.0 * (2.0 * std::sqrt(3.0) * r * ex + ex * ex + 4.0 * 5.97e-8 * r * r));
+}
+
 namespace {
 
 __global__ void k_wrap(const double *R, double *Rw, int n, double L) {
@@ -78,68 +90,194 @@ k_tile_candidates(int n, double h, double L, const double *Rw, int n_atoms,
 
 // Point-major table: for each grid point the atoms whose projector reaches it
 // (p summed over that atom's images), in increasing atom order; and the total
-// Gaussian ion charge at the point.  One block = one tile.
+// Gaussian ion charge at the point.  One block = one tile, one thread = one
+// point.  FP32 distances settle the support decisions away from a thin shell
+// around each radius; FP64 computes the decisions inside it and every stored
+// FP64 value (the ion charge always, p when F32 = false).  With F32 = true
+// (complex64 path) p is evaluated in FP32, the precision its readers use,
+// and the block also writes the tile's entries grouped by atom (te_*): the
+// tile's distinct atoms (slots) are the runs of equal J in its candidate
+// list, and the points of each slot are compacted in point order.
+template <bool F32>
 __global__ void __launch_bounds__(512)
 k_point_table(int n, int n3, double h, double L, const double *Rw,
-              SpeciesDev sp, const int *tile_cnt, const int *tile_ent,
+              SpeciesDev sp, float margin, const int *tile_cnt, const int *tile_ent,
               int *pt_cnt, int *pt_J, double *pt_p, float *pt_pf, int2 *pt4,
-              double *g_ion, int *err) {
+              double *g_ion, int *te_off, unsigned short *te_pt, float *te_p,
+              float4 *te_q, int *err) {
   __shared__ int cand[EMD_TILE_CAND_MAX];
+  __shared__ float cfs[EMD_TILE_CAND_MAX][3];
+  __shared__ int run_start[EMD_TILE_ATOM_MAX + 1];
+  __shared__ int s_nrun;
+  __shared__ int warp_tot[16];
   const int nt = (n + EMD_TILE - 1) / EMD_TILE;
   const int t = blockIdx.x;
   const int tx = t % nt, ty = (t / nt) % nt, tz = t / (nt * nt);
   const int nc = tile_cnt[t];
-  for (int i = threadIdx.x; i < nc; i += blockDim.x)
-    cand[i] = tile_ent[t * EMD_TILE_CAND_MAX + i];
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    const int code = tile_ent[t * EMD_TILE_CAND_MAX + i];
+    const int J = code / 27, img = code % 27;
+    cand[i] = code;
+    cfs[i][0] = (float)(Rw[3 * J + 0] + (img % 3 - 1) * L);
+    cfs[i][1] = (float)(Rw[3 * J + 1] + ((img / 3) % 3 - 1) * L);
+    cfs[i][2] = (float)(Rw[3 * J + 2] + (img / 9 - 1) * L);
+  }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    // runs of equal atom in the (atom, image)-ordered candidate list
+    int r = 0, last = -1;
+    for (int i = 0; i < nc; ++i) {
+      const int J = cand[i] / 27;
+      if (J != last) {
+        if (r < EMD_TILE_ATOM_MAX) run_start[r] = i;
+        ++r;
+        last = J;
+      }
+    }
+    if (r > EMD_TILE_ATOM_MAX) {
+      if (F32) atomicOr(err, EMD_ERRBIT_TILE);
+      r = EMD_TILE_ATOM_MAX;   // (F32 = false: the runs are only a loop structure)
+    }
+    // with F32 = false every candidate must still be visited: one run per
+    // slot is kept and the last run extends to the end of the list
+    run_start[r] = nc;
+    s_nrun = r;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int x = tx * EMD_TILE + (threadIdx.x & 7);
   const int y = ty * EMD_TILE + ((threadIdx.x >> 3) & 7);
   const int z = tz * EMD_TILE + (threadIdx.x >> 6);
-  if (x >= n || y >= n || z >= n) return;
-  const int p = (z * n + y) * n + x;
+  const bool in = x < n && y < n && z < n;
+  const int p = in ? (z * n + y) * n + x : 0;
   const double rp2 = __dmul_rn(sp.r_proj, sp.r_proj);
   const double rl2 = __dmul_rn(sp.r_loc, sp.r_loc);
-  int cnt = 0, curJ = -1;
-  double psum = 0.0, gsum = 0.0;
-  bool hit = false;
-  for (int e = 0; e < nc; ++e) {
-    const int code = cand[e];
-    const int J = code / 27, img = code % 27;
-    if (J != curJ) {
-      if (hit) {
+  const float rp2f = (float)rp2, rl2f = (float)rl2, hf = (float)h;
+  const float rmax2f = fmaxf(rp2f, rl2f) + margin;
+  const float xf = (float)x * hf, yf = (float)y * hf, zf = (float)z * hf;
+  const int nrun = s_nrun;
+  int cnt = 0;
+  double gsum = 0.0;
+  int te_base = 0;
+  for (int r = 0; r < nrun; ++r) {
+    double psum = 0.0;
+    float psumf = 0.f, pdx = 0.f, pdy = 0.f, pdz = 0.f;
+    bool hit = false;
+    int J = -1;
+    for (int e = run_start[r]; e < run_start[r + 1]; ++e) {
+      const int code = cand[e];
+      const int Je = code / 27, img = code % 27;
+      if (!F32 && Je != J && hit) {
+        // F32 = false with more than EMD_TILE_ATOM_MAX atoms: the last run
+        // holds several atoms; close the previous one
         if (cnt < EMD_PT_KMAX) {
-          pt_J[cnt * n3 + p] = curJ;
+          pt_J[cnt * n3 + p] = J;
           pt_p[cnt * n3 + p] = psum;
           pt_pf[cnt * n3 + p] = (float)psum;
           ++cnt;
         } else {
           atomicOr(err, EMD_ERRBIT_PT);
         }
+        psum = 0.0;
+        hit = false;
       }
-      curJ = J;
-      psum = 0.0;
-      hit = false;
+      J = Je;
+      if (!in) continue;
+      const float dxf = xf - cfs[e][0], dyf = yf - cfs[e][1], dzf = zf - cfs[e][2];
+      const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+      if (d2f > rmax2f) continue;
+      // decisions: FP32 where it is certain, FP64 in the shells
+      bool in_p, in_l;
+      double d2 = 0.0;
+      bool have64 = false;
+      if (d2f < rp2f - margin) {
+        in_p = true;
+      } else if (d2f > rp2f + margin) {
+        in_p = false;
+      } else {
+        const double dx = emd_disp(x, h, Rw[3 * J + 0], img % 3 - 1, L);
+        const double dy = emd_disp(y, h, Rw[3 * J + 1], (img / 3) % 3 - 1, L);
+        const double dz = emd_disp(z, h, Rw[3 * J + 2], img / 9 - 1, L);
+        d2 = emd_norm2(dx, dy, dz);
+        have64 = true;
+        in_p = d2 < rp2;
+      }
+      if (d2f < rl2f - margin) {
+        in_l = true;
+      } else if (d2f > rl2f + margin) {
+        in_l = false;
+      } else {
+        if (!have64) {
+          const double dx = emd_disp(x, h, Rw[3 * J + 0], img % 3 - 1, L);
+          const double dy = emd_disp(y, h, Rw[3 * J + 1], (img / 3) % 3 - 1, L);
+          const double dz = emd_disp(z, h, Rw[3 * J + 2], img / 9 - 1, L);
+          d2 = emd_norm2(dx, dy, dz);
+          have64 = true;
+        }
+        in_l = d2 < rl2;
+      }
+      if (!have64 && (in_l || (in_p && !F32))) {
+        const double dx = emd_disp(x, h, Rw[3 * J + 0], img % 3 - 1, L);
+        const double dy = emd_disp(y, h, Rw[3 * J + 1], (img / 3) % 3 - 1, L);
+        const double dz = emd_disp(z, h, Rw[3 * J + 2], img / 9 - 1, L);
+        d2 = emd_norm2(dx, dy, dz);
+      }
+      if (in_p) {
+        if (F32) {
+          const float pv = (float)sp.c_p * expf(-d2f * (float)sp.inv_2rc2);
+          const float w = pv * (float)sp.inv_rc2;
+          psumf += pv;
+          pdx += w * dxf;
+          pdy += w * dyf;
+          pdz += w * dzf;
+        } else {
+          psum += sp.c_p * exp(-d2 * sp.inv_2rc2);
+        }
+        hit = true;
+      }
+      if (in_l) gsum += sp.c_g * exp(-d2 * sp.inv_a2);
     }
-    const double dx = emd_disp(x, h, Rw[3 * J + 0], img % 3 - 1, L);
-    const double dy = emd_disp(y, h, Rw[3 * J + 1], (img / 3) % 3 - 1, L);
-    const double dz = emd_disp(z, h, Rw[3 * J + 2], img / 9 - 1, L);
-    const double d2 = emd_norm2(dx, dy, dz);
-    if (d2 < rp2) {
-      psum += sp.c_p * exp(-d2 * sp.inv_2rc2);
-      hit = true;
+    if (hit) {
+      if (cnt < EMD_PT_KMAX) {
+        pt_J[cnt * n3 + p] = J;
+        pt_p[cnt * n3 + p] = F32 ? (double)psumf : psum;
+        pt_pf[cnt * n3 + p] = F32 ? psumf : (float)psum;
+        ++cnt;
+      } else {
+        atomicOr(err, EMD_ERRBIT_PT);
+      }
     }
-    if (d2 < rl2) gsum += sp.c_g * exp(-d2 * sp.inv_a2);
+    if (F32) {
+      // compaction of this slot's points, in point order
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (lane == 0) warp_tot[warp] = __popc(m);
+      __syncthreads();
+      int off = te_base, tot = 0;
+      for (int w = 0; w < 16; ++w) {
+        if (w < warp) off += warp_tot[w];
+        tot += warp_tot[w];
+      }
+      if (hit) {
+        const int e = off + __popc(m & ((1u << lane) - 1u));
+        if (e < EMD_TE_CAP) {
+          const size_t q = (size_t)t * EMD_TE_CAP + e;
+          te_pt[q] = (unsigned short)threadIdx.x;
+          te_p[q] = psumf;
+          te_q[q] = make_float4(pdx, pdy, pdz, psumf);
+        } else {
+          atomicOr(err, EMD_ERRBIT_TILE);
+        }
+      }
+      if (threadIdx.x == 0) te_off[t * (EMD_TILE_ATOM_MAX + 1) + r] = min(te_base, EMD_TE_CAP);
+      te_base += tot;
+      __syncthreads();
+    }
   }
-  if (hit) {
-    if (cnt < EMD_PT_KMAX) {
-      pt_J[cnt * n3 + p] = curJ;
-      pt_p[cnt * n3 + p] = psum;
-      pt_pf[cnt * n3 + p] = (float)psum;
-      ++cnt;
-    } else {
-      atomicOr(err, EMD_ERRBIT_PT);
-    }
+  if (F32 && threadIdx.x == 0) {
+    for (int r = nrun; r <= EMD_TILE_ATOM_MAX; ++r)
+      te_off[t * (EMD_TILE_ATOM_MAX + 1) + r] = min(te_base, EMD_TE_CAP);
   }
+  if (!in) return;
   pt_cnt[p] = cnt;
   g_ion[p] = gsum;
   for (int e = 0; e < 4; ++e) {
@@ -188,23 +326,35 @@ __device__ void image_boxes(const double *c, double L, double h, double r,
 // Grid (atom, split): the flattened box space of the atom is cut into
 // `nsplit` contiguous ranges.  Pass 0 counts the hits of each range; pass 1
 // writes them at the offset given by the counts of the earlier ranges.
+// The decision d^2 < r^2 is the FP64 one; FP32 settles it wherever the FP32
+// d^2 is farther than `margin` (a bound on its error, set by the host) from
+// r^2, so FP64 arithmetic runs only in a thin shell (and for the stored
+// FP64 values of the hits).  Built for the complex128 path
+// only (the complex64 kernels read the per-tile entries of the point table).
 __global__ void __launch_bounds__(256)
 k_atom_table(int pass, int n, double h, double L, const double *Rw,
-             SpeciesDev sp, int cap, int *split_cnt, int *at_cnt, int *at_pt,
-             double *at_p, double *at_d, int *err) {
+             SpeciesDev sp, int cap, float margin, int *split_cnt, int *at_cnt,
+             int *at_pt, double *at_p, double *at_d, int *err) {
   __shared__ ImageBoxes B;
+  __shared__ float cf[27][3];
   __shared__ int warp_tot[8];
   __shared__ int s_base;
   const int J = blockIdx.x, split = blockIdx.y, nsplit = gridDim.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double c[3] = {Rw[3 * J], Rw[3 * J + 1], Rw[3 * J + 2]};
   const double rp2 = __dmul_rn(sp.r_proj, sp.r_proj);
+  const float rp2f = (float)rp2, hf = (float)h;
   if (threadIdx.x == 0) {
     image_boxes(c, L, h, sp.r_proj, n, B);
     int base = 0;
     if (pass == 1)
       for (int s2 = 0; s2 < split; ++s2) base += split_cnt[J * nsplit + s2];
     s_base = base;
+  }
+  if (threadIdx.x < 81) {
+    const int img = threadIdx.x / 3, a = threadIdx.x % 3;
+    const int ni = a == 0 ? img % 3 - 1 : a == 1 ? (img / 3) % 3 - 1 : img / 9 - 1;
+    cf[img][a] = (float)(c[a] + ni * L);
   }
   __syncthreads();
   const int total = B.start[27];
@@ -214,21 +364,28 @@ k_atom_table(int pass, int n, double h, double L, const double *Rw,
   for (int b0 = f0; b0 < f1; b0 += blockDim.x) {
     const int f = b0 + threadIdx.x;
     bool flag = false;
-    double dx = 0, dy = 0, dz = 0, d2 = 0;
-    int pidx = 0;
+    int ix = 0, iy = 0, iz = 0;
+    float dxf = 0.f, dyf = 0.f, dzf = 0.f, d2f = 0.f;
     if (f < f1) {
       while (img < 26 && f >= B.start[img + 1]) ++img;
       const int k = f - B.start[img];
       const int ex = B.ext[img][0], ey = B.ext[img][1];
-      const int ix = B.lo[img][0] + k % ex, iy = B.lo[img][1] + (k / ex) % ey,
-                iz = B.lo[img][2] + k / (ex * ey);
-      const int ni[3] = {img % 3 - 1, (img / 3) % 3 - 1, img / 9 - 1};
-      dx = emd_disp(ix, h, c[0], ni[0], L);
-      dy = emd_disp(iy, h, c[1], ni[1], L);
-      dz = emd_disp(iz, h, c[2], ni[2], L);
-      d2 = emd_norm2(dx, dy, dz);
-      flag = d2 < rp2;
-      pidx = (iz * n + iy) * n + ix;
+      ix = B.lo[img][0] + k % ex;
+      iy = B.lo[img][1] + (k / ex) % ey;
+      iz = B.lo[img][2] + k / (ex * ey);
+      dxf = (float)ix * hf - cf[img][0];
+      dyf = (float)iy * hf - cf[img][1];
+      dzf = (float)iz * hf - cf[img][2];
+      d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+      if (d2f < rp2f - margin) {
+        flag = true;
+      } else if (d2f <= rp2f + margin) {
+        const int ni[3] = {img % 3 - 1, (img / 3) % 3 - 1, img / 9 - 1};
+        const double dx = emd_disp(ix, h, c[0], ni[0], L);
+        const double dy = emd_disp(iy, h, c[1], ni[1], L);
+        const double dz = emd_disp(iz, h, c[2], ni[2], L);
+        flag = emd_norm2(dx, dy, dz) < rp2;
+      }
     }
     const unsigned m = __ballot_sync(0xffffffffu, flag);
     if (lane == 0) warp_tot[warp] = __popc(m);
@@ -241,9 +398,14 @@ k_atom_table(int pass, int n, double h, double L, const double *Rw,
     if (pass == 1 && flag) {
       const int e = off + __popc(m & ((1u << lane) - 1u));
       if (e < cap) {
-        at_pt[(size_t)J * cap + e] = pidx;
-        at_p[(size_t)J * cap + e] = sp.c_p * exp(-d2 * sp.inv_2rc2);
-        double *dd = at_d + 3 * ((size_t)J * cap + e);
+        const size_t q = (size_t)J * cap + e;
+        at_pt[q] = (iz * n + iy) * n + ix;
+        const int ni[3] = {img % 3 - 1, (img / 3) % 3 - 1, img / 9 - 1};
+        const double dx = emd_disp(ix, h, c[0], ni[0], L);
+        const double dy = emd_disp(iy, h, c[1], ni[1], L);
+        const double dz = emd_disp(iz, h, c[2], ni[2], L);
+        at_p[q] = sp.c_p * exp(-emd_norm2(dx, dy, dz) * sp.inv_2rc2);
+        double *dd = at_d + 3 * q;
         dd[0] = dx;
         dd[1] = dy;
         dd[2] = dz;
@@ -412,18 +574,24 @@ void emd_launch_tables(const GridInfo &g, const SpeciesDev &sp, int n_atoms,
   const float rmax = (float)fmax(sp.r_proj, sp.r_loc);
   k_tile_candidates<<<ntiles, 256, 0, st>>>(
       g.n, g.h, g.L, t.Rw, n_atoms, rmax, t.tile_cnt, t.tile_ent, err);
-  k_point_table<<<ntiles, 512, 0, st>>>(g.n, g.n3, g.h, g.L, t.Rw, sp,
-                                        t.tile_cnt, t.tile_ent, t.pt_cnt,
-                                        t.pt_J, t.pt_p, t.pt_pf, t.pt4, t.g_ion,
-                                        err);
-  if (n_atoms > 0) {
+  const float margin_pt = emd_fp32_d2_margin(g.L, fmax(sp.r_proj, sp.r_loc));
+  if (t.te_off)
+    k_point_table<true><<<ntiles, 512, 0, st>>>(g.n, g.n3, g.h, g.L, t.Rw, sp, margin_pt,
+                                                t.tile_cnt, t.tile_ent, t.pt_cnt,
+                                                t.pt_J, t.pt_p, t.pt_pf, t.pt4, t.g_ion,
+                                                t.te_off, t.te_pt, t.te_p, t.te_q, err);
+  else
+    k_point_table<false><<<ntiles, 512, 0, st>>>(g.n, g.n3, g.h, g.L, t.Rw, sp, margin_pt,
+                                                 t.tile_cnt, t.tile_ent, t.pt_cnt,
+                                                 t.pt_J, t.pt_p, t.pt_pf, t.pt4, t.g_ion,
+                                                 t.te_off, t.te_pt, t.te_p, t.te_q, err);
+  if (n_atoms > 0 && !t.te_off) {
     dim3 grid(n_atoms, EMD_SPLIT);
-    k_atom_table<<<grid, 256, 0, st>>>(0, g.n, g.h, g.L, t.Rw, sp, t.cap,
-                                       t.split_cnt, t.at_cnt, t.at_pt, t.at_p,
-                                       t.at_d, err);
-    k_atom_table<<<grid, 256, 0, st>>>(1, g.n, g.h, g.L, t.Rw, sp, t.cap,
-                                       t.split_cnt, t.at_cnt, t.at_pt, t.at_p,
-                                       t.at_d, err);
+    const float margin = emd_fp32_d2_margin(g.L, sp.r_proj);
+    for (int pass = 0; pass < 2; ++pass)
+      k_atom_table<<<grid, 256, 0, st>>>(pass, g.n, g.h, g.L, t.Rw, sp, t.cap, margin,
+                                         t.split_cnt, t.at_cnt, t.at_pt, t.at_p, t.at_d,
+                                         err);
   }
 }
 

@@ -161,3 +161,16 @@ def test_gpu_moving_ion_adjoint_continues_dynamics():
     emd.emd_destroy(h)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+def test_autograd_function_moving_ions():
+    s = small()
+    s.V = s.V * 200.0
+    field = np.linspace(-0.01, 0.01, 4)
+    L, dR, df, _, _ = gpu_grad_md(s, field, 4, 0.05, 1.0, 2, "energy")
+    R = torch.tensor(s.R, requires_grad=True)
+    f = torch.tensor(field, requires_grad=True)
+    out = gadj.ObservableGrad.apply(R, f, s, 4, 0.05, 1.0, 2, "energy", torch.tensor(s.V))
+    gR, gf = torch.autograd.grad(out, [R, f])
+    assert float(out.detach()) == L
+    assert np.array_equal(gR.numpy(), dR) and np.array_equal(gf.numpy(), df)

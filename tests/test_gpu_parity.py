@@ -223,3 +223,49 @@ def test_point_major_projections_equal_atom_major(prec, tol):
         out.append(emd.emd_get_projections(g.handle, s.n_atoms, s.n_orb))
         g.close()
     assert np.max(np.abs(out[0] - out[1])) <= tol * np.max(np.abs(out[1]))
+
+
+@pytest.mark.parametrize("bo,variant", [(2, 0), (2, 1), (2, 2), (2, 3), (4, 0), (4, 1)])
+@pytest.mark.parametrize("order", [4, 8])
+def test_fp32_stage_variants(bo, variant, order):
+    """Every complex64 Horner-stage kernel: H psi against the FP64 oracle with
+    8 atoms on a 33^3 grid (up to 8 projectors per point, so the records past
+    the first four are read), and 4 MD steps against the FP64 path."""
+    s = inputs.small_system(n=33, h=0.32, fd_order=order, n_atoms=8, seed=21, n_orb=6)
+    st = O.init_state(s)
+    per_point = np.zeros(s.n ** 3, dtype=int)
+    for idx, _ in st.tables.pmerged:
+        per_point[idx] += 1
+    assert per_point.max() >= 5
+    g = emd.System(s, emd.EMD_FP32_ORBITALS, block_orbitals=bo)
+    emd.emd_set_option(g.handle, emd.EMD_OPT_STAGE_VARIANT, variant)
+    rng = np.random.default_rng(4)
+    u = rng.normal(size=(5, s.n, s.n, s.n)) + 1j * rng.normal(size=(5, s.n, s.n, s.n))
+    H = O.Hamiltonian(st.v_loc + st.v_h + st.v_xc, st.tables, s.species, s.h, s.fd_order)
+    got = emd.emd_apply_hamiltonian(g.handle, u)
+    assert rel(got, H.apply(u)) < 3e-6
+    g.propagate(4, dt=0.04, mu=1.0)
+    psi32 = g.state()[2]
+    F32 = g.forces()
+    g.close()
+    g = emd.System(s, emd.EMD_FP64)
+    g.propagate(4, dt=0.04, mu=1.0)
+    psi64 = g.state()[2]
+    F64 = g.forces()
+    g.close()
+    assert np.max(np.abs(psi32 - psi64)) < 1e-5
+    assert rel(F32, F64) < 1e-4
+
+
+def test_fp32_tile_projections_and_forces(small):
+    """complex64 path (per-tile entry lists): projections of the uploaded
+    orbitals against the oracle's projections of the same complex64 values,
+    and the initial forces against the oracle's FP64 forces."""
+    s = small
+    g = emd.System(s, emd.EMD_FP32_ORBITALS)
+    st = O.init_state(s)
+    psi32 = s.psi.astype(np.complex64).astype(np.complex128)
+    c = emd.emd_get_projections(g.handle, s.n_atoms, s.n_orb)
+    assert rel(c, O.projections(psi32, st.tables, s.species, s.h)) < 2e-6
+    assert rel(g.forces(), st.F) < 1e-5
+    g.close()
