@@ -102,6 +102,7 @@ struct emd_system {
   double2 *stage_buf = nullptr;   // canonical staging for one orbital block
   double *veff1 = nullptr, *veff2 = nullptr;
   float *veff1f = nullptr, *veff2f = nullptr;
+  float4 *veff1d = nullptr, *veff2d = nullptr;   // complex64: (w_0 + v_eff) x4
   double *hist[3] = {nullptr, nullptr, nullptr};
   int hist_len = 0;
   double *rho = nullptr, *v_h = nullptr, *v_xc = nullptr, *eps_xc = nullptr;
@@ -203,10 +204,12 @@ void stage(emd_system *s, const void *u_in, const void *psi0, void *u_out,
   a_.u_in = u_in;
   a_.psi0 = psi0;
   a_.u_out = u_out;
-  if (s->o.prec == EMD_FP64)
+  if (s->o.prec == EMD_FP64) {
     a_.v_eff = which_veff == 1 ? (const void *)s->veff1 : (const void *)s->veff2;
-  else
+  } else {
     a_.v_eff = which_veff == 1 ? (const void *)s->veff1f : (const void *)s->veff2f;
+    a_.v_diag = which_veff == 1 ? (const void *)s->veff1d : (const void *)s->veff2d;
+  }
   a_.tab = &s->ts[set];
   a_.hc = s->hc;
   a_.a = a;
@@ -429,6 +432,8 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
   if (c.precision != EMD_FP64) {
     TRY(A((void **)&s->veff1f, n3 * 4));
     TRY(A((void **)&s->veff2f, n3 * 4));
+    TRY(A((void **)&s->veff1d, n3 * 16));
+    TRY(A((void **)&s->veff2d, n3 * 16));
   }
   for (int k = 0; k < 3; ++k) TRY(A((void **)&s->hist[k], n3 * 8));
   TRY(A((void **)&s->rho, n3 * 8));
@@ -643,9 +648,9 @@ int step_once(emd_system *s, double dt, double mu, double e) {
     negate_grid(s->ts[nw].v_loc, s->g.n3, s->st);
   }
   emd_launch_veff(s->g, s->ts[cur].v_loc, s->hist, 1, e, s->veff1, s->veff1f,
-                  s->st);
+                  s->st, s->veff1d, s->o.w[0]);
   emd_launch_veff(s->g, s->ts[nw].v_loc, s->hist, s->hist_len, e, s->veff2,
-                  s->veff2f, s->st);
+                  s->veff2f, s->st, s->veff2d, s->o.w[0]);
   if (!s->c_valid) project(s, s->psi, cur);
   // exponential 1: psi -> ub with H(t)
   exponential(s, s->psi, s->ua, s->ub, cur, 1, tau);
@@ -1654,7 +1659,7 @@ int emd_apply_hamiltonian(emd_system *s, int n_vec, const double *psi,
   OrbLayout o = s->o;
   o.n_blk = (n_vec + o.bo - 1) / o.bo;
   emd_launch_veff(s->g, s->ts[s->cur].v_loc, s->hist, 1, 0.0, s->veff1,
-                  s->veff1f, s->st);
+                  s->veff1f, s->st, s->veff1d, s->o.w[0]);
   if (o.prec == EMD_FP32_ORBITALS)
     emd_launch_project_tile(o, s->ts[s->cur], s->n_atoms, s->ua,
                             s->g.h * s->g.h * s->g.h, s->sp.h_kb, s->c, s->hc,
@@ -1668,6 +1673,7 @@ int emd_apply_hamiltonian(emd_system *s, int n_vec, const double *psi,
   a.psi0 = s->ua;
   a.u_out = s->ub;
   a.v_eff = s->o.prec == EMD_FP64 ? (const void *)s->veff1 : (const void *)s->veff1f;
+  if (s->o.prec != EMD_FP64) a.v_diag = s->veff1d;
   a.tab = &s->ts[s->cur];
   a.hc = s->hc;
   a.a = 0.0;

@@ -158,9 +158,12 @@ void emd_launch_poisson(const GridInfo &g, const double *charge, double *v,
 void emd_launch_lda(int n3, const double *rho, const double *v_h,
                     double *eps_xc, double *v_xc, double *vhxc,
                     cudaStream_t st);
+// v_eff = v_loc + extrapolated v_Hxc + field term (FP64 and, if v_eff_f,
+// FP32); if v_diag, also (d, d, d, d) with d = w0 + v_eff in FP32
 void emd_launch_veff(const GridInfo &g, const double *v_loc,
                      const double *const *hist, int hist_len, double field,
-                     double *v_eff, float *v_eff_f, cudaStream_t st);
+                     double *v_eff, float *v_eff_f, cudaStream_t st,
+                     float4 *v_diag = nullptr, double w0 = 0.0);
 // partials[b] = block sums of (a - c)(b + d); c, d, b may be NULL
 void emd_launch_dot_partials(int n3, const double *a, const double *b,
                              const double *c, const double *d,
@@ -174,6 +177,7 @@ struct StageArgs {
   const void *psi0;
   void *u_out;
   const void *v_eff;       // double* (FP64) or float* (FP32)
+  const void *v_diag = nullptr;   // FP32: float4 (d, d, d, d), d = w_0 + v_eff
   const TableSet *tab;
   const void *hc;          // [n_atoms][n_orb_pad] h_kb*c in orbital precision
   double a;                // tau / k ; u_out = psi0 + (-i a) H u_in

@@ -416,15 +416,24 @@ template <int M> struct LeanGroup {
   static constexpr int G = NS % 3 == 0 ? NS : 3 * NS;
 };
 
+// Lean kernel's tile: as ZTile, with the diagonal d = w_0 + v_eff staged as
+// (d, d, d, d) per point (16 bytes) instead of v_eff (4 bytes).
+template <int BO, int M> struct ZCTile : ZTile<BO, M> {
+  typedef ZTile<BO, M> B;
+  static constexpr int VB = B::NV * 16;
+  static constexpr int SLOT = B::UB + VB + B::QB + B::SB;
+  static constexpr size_t SMEM_FIXED = (size_t)B::NB * SLOT;
+};
+
 template <int BO, int M, bool HCS>
 __global__ void __launch_bounds__(512, 1)
 k_stage_c(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
-          float2 *__restrict__ u_out, const float *__restrict__ v_eff,
+          float2 *__restrict__ u_out, const float4 *__restrict__ diag,
           const int2 *__restrict__ pt4, const int *__restrict__ pt_J,
           const float *__restrict__ pt_pf, const float2 *__restrict__ hc,
           int n, int ntx, int zc, int n_orb_pad, int n_atoms, float a,
           int apply_only, WPairs<float> W) {
-  typedef ZTile<BO, M> Z;
+  typedef ZCTile<BO, M> Z;
   constexpr int RY = Z::RY;
   constexpr int NS = Z::NS;
   constexpr int G = LeanGroup<M>::G;
@@ -507,8 +516,8 @@ k_stage_c(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + dst_b[i]),
                      "l"(src + src_off[i]) : "memory");
     if (v_src >= 0)
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(base + Z::UB + tid * 4),
-                   "l"(v_eff + poff + v_src) : "memory");
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + Z::UB + tid * 16),
+                   "l"(diag + poff + v_src) : "memory");
     if (zi >= 2 * M) {
       const size_t zo = (size_t)(z0 + zi - 2 * M) * n2;
 #pragma unroll
@@ -533,7 +542,6 @@ k_stage_c(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
     orow[r] = (y * n + x) * BO + j;
   }
   const int win0 = ((tyr * RY) * Z::SW + xl + M) * BO + j;     // float2 index
-  const int vp0 = (tyr * RY) * Z::TX + xl;
   const int pnt0 = (tyr * RY) * Z::TX + xl;
 
   float2 acc[RY][NS];
@@ -551,18 +559,16 @@ k_stage_c(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
       if (zi >= total) break;
       const int sb = ph % 3;
       const int dl = ph % NS;             // delay-line slot of this plane
-      if (zi + 2 < total) {
-        issue(zi + 2, (ph + 2) % 3);
-        cp_async_wait<2>();
-      } else if (zi + 1 < total) {
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
+      // planes zi (and zi + 1) are in flight: wait for zi, then one barrier
+      // makes every thread's copies visible and proves that every thread has
+      // finished plane zi - 1, whose ring slot the prefetch of zi + 2 reuses
+      if (zi + 1 < total) cp_async_wait<1>();
+      else cp_async_wait<0>();
       __syncthreads();
+      if (zi + 2 < total) issue(zi + 2, (ph + 2) % 3);
       const unsigned char *base = smraw + sb * Z::SLOT;
       const float2 *P = reinterpret_cast<const float2 *>(base);
-      const float *VP = reinterpret_cast<const float *>(base + Z::UB);
+      const float2 *DP = reinterpret_cast<const float2 *>(base + Z::UB);   // (d, d) at 2 pnt
       float2 win[RY + 2 * M];
 #pragma unroll
       for (int w = 0; w < RY + 2 * M; ++w) win[w] = P[win0 + w * Z::SW * BO];
@@ -570,15 +576,14 @@ k_stage_c(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
       for (int r = 0; r < RY; ++r) {
         const float2 c = win[r + M];
         const float2 *row = P + win0 + (r + M) * Z::SW * BO;
-        float2 s2 = __ffma2_rn(W.w[0], c, acc[r][dl]);
+        float2 s2 = __ffma2_rn(DP[2 * (pnt0 + r * Z::TX)], c, acc[r][dl]);
 #pragma unroll
         for (int k = 1; k <= M; ++k) {
           const float2 t = __fadd2_rn(__fadd2_rn(row[k * BO], row[-k * BO]),
                                       __fadd2_rn(win[r + M + k], win[r + M - k]));
           s2 = __ffma2_rn(W.w[k], t, s2);
         }
-        const float ve = VP[vp0 + r * Z::TX];
-        acc[r][dl] = __ffma2_rn(make_float2(ve, ve), c, s2);
+        acc[r][dl] = s2;
 #pragma unroll
         for (int k = 1; k <= M; ++k) {
           acc[r][(ph + k) % NS] = __ffma2_rn(W.w[k], c, acc[r][(ph + k) % NS]);
@@ -634,7 +639,6 @@ k_stage_c(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
 #pragma unroll
         for (int r = 0; r < RY; ++r) acc[r][slot] = make_float2(0.f, 0.f);
       }
-      __syncthreads();
     }
   }
 }
@@ -1232,7 +1236,7 @@ void stage_z_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
 
 template <int BO, int M, bool HCS>
 void stage_c_tt(const OrbLayout &o, const StageArgs &a, size_t smem, cudaStream_t st) {
-  typedef ZTile<BO, M> Z;
+  typedef ZCTile<BO, M> Z;
   static bool attr_done = false;
   if (!attr_done) {
     cudaFuncSetAttribute(k_stage_c<BO, M, HCS>,
@@ -1245,14 +1249,14 @@ void stage_c_tt(const OrbLayout &o, const StageArgs &a, size_t smem, cudaStream_
   dim3 grid(ntx * nty, (o.n + zc - 1) / zc, o.n_blk);
   k_stage_c<BO, M, HCS><<<grid, Z::NT, smem, st>>>(
       (const float2 *)a.u_in, (const float2 *)a.psi0, (float2 *)a.u_out,
-      (const float *)a.v_eff, a.tab->pt4, a.tab->pt_J, a.tab->pt_pf,
+      (const float4 *)a.v_diag, a.tab->pt4, a.tab->pt_J, a.tab->pt_pf,
       (const float2 *)a.hc, o.n, ntx, zc, o.n_orb_pad, o.n_atoms, (float)a.a,
       a.apply_only, wpairs_of(o));
 }
 
 template <int BO, int M>
 void stage_c_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
-  typedef ZTile<BO, M> Z;
+  typedef ZCTile<BO, M> Z;
   const int hc_bytes = o.n_atoms * BO * (int)sizeof(float2);
   if (hc_bytes <= 16384)
     stage_c_tt<BO, M, true>(o, a, Z::SMEM_FIXED + hc_bytes, st);
@@ -1420,11 +1424,13 @@ void emd_launch_stage(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
         if (o.stage_variant == 1) stage_z_m<2>(o, a, st);
         else if (o.stage_variant == 2) stage_zp_m<2, 1>(o, a, st);
         else if (o.stage_variant == 3) stage_zp_m<2, 2>(o, a, st);
-        else stage_c_m<2>(o, a, st);
+        else if (a.v_diag) stage_c_m<2>(o, a, st);
+        else stage_zp_m<2, 2>(o, a, st);
         break;
       case 4:   // point-per-thread needs > 128 registers
         if (o.stage_variant == 1) stage_z_m<4>(o, a, st);
-        else stage_c_m<4>(o, a, st);
+        else if (a.v_diag) stage_c_m<4>(o, a, st);
+        else stage_z_m<4>(o, a, st);
         break;
     }
   }

@@ -243,7 +243,8 @@ __global__ void k_lda(int n3, const double *rho, const double *vh,
 // v_eff = v_loc + extrapolated v_Hxc + field * (z - L/2).
 __global__ void k_veff(int n, double h, double L, const double *vloc,
                        const double *h0, const double *h1, const double *h2,
-                       int hist_len, double field, double *ve, float *vef) {
+                       int hist_len, double field, double *ve, float *vef,
+                       float4 *vdiag, double w0) {
   const int n3 = n * n * n;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n3) return;
@@ -261,6 +262,10 @@ __global__ void k_veff(int n, double h, double L, const double *vloc,
   }
   ve[i] = v;
   if (vef) vef[i] = (float)v;
+  if (vdiag) {
+    const float d = (float)(w0 + v);
+    vdiag[i] = make_float4(d, d, d, d);
+  }
 }
 
 // partial[b] = sum over block b of (a - c)(b + d) (c, d optional).
@@ -358,11 +363,12 @@ void emd_launch_lda(int n3, const double *rho, const double *v_h,
 
 void emd_launch_veff(const GridInfo &g, const double *v_loc,
                      const double *const *hist, int hist_len, double field,
-                     double *v_eff, float *v_eff_f, cudaStream_t st) {
+                     double *v_eff, float *v_eff_f, cudaStream_t st,
+                     float4 *v_diag, double w0) {
   emd_note_launches(1);
   k_veff<<<(g.n3 + 255) / 256, 256, 0, st>>>(
       g.n, g.h, g.L, v_loc, hist[0], hist_len > 1 ? hist[1] : hist[0],
-      hist_len > 2 ? hist[2] : hist[0], hist_len, field, v_eff, v_eff_f);
+      hist_len > 2 ? hist[2] : hist[0], hist_len, field, v_eff, v_eff_f, v_diag, w0);
 }
 
 void emd_launch_dot_partials(int n3, const double *a, const double *b,

@@ -269,3 +269,23 @@ def test_fp32_tile_projections_and_forces(small):
     assert rel(c, O.projections(psi32, st.tables, s.species, s.h)) < 2e-6
     assert rel(g.forces(), st.F) < 1e-5
     g.close()
+
+
+@pytest.mark.parametrize("bo", [2, 4])
+@pytest.mark.parametrize("order", [2, 8])
+def test_fp32_stage_small_grid_wrapped_rows(bo, order):
+    """16^3 grid, smaller than the staged row of a tile (so halo rows wrap
+    around the grid more than once): every complex64 stage kernel against the
+    oracle."""
+    s = inputs.small_system(n=16, h=0.32, fd_order=order, n_atoms=3, seed=23, n_orb=5)
+    st = O.init_state(s)
+    rng = np.random.default_rng(8)
+    u = rng.normal(size=(5, s.n, s.n, s.n)) + 1j * rng.normal(size=(5, s.n, s.n, s.n))
+    H = O.Hamiltonian(st.v_loc + st.v_h + st.v_xc, st.tables, s.species, s.h, s.fd_order)
+    ref = H.apply(u)
+    for variant in (0, 1):
+        g = emd.System(s, emd.EMD_FP32_ORBITALS, block_orbitals=bo)
+        emd.emd_set_option(g.handle, emd.EMD_OPT_STAGE_VARIANT, variant)
+        got = emd.emd_apply_hamiltonian(g.handle, u)
+        g.close()
+        assert rel(got, ref) < 3e-6, variant
