@@ -255,7 +255,7 @@ void electrons(emd_system *s, int slot) {
 
 // Forces at set k (projections of psi at k must be in c).
 void forces(emd_system *s, int k, double field, double dt, int update_v) {
-  emd_launch_local_force(s->g, s->sp, s->n_atoms, s->ts[k].Rw, s->v_h,
+  emd_launch_local_force(s->g, s->sp, s->n_atoms, s->ts[k], s->v_h,
                          s->ts[k].v_loc, s->lf_part, s->F_loc, s->st);
   if (s->o.prec == EMD_FP32_ORBITALS)
     emd_launch_nl_force_tile(s->o, s->ts[k], s->n_atoms, s->psi, s->c,
@@ -487,6 +487,15 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
     TRY(A((void **)&t.at_ntiles, na * 4));
     TRY(A((void **)&t.at_tiles, (size_t)na * ntiles * sizeof(int2)));
     TRY(A((void **)&t.g_ion, n3 * 8));
+    t.gtab = nullptr;
+    t.glo = nullptr;
+    t.gtabd = nullptr;
+    // an image box spans at most 2 r / h + 5 points per axis
+    if (c.n_atoms > 0 && 2 * (int)std::ceil(p.r_loc / c.h) + 6 <= EMD_GT_EXT) {
+      TRY(A((void **)&t.gtab, (size_t)na * 27 * 3 * EMD_GT_EXT * sizeof(double)));
+      TRY(A((void **)&t.glo, (size_t)na * 27 * 3 * sizeof(int)));
+      TRY(A((void **)&t.gtabd, (size_t)na * 27 * EMD_GT_EXT * sizeof(double)));
+    }
     TRY(A((void **)&t.v_loc, n3 * 8));
   }
   TRY(A((void **)&s->proj_part, (size_t)o.n_blk * ntiles * EMD_TILE_ATOM_MAX *
@@ -1059,7 +1068,7 @@ void reverse_forces(emd_system *s, int k, const double2 *psi, double2 *lam) {
                            A->m2, s->st);
   emd_adj_nl_force_r(A->cu, A->dcu, A->m2, A->lamF, s->n_atoms, o.n_orb,
                      o.n_orb_pad, coef, A->fr, s->st);
-  emd_launch_local_force_hvp(s->g, s->sp, s->n_atoms, t.Rw, A->vh, t.v_loc,
+  emd_launch_local_force_hvp(s->g, s->sp, s->n_atoms, t, A->vh, t.v_loc,
                              A->lamF, s->lf_part, A->fl, s->st);
   emd_adj_sr_hvp(s->sp, s->n_atoms, t.Rw, s->g.L, A->lamF, A->fs, s->st);
 }
@@ -1247,7 +1256,7 @@ int adjoint_moving(emd_system *s, int n_steps, double dt, double mu,
       // v_loc(R_{n+1}) adjoint complete: to positions, then restart with gv1
       emd_adj_lincomb(n3, A->gvloc, 1.0, A->gvloc, 1.0, A->gv2, 0.0, nullptr, 0.0, nullptr, s->st);
       emd_launch_poisson(s->g, A->gvloc, A->tmp, s->fft_a, s->fft_b, s->st);
-      emd_launch_local_force(s->g, s->sp, na, s->ts[setB].Rw, A->tmp, A->zgrid,
+      emd_launch_local_force(s->g, s->sp, na, s->ts[setB], A->tmp, A->zgrid,
                              s->lf_part, A->fconv, s->st);
       emd_adj_lincomb(n3, A->tmp, 1.0, A->gv1, 1.0, A->gv2, 0.0, nullptr, 0.0, nullptr, s->st);
       grid_dot(s, A->tmp, A->saw, A->dfield + n);
@@ -1293,7 +1302,7 @@ int adjoint_moving(emd_system *s, int n_steps, double dt, double mu,
   reverse_forces(s, setA, A->seg_psi[0], nullptr);
   emd_adj_lincomb(n3, A->gvloc, 1.0, A->gvloc, 1.0, A->w, 0.0, nullptr, 0.0, nullptr, s->st);
   emd_launch_poisson(s->g, A->gvloc, A->tmp, s->fft_a, s->fft_b, s->st);
-  emd_launch_local_force(s->g, s->sp, na, s->ts[setA].Rw, A->tmp, A->zgrid,
+  emd_launch_local_force(s->g, s->sp, na, s->ts[setA], A->tmp, A->zgrid,
                          s->lf_part, A->fconv, s->st);
   if (na) {
     CK(cudaMemcpyAsync(fl.data(), A->fl, ab, cudaMemcpyDeviceToHost, s->st));
@@ -1502,7 +1511,7 @@ int emd_propagate_adjoint(emd_system *s, int n_steps, double dt, double mu,
 
   // ---- ionic potential adjoint: dL/dR_J = -h^-3 F_loc[w], w = Poisson(gvloc)
   emd_launch_poisson(s->g, A->gvloc, A->tmp, s->fft_a, s->fft_b, s->st);
-  emd_launch_local_force(s->g, s->sp, na, s->ts[s->cur].Rw, A->tmp, A->zgrid,
+  emd_launch_local_force(s->g, s->sp, na, s->ts[s->cur], A->tmp, A->zgrid,
                          s->lf_part, s->F_loc, s->st);
   std::vector<double> Fw(3 * std::max(1, na)), gRd(3 * std::max(1, na));
   if (na) {

@@ -10,6 +10,7 @@
 #define EMD_TILE_ATOM_MAX 32    // distinct atoms per tile (point-major projections)
 #define EMD_MAX_HALF_ORDER 6    // fd_order / 2 <= 6
 #define EMD_TE_CAP (EMD_TILE * EMD_TILE * EMD_TILE * EMD_PT_KMAX)
+#define EMD_GT_EXT 64
 #define EMD_SPLIT 16            // CTAs per atom for table building and local forces
 
 // error bits raised by kernels (device flag, read by emd_get_*)
@@ -62,6 +63,12 @@ struct TableSet {
   int2 *at_tiles;   // [n_atoms][n_tiles] (tile, slot) in tile order
   int n_slots_cap;  // n_tiles * EMD_TILE_ATOM_MAX
   double *g_ion;    // [n3] sum of Gaussian ion charges
+  // separable ion Gaussian: exp(-d_a^2 / a^2) per atom, image and axis along
+  // the image box of the r_loc sphere, [n_atoms][27][3][EMD_GT_EXT]; NULL if
+  // a box is longer than EMD_GT_EXT points (the kernels then call exp)
+  double *gtab;
+  int *glo;         // [n_atoms][27][3] first grid index of each table
+  double *gtabd;    // [n_atoms][27][EMD_GT_EXT] T_x d_x along x
   double *v_loc;    // [n3] Poisson(-g_ion)
   int cap;
 };
@@ -135,7 +142,7 @@ void emd_launch_tables(const GridInfo &g, const SpeciesDev &sp, int n_atoms,
                        TableSet &t, int *err, cudaStream_t st);
 // part: [n_atoms][EMD_SPLIT][3] scratch
 void emd_launch_local_force(const GridInfo &g, const SpeciesDev &sp,
-                            int n_atoms, const double *Rw, const double *v_es_a,
+                            int n_atoms, const TableSet &t, const double *v_es_a,
                             const double *v_es_b, double *part, double *F,
                             cudaStream_t st);
 void emd_launch_short_range(const SpeciesDev &sp, int n_atoms, const double *R,
@@ -245,7 +252,7 @@ void emd_adj_nl_second_moment(const OrbLayout &o, const TableSet &t, int n_atoms
                               const double2 *u, double h3, double inv_rc2,
                               const double *lamF, double2 *m, cudaStream_t st);
 void emd_launch_local_force_hvp(const GridInfo &g, const SpeciesDev &sp,
-                                int n_atoms, const double *Rw,
+                                int n_atoms, const TableSet &t,
                                 const double *v_es_a, const double *v_es_b,
                                 const double *lam, double *part, double *out,
                                 cudaStream_t st);

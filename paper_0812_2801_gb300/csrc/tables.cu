@@ -102,6 +102,7 @@ template <bool F32>
 __global__ void __launch_bounds__(512)
 k_point_table(int n, int n3, double h, double L, const double *Rw,
               SpeciesDev sp, float margin, const int *tile_cnt, const int *tile_ent,
+              const double *gtab, const int *glo,
               int *pt_cnt, int *pt_J, double *pt_p, float *pt_pf, int2 *pt4,
               double *g_ion, int *te_off, unsigned short *te_pt, float *te_p,
               float4 *te_q, int *err) {
@@ -216,7 +217,20 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
         }
         in_l = d2 < rl2;
       }
-      if (!have64 && (in_l || (in_p && !F32))) {
+      // the ion charge from the separable tables (g = c_g T_x T_y T_z)
+      bool g_tab = false;
+      double g_val = 0.0;
+      if (in_l && gtab) {
+        const int *lo = glo + ((size_t)J * 27 + img) * 3;
+        const int kx = x - lo[0], ky = y - lo[1], kz = z - lo[2];
+        if (kx >= 0 && ky >= 0 && kz >= 0 && kx < EMD_GT_EXT && ky < EMD_GT_EXT &&
+            kz < EMD_GT_EXT) {
+          const double *T = gtab + ((size_t)J * 27 + img) * 3 * EMD_GT_EXT;
+          g_val = sp.c_g * (T[kx] * (T[EMD_GT_EXT + ky] * T[2 * EMD_GT_EXT + kz]));
+          g_tab = true;
+        }
+      }
+      if (!have64 && ((in_l && !g_tab) || (in_p && !F32))) {
         const double dx = emd_disp(x, h, Rw[3 * J + 0], img % 3 - 1, L);
         const double dy = emd_disp(y, h, Rw[3 * J + 1], (img / 3) % 3 - 1, L);
         const double dz = emd_disp(z, h, Rw[3 * J + 2], img / 9 - 1, L);
@@ -235,7 +249,7 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
         }
         hit = true;
       }
-      if (in_l) gsum += sp.c_g * exp(-d2 * sp.inv_a2);
+      if (in_l) gsum += g_tab ? g_val : sp.c_g * exp(-d2 * sp.inv_a2);
     }
     if (hit) {
       if (cnt < EMD_PT_KMAX) {
@@ -302,23 +316,28 @@ __device__ __forceinline__ void axis_range(double c, int nimg, double L,
 struct ImageBoxes {
   int lo[27][3], ext[27][3], start[28];
 };
+// Called by every thread of the block (contains barriers): threads 0..80
+// compute one (image, axis) range each, thread 0 then the flattened starts.
 __device__ void image_boxes(const double *c, double L, double h, double r,
                             int n, ImageBoxes &B) {
-  int acc = 0;
-  for (int img = 0; img < 27; ++img) {
-    const int ni[3] = {img % 3 - 1, (img / 3) % 3 - 1, img / 9 - 1};
-    int nb = 1;
-    for (int a = 0; a < 3; ++a) {
-      int lo, hi;
-      axis_range(c[a], ni[a], L, h, r, n, lo, hi);
-      B.lo[img][a] = lo;
-      B.ext[img][a] = hi >= lo ? hi - lo + 1 : 0;
-      nb *= B.ext[img][a];
-    }
-    B.start[img] = acc;
-    acc += nb;
+  if (threadIdx.x < 81) {
+    const int img = threadIdx.x / 3, a = threadIdx.x % 3;
+    const int ni = a == 0 ? img % 3 - 1 : a == 1 ? (img / 3) % 3 - 1 : img / 9 - 1;
+    int lo, hi;
+    axis_range(c[a], ni, L, h, r, n, lo, hi);
+    B.lo[img][a] = lo;
+    B.ext[img][a] = hi >= lo ? hi - lo + 1 : 0;
   }
-  B.start[27] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int img = 0; img < 27; ++img) {
+      B.start[img] = acc;
+      acc += B.ext[img][0] * B.ext[img][1] * B.ext[img][2];
+    }
+    B.start[27] = acc;
+  }
+  __syncthreads();
 }
 
 // Atom-major projector table: every (point, image) pair within r_proj of atom
@@ -344,8 +363,8 @@ k_atom_table(int pass, int n, double h, double L, const double *Rw,
   const double c[3] = {Rw[3 * J], Rw[3 * J + 1], Rw[3 * J + 2]};
   const double rp2 = __dmul_rn(sp.r_proj, sp.r_proj);
   const float rp2f = (float)rp2, hf = (float)h;
+  image_boxes(c, L, h, sp.r_proj, n, B);
   if (threadIdx.x == 0) {
-    image_boxes(c, L, h, sp.r_proj, n, B);
     int base = 0;
     if (pass == 1)
       for (int s2 = 0; s2 < split; ++s2) base += split_cnt[J * nsplit + s2];
@@ -423,25 +442,62 @@ k_atom_table(int pass, int n, double h, double L, const double *Rw,
   }
 }
 
+// 1-D factors of the ion Gaussian along each image box of atom J's r_loc
+// sphere: exp(-d^2 / a^2) with d the FP64 displacement of grid index
+// lo + i (the same operations as every displacement here), so that
+// g = c_g T_x T_y T_z (three roundings from exp(-|d|^2 / a^2)).  One block
+// per atom.
+__global__ void __launch_bounds__(256)
+k_gauss_tables(int n, double h, double L, const double *Rw, SpeciesDev sp, double *gtab,
+               double *gtabd, int *glo) {
+  __shared__ ImageBoxes B;
+  const int J = blockIdx.x;
+  const double c[3] = {Rw[3 * J], Rw[3 * J + 1], Rw[3 * J + 2]};
+  image_boxes(c, L, h, sp.r_loc, n, B);
+  __syncthreads();
+  if (threadIdx.x < 81)
+    glo[(size_t)J * 81 + threadIdx.x] = B.lo[threadIdx.x / 3][threadIdx.x % 3];
+  double *T = gtab + (size_t)J * 27 * 3 * EMD_GT_EXT;
+  for (int q = threadIdx.x; q < 27 * 3 * EMD_GT_EXT; q += blockDim.x) {
+    const int img = q / (3 * EMD_GT_EXT), a = (q / EMD_GT_EXT) % 3, i = q % EMD_GT_EXT;
+    if (i >= B.ext[img][a] || B.start[img + 1] == B.start[img]) continue;
+    const int ni = a == 0 ? img % 3 - 1 : a == 1 ? (img / 3) % 3 - 1 : img / 9 - 1;
+    const double d = emd_disp(B.lo[img][a] + i, h, c[a], ni, L);
+    const double t = exp(-__dmul_rn(d, d) * sp.inv_a2);
+    T[q] = t;
+    if (a == 0) gtabd[((size_t)J * 27 + img) * EMD_GT_EXT + i] = t * d;
+  }
+}
+
 // F_J^loc = h^3 sum_r v_es(r) g_J(d) 2 d / a^2 over the Gaussian support
 // (-dE_es/dR_J of 1/2 h^3 sum n_tot v_es, n_tot = rho - sum g).  Grid
 // (atom, split) over contiguous ranges of the flattened box space; partials
-// are summed in split order by k_local_force_sum.
+// are summed in split order by k_local_force_sum.  FP32 distances discard
+// the box points certainly outside the sphere; the others get the exact FP64
+// decision, and g comes from the separable tables (when present).
 // HVP = true gives instead, for a direction lam per atom, the derivative
 // d/dR_J of lam_J . F_loc,J at fixed potential:
 //   h^3 sum v_es g_J (-2/a^2) [lam_J - 2 d (d . lam_J) / a^2].
 template <bool HVP>
 __global__ void __launch_bounds__(256)
-k_local_force(int n, double h, double L, const double *Rw, SpeciesDev sp,
-              const double *va, const double *vb, const double *lam,
-              double *part) {
+k_local_force(int n, double h, double L, const double *Rw, const double *gtab,
+              SpeciesDev sp, float margin, const double *va, const double *vb,
+              const double *lam, double *part) {
   __shared__ ImageBoxes B;
+  __shared__ float cf[27][3];
   __shared__ double red[8 * 3];
   const int J = blockIdx.x, split = blockIdx.y, nsplit = gridDim.y;
   const double c[3] = {Rw[3 * J], Rw[3 * J + 1], Rw[3 * J + 2]};
   const double rl2 = __dmul_rn(sp.r_loc, sp.r_loc);
-  if (threadIdx.x == 0) image_boxes(c, L, h, sp.r_loc, n, B);
+  const float rl2f = (float)rl2, hf = (float)h;
+  image_boxes(c, L, h, sp.r_loc, n, B);
+  if (threadIdx.x < 81) {
+    const int img = threadIdx.x / 3, a = threadIdx.x % 3;
+    const int ni = a == 0 ? img % 3 - 1 : a == 1 ? (img / 3) % 3 - 1 : img / 9 - 1;
+    cf[img][a] = (float)(c[a] + ni * L);
+  }
   __syncthreads();
+  const double *T = gtab ? gtab + (size_t)J * 27 * 3 * EMD_GT_EXT : nullptr;
   const int total = B.start[27];
   const int per = (total + nsplit - 1) / nsplit;
   const int f0 = split * per, f1 = min(total, f0 + per);
@@ -451,8 +507,11 @@ k_local_force(int n, double h, double L, const double *Rw, SpeciesDev sp,
     while (img < 26 && f >= B.start[img + 1]) ++img;
     const int k = f - B.start[img];
     const int ex = B.ext[img][0], ey = B.ext[img][1];
-    const int ix = B.lo[img][0] + k % ex, iy = B.lo[img][1] + (k / ex) % ey,
-              iz = B.lo[img][2] + k / (ex * ey);
+    const int kx = k % ex, ky = (k / ex) % ey, kz = k / (ex * ey);
+    const int ix = B.lo[img][0] + kx, iy = B.lo[img][1] + ky, iz = B.lo[img][2] + kz;
+    const float dxf = (float)ix * hf - cf[img][0], dyf = (float)iy * hf - cf[img][1],
+                dzf = (float)iz * hf - cf[img][2];
+    if (dxf * dxf + dyf * dyf + dzf * dzf > rl2f + margin) continue;
     const int ni[3] = {img % 3 - 1, (img / 3) % 3 - 1, img / 9 - 1};
     const double dx = emd_disp(ix, h, c[0], ni[0], L);
     const double dy = emd_disp(iy, h, c[1], ni[1], L);
@@ -460,7 +519,10 @@ k_local_force(int n, double h, double L, const double *Rw, SpeciesDev sp,
     const double d2 = emd_norm2(dx, dy, dz);
     if (d2 < rl2) {
       const int p = (iz * n + iy) * n + ix;
-      const double g = sp.c_g * exp(-d2 * sp.inv_a2);
+      const double *Ti = T ? T + (size_t)img * 3 * EMD_GT_EXT : nullptr;
+      const bool tab = T && kx < EMD_GT_EXT && ky < EMD_GT_EXT && kz < EMD_GT_EXT;
+      const double g = tab ? sp.c_g * (Ti[kx] * Ti[EMD_GT_EXT + ky] * Ti[2 * EMD_GT_EXT + kz])
+                           : sp.c_g * exp(-d2 * sp.inv_a2);
       if (HVP) {
         const double l0 = lam[3 * J], l1 = lam[3 * J + 1], l2 = lam[3 * J + 2];
         const double w = (va[p] + vb[p]) * g * (-2.0 * sp.inv_a2);
@@ -475,6 +537,96 @@ k_local_force(int n, double h, double L, const double *Rw, SpeciesDev sp,
         acc[2] += w * dz;
       }
     }
+  }
+  emd_block_sum<3>(acc, red);
+  if (threadIdx.x == 0) {
+    const double h3 = h * h * h;
+    for (int a = 0; a < 3; ++a) part[((size_t)J * nsplit + split) * 3 + a] = h3 * acc[a];
+  }
+}
+
+// The same force with one thread per row (y, z) of the image boxes and the
+// Gaussian factored, g = c_g T_x(x) T_y(y) T_z(z):
+//   F_x += c_g T_y T_z sum_x v T_x d_x,  F_{y,z} += c_g T_y T_z d_{y,z} sum_x v T_x
+// over the row's chord through the sphere.  The chord is a contiguous run of
+// x (the FP64 distance is monotone in x on each side of the centre); its
+// exact ends are found by the FP64 decision, starting from an FP32 estimate,
+// so the per-point work is two multiply-adds.  Tables T_x and T_x d_x come
+// from k_gauss_tables.  Used for the forward force when the tables exist.
+__global__ void __launch_bounds__(256)
+k_local_force_rows(int n, double h, double L, const double *Rw, const double *gtab,
+                   const double *gtabd, SpeciesDev sp, const double *va,
+                   const double *vb, double *part) {
+  __shared__ ImageBoxes B;
+  __shared__ int rstart[28];
+  __shared__ float cf[27][3];
+  __shared__ double red[8 * 3];
+  const int J = blockIdx.x, split = blockIdx.y, nsplit = gridDim.y;
+  const double c[3] = {Rw[3 * J], Rw[3 * J + 1], Rw[3 * J + 2]};
+  const double rl2 = __dmul_rn(sp.r_loc, sp.r_loc);
+  const float rl2f = (float)rl2, hf = (float)h, ihf = (float)(1.0 / h);
+  image_boxes(c, L, h, sp.r_loc, n, B);
+  if (threadIdx.x == 0) {
+    int acc = 0;   // rows (y, z) per image, boxes with no point skipped
+    for (int img = 0; img < 27; ++img) {
+      rstart[img] = acc;
+      if (B.start[img + 1] > B.start[img]) acc += B.ext[img][1] * B.ext[img][2];
+    }
+    rstart[27] = acc;
+  }
+  if (threadIdx.x < 81) {
+    const int img = threadIdx.x / 3, a = threadIdx.x % 3;
+    const int ni = a == 0 ? img % 3 - 1 : a == 1 ? (img / 3) % 3 - 1 : img / 9 - 1;
+    cf[img][a] = (float)(c[a] + ni * L);
+  }
+  __syncthreads();
+  const double *TJ = gtab + (size_t)J * 27 * 3 * EMD_GT_EXT;
+  const double *DJ = gtabd + (size_t)J * 27 * EMD_GT_EXT;
+  const int nrows = rstart[27];
+  const int per = (nrows + nsplit - 1) / nsplit;
+  const int q0 = split * per, q1 = min(nrows, q0 + per);
+  double acc[3] = {0.0, 0.0, 0.0};
+  int img = 0;
+  for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    while (img < 26 && q >= rstart[img + 1]) ++img;
+    const int k = q - rstart[img];
+    const int ey = B.ext[img][1];
+    const int ky = k % ey, kz = k / ey;
+    const int iy = B.lo[img][1] + ky, iz = B.lo[img][2] + kz;
+    const float dyf = (float)iy * hf - cf[img][1], dzf = (float)iz * hf - cf[img][2];
+    const float remf = rl2f - (dyf * dyf + dzf * dzf);
+    if (remf < -4.0f * hf * hf - 1e-3f * rl2f) continue;   // far from the sphere
+    const int ni[3] = {img % 3 - 1, (img / 3) % 3 - 1, img / 9 - 1};
+    const int lo0 = B.lo[img][0], hi0 = lo0 + B.ext[img][0] - 1;
+    const float wf = sqrtf(fmaxf(remf, 0.f));
+    // the exact chord lies within two points of the FP32 estimate (FP32
+    // errors are far below a grid step); scan in from both ends of that range
+    const int xa = max(lo0, (int)ceilf((cf[img][0] - wf) * ihf) - 2);
+    const int xb = min(hi0, (int)floorf((cf[img][0] + wf) * ihf) + 2);
+    const double dy = emd_disp(iy, h, c[1], ni[1], L);
+    const double dz = emd_disp(iz, h, c[2], ni[2], L);
+    auto inside = [&](int x) {
+      return emd_norm2(emd_disp(x, h, c[0], ni[0], L), dy, dz) < rl2;
+    };
+    int xs = xa;
+    while (xs <= xb && !inside(xs)) ++xs;
+    if (xs > xb) continue;                                   // row misses the sphere
+    int xe = xb;
+    while (xe > xs && !inside(xe)) --xe;
+    const double *Tx = TJ + (size_t)img * 3 * EMD_GT_EXT;
+    const double *Dx = DJ + (size_t)img * EMD_GT_EXT;
+    const double tyz = Tx[EMD_GT_EXT + ky] * Tx[2 * EMD_GT_EXT + kz];
+    const size_t rowp = ((size_t)iz * n + iy) * n;
+    double s0 = 0.0, s1 = 0.0;
+    for (int x = xs; x <= xe; ++x) {
+      const double v = va[rowp + x] + vb[rowp + x];
+      s0 += v * Tx[x - lo0];
+      s1 += v * Dx[x - lo0];
+    }
+    const double w = sp.c_g * tyz * (2.0 * sp.inv_a2);
+    acc[0] += w * s1;
+    acc[1] += w * dy * s0;
+    acc[2] += w * dz * s0;
   }
   emd_block_sum<3>(acc, red);
   if (threadIdx.x == 0) {
@@ -574,17 +726,24 @@ void emd_launch_tables(const GridInfo &g, const SpeciesDev &sp, int n_atoms,
   const float rmax = (float)fmax(sp.r_proj, sp.r_loc);
   k_tile_candidates<<<ntiles, 256, 0, st>>>(
       g.n, g.h, g.L, t.Rw, n_atoms, rmax, t.tile_cnt, t.tile_ent, err);
+  if (t.gtab && n_atoms > 0) {
+    emd_note_launches(1);
+    k_gauss_tables<<<n_atoms, 256, 0, st>>>(g.n, g.h, g.L, t.Rw, sp, t.gtab, t.gtabd,
+                                            t.glo);
+  }
   const float margin_pt = emd_fp32_d2_margin(g.L, fmax(sp.r_proj, sp.r_loc));
   if (t.te_off)
     k_point_table<true><<<ntiles, 512, 0, st>>>(g.n, g.n3, g.h, g.L, t.Rw, sp, margin_pt,
-                                                t.tile_cnt, t.tile_ent, t.pt_cnt,
-                                                t.pt_J, t.pt_p, t.pt_pf, t.pt4, t.g_ion,
-                                                t.te_off, t.te_pt, t.te_p, t.te_q, err);
+                                                t.tile_cnt, t.tile_ent, t.gtab, t.glo,
+                                                t.pt_cnt, t.pt_J, t.pt_p, t.pt_pf, t.pt4,
+                                                t.g_ion, t.te_off, t.te_pt, t.te_p, t.te_q,
+                                                err);
   else
     k_point_table<false><<<ntiles, 512, 0, st>>>(g.n, g.n3, g.h, g.L, t.Rw, sp, margin_pt,
-                                                 t.tile_cnt, t.tile_ent, t.pt_cnt,
-                                                 t.pt_J, t.pt_p, t.pt_pf, t.pt4, t.g_ion,
-                                                 t.te_off, t.te_pt, t.te_p, t.te_q, err);
+                                                 t.tile_cnt, t.tile_ent, t.gtab, t.glo,
+                                                 t.pt_cnt, t.pt_J, t.pt_p, t.pt_pf, t.pt4,
+                                                 t.g_ion, t.te_off, t.te_pt, t.te_p, t.te_q,
+                                                 err);
   if (n_atoms > 0 && !t.te_off) {
     dim3 grid(n_atoms, EMD_SPLIT);
     const float margin = emd_fp32_d2_margin(g.L, sp.r_proj);
@@ -596,27 +755,33 @@ void emd_launch_tables(const GridInfo &g, const SpeciesDev &sp, int n_atoms,
 }
 
 void emd_launch_local_force(const GridInfo &g, const SpeciesDev &sp,
-                            int n_atoms, const double *Rw, const double *v_es_a,
+                            int n_atoms, const TableSet &t, const double *v_es_a,
                             const double *v_es_b, double *part, double *F,
                             cudaStream_t st) {
   if (n_atoms <= 0) return;
   emd_note_launches(2);
   dim3 grid(n_atoms, EMD_SPLIT);
-  k_local_force<false><<<grid, 256, 0, st>>>(g.n, g.h, g.L, Rw, sp, v_es_a,
-                                             v_es_b, nullptr, part);
+  if (t.gtab)
+    k_local_force_rows<<<grid, 256, 0, st>>>(g.n, g.h, g.L, t.Rw, t.gtab, t.gtabd, sp,
+                                             v_es_a, v_es_b, part);
+  else
+    k_local_force<false><<<grid, 256, 0, st>>>(g.n, g.h, g.L, t.Rw, t.gtab, sp,
+                                               emd_fp32_d2_margin(g.L, sp.r_loc), v_es_a,
+                                               v_es_b, nullptr, part);
   const int m = 3 * n_atoms;
   k_local_force_sum<<<(m + 127) / 128, 128, 0, st>>>(part, n_atoms, EMD_SPLIT, F);
 }
 
 void emd_launch_local_force_hvp(const GridInfo &g, const SpeciesDev &sp,
-                                int n_atoms, const double *Rw,
+                                int n_atoms, const TableSet &t,
                                 const double *v_es_a, const double *v_es_b,
                                 const double *lam, double *part, double *out,
                                 cudaStream_t st) {
   if (n_atoms <= 0) return;
   emd_note_launches(2);
   dim3 grid(n_atoms, EMD_SPLIT);
-  k_local_force<true><<<grid, 256, 0, st>>>(g.n, g.h, g.L, Rw, sp, v_es_a,
+  k_local_force<true><<<grid, 256, 0, st>>>(g.n, g.h, g.L, t.Rw, t.gtab, sp,
+                                            emd_fp32_d2_margin(g.L, sp.r_loc), v_es_a,
                                             v_es_b, lam, part);
   const int m = 3 * n_atoms;
   k_local_force_sum<<<(m + 127) / 128, 128, 0, st>>>(part, n_atoms, EMD_SPLIT, out);
