@@ -44,7 +44,7 @@ BYTES_PER_UPDATE = {"f32": 24, "f64": 48}
 # dram__bytes_read.sum + dram__bytes_write.sum of one Horner-stage launch
 # (profiles/horner_stage_c96.md), per precision, for the kernel as built;
 # None until a capture exists for it.
-TRAFFIC_PER_LAUNCH = {"f32": 3.350e9, "f64": None}
+TRAFFIC_PER_LAUNCH = {"f32": 3.515e9, "f64": None}
 
 
 def dist_env():
