@@ -122,6 +122,7 @@ struct emd_system {
   int ions_set = 0, orbs_set = 0;
   int frozen_ions = 0, profile = 0, check_stable = 1, proj_atom_major = 1;
   double2 *proj_part = nullptr;   // point-major projection partials
+  void *hc_zero = nullptr;          // complex64: zero projector coefficients
   double v_max = 0.0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending, prof_free;
   double prof_ms = 0.0;
@@ -275,6 +276,7 @@ void forces(emd_system *s, int k, double field, double dt, int update_v) {
 }
 
 int reduce_max_veff(emd_system *s, double *out);
+void kinetic_fp32(emd_system *s, int *np);
 
 // After new orbitals or ions: rho(0), v_Hxc(0), F(0); history restarts.
 int restart_dynamics(emd_system *s) {
@@ -305,6 +307,10 @@ __global__ void k_negate(double *v, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = -v[i];
 }
+__global__ void k_fill4(float4 *v, int n, float d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = make_float4(d, d, d, d);
+}
 __global__ void k_max_sum(const double *a, const double *b, int n, double *out) {
   __shared__ double sm[256];
   double m = -1e300;
@@ -321,6 +327,27 @@ __global__ void k_max_sum(const double *a, const double *b, int n, double *out) 
 void negate_grid(double *v, int n3, cudaStream_t st) {
   emd_note_launches(1);
   k_negate<<<(n3 + 255) / 256, 256, 0, st>>>(v, n3);
+}
+// complex64: partial sums of Re<psi|T psi> (T psi by the stage kernel with
+// diagonal w_0, no potential and zero projector coefficients, into ua)
+void kinetic_fp32(emd_system *s, int *np) {
+  emd_note_launches(1);
+  k_fill4<<<(s->g.n3 + 255) / 256, 256, 0, s->st>>>(s->veff1d, s->g.n3,
+                                                     (float)s->o.w[0]);
+  OrbLayout o = s->o;
+  o.stage_variant = 0;
+  StageArgs a;
+  a.u_in = s->psi;
+  a.psi0 = s->psi;
+  a.u_out = s->ua;
+  a.v_eff = s->veff1f;
+  a.v_diag = s->veff1d;
+  a.tab = &s->ts[s->cur];
+  a.hc = s->hc_zero;
+  a.a = 0.0;
+  a.apply_only = 1;
+  emd_launch_stage(o, a, s->st);
+  emd_launch_cdot_re_c64(s->o, s->psi, s->ua, s->partials, np, s->st);
 }
 int reduce_max_veff(emd_system *s, double *out) {
   emd_note_launches(1);
@@ -471,13 +498,11 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
     TRY(A((void **)&t.at_p, (size_t)na * cap * 8));
     TRY(A((void **)&t.at_d, (size_t)na * cap * 24));
     t.te_off = nullptr;
-    t.te_pt = nullptr;
-    t.te_p = nullptr;
+    t.te_pp = nullptr;
     t.te_q = nullptr;
     if (c.precision == EMD_FP32_ORBITALS) {
       TRY(A((void **)&t.te_off, (size_t)ntiles * (EMD_TILE_ATOM_MAX + 1) * 4));
-      TRY(A((void **)&t.te_pt, (size_t)ntiles * EMD_TE_CAP * 2));
-      TRY(A((void **)&t.te_p, (size_t)ntiles * EMD_TE_CAP * 4));
+      TRY(A((void **)&t.te_pp, (size_t)ntiles * EMD_TE_CAP * sizeof(uint2)));
       TRY(A((void **)&t.te_q, (size_t)ntiles * EMD_TE_CAP * 16));
     }
     t.n_slots_cap = ntiles * EMD_TILE_ATOM_MAX;
@@ -501,6 +526,12 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
   TRY(A((void **)&s->proj_part, (size_t)o.n_blk * ntiles * EMD_TILE_ATOM_MAX *
                                      o.bo * (c.precision == EMD_FP32_ORBITALS ? 3 : 1) *
                                      sizeof(double2)));
+  if (c.precision == EMD_FP32_ORBITALS) {
+    TRY(A(&s->hc_zero, (size_t)na * o.n_orb_pad * sizeof(float2)));
+    TRY(cudaMemset(s->hc_zero, 0, (size_t)na * o.n_orb_pad * sizeof(float2)) == cudaSuccess
+            ? EMD_OK
+            : fail(EMD_ECUDA, "cudaMemset failed"));
+  }
   TRY(A((void **)&s->c, (size_t)na * o.n_orb_pad * sizeof(double2)));
   TRY(A(&s->hc, (size_t)na * o.n_orb_pad * esz));
   TRY(A((void **)&s->V, na * 3 * 8));
@@ -1555,7 +1586,10 @@ int emd_get_energy(emd_system *s, emd_energy *out) {
   const int cur = s->cur;
   const double h3 = s->g.h * s->g.h * s->g.h;
   int np = 0;
-  emd_launch_kinetic_partials(s->o, s->psi, s->partials, &np, s->st);
+  if (s->o.prec == EMD_FP32_ORBITALS)
+    kinetic_fp32(s, &np);
+  else
+    emd_launch_kinetic_partials(s->o, s->psi, s->partials, &np, s->st);
   emd_launch_sum(s->partials, np, s->scal + 0, s->st);
   if (!s->c_valid) {
     project(s, s->psi, cur);

@@ -53,9 +53,9 @@ struct TableSet {
   // is the first entry of slot s (te_off[t][S] the end), an entry holds the
   // point's index in the tile, p summed over images, and sum p d / r_c^2
   int *te_off;             // [n_tiles][EMD_TILE_ATOM_MAX + 1]
-  unsigned short *te_pt;   // [n_tiles][EMD_TE_CAP]
-  float *te_p;             // [n_tiles][EMD_TE_CAP]
-  float4 *te_q;            // [n_tiles][EMD_TE_CAP] (sum p d / r_c^2, p)
+  uint2 *te_pp;            // [n_tiles][EMD_TE_CAP] (point index, bits of p)
+  float4 *te_q;            // [n_tiles][EMD_TE_CAP] (sum p d / r_c^2, bits of
+                           // the point index)
   int *tile_nat;    // [n_tiles] distinct atoms per tile
   int *tile_atoms;  // [n_tiles][EMD_TILE_ATOM_MAX] in atom order
   int *tile_off;    // [n_tiles] exclusive prefix sum of tile_nat
@@ -268,3 +268,7 @@ void emd_launch_project_tile(const OrbLayout &o, const TableSet &t, int n_atoms,
 void emd_launch_nl_force_tile(const OrbLayout &o, const TableSet &t, int n_atoms,
                               const void *u, const double2 *c, double h3, double coef,
                               double2 *partial, double *F_nl, cudaStream_t st);
+// partial sums of Re(conj(a) b) over complex64 orbital arrays (double-float
+// per point, FP64 across points)
+void emd_launch_cdot_re_c64(const OrbLayout &o, const void *a, const void *b,
+                            double *partials, int *nparts, cudaStream_t st);

@@ -995,6 +995,43 @@ k_project(const typename cplx<T>::type *__restrict__ u, size_t n3,
   }
 }
 
+// partial[b] = sum over the points of block b and all orbitals of
+// Re(conj(a) b) for complex64 arrays: per point in double-float arithmetic
+// (exact FP32 products, TwoSum accumulation, as the density), converted to
+// FP64 once per point, then a fixed-tree FP64 block sum.
+template <int BO>
+__global__ void __launch_bounds__(256)
+k_cdot_re_c64(const float2 *__restrict__ a, const float2 *__restrict__ b, size_t n3,
+              int n_blk, double *part) {
+  __shared__ double red[8];
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  if (p < n3) {
+    float hi = 0.f, lo = 0.f;
+    for (int k = 0; k < n_blk; ++k) {
+      const size_t o = ((size_t)k * n3 + p) * BO;
+#pragma unroll
+      for (int j = 0; j < BO; ++j) {
+        const float2 x = a[o + j], y = b[o + j];
+        const float px = __fmul_rn(x.x, y.x), py = __fmul_rn(x.y, y.y);
+        lo = __fadd_rn(lo, __fadd_rn(__fmaf_rn(x.x, y.x, -px), __fmaf_rn(x.y, y.y, -py)));
+        float t = px;
+        float s2 = __fadd_rn(hi, t), bb = __fsub_rn(s2, hi);
+        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s2, bb)), __fsub_rn(t, bb)));
+        hi = s2;
+        t = py;
+        s2 = __fadd_rn(hi, t);
+        bb = __fsub_rn(s2, hi);
+        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s2, bb)), __fsub_rn(t, bb)));
+        hi = s2;
+      }
+    }
+    acc[0] = (double)hi + (double)lo;
+  }
+  emd_block_sum<1>(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
+}
+
 template <typename T, int BO>
 __global__ void k_density(const typename cplx<T>::type *__restrict__ u,
                           size_t n3, int n_blk, double occ, double *rho) {
@@ -1510,4 +1547,16 @@ void emd_launch_abs2_sum(const double2 *c, int n, double *out,
                          cudaStream_t st) {
   emd_note_launches(1);
   k_abs2_sum<<<1, 256, 0, st>>>(c, n, out);
+}
+
+void emd_launch_cdot_re_c64(const OrbLayout &o, const void *a, const void *b,
+                            double *partials, int *nparts, cudaStream_t st) {
+  emd_note_launches(1);
+  const int nb = (o.n3 + 255) / 256;
+  *nparts = nb;
+  switch (o.bo) {
+    case 1: k_cdot_re_c64<1><<<nb, 256, 0, st>>>((const float2 *)a, (const float2 *)b, (size_t)o.n3, o.n_blk, partials); break;
+    case 2: k_cdot_re_c64<2><<<nb, 256, 0, st>>>((const float2 *)a, (const float2 *)b, (size_t)o.n3, o.n_blk, partials); break;
+    case 4: k_cdot_re_c64<4><<<nb, 256, 0, st>>>((const float2 *)a, (const float2 *)b, (size_t)o.n3, o.n_blk, partials); break;
+  }
 }

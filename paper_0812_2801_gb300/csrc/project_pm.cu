@@ -262,8 +262,8 @@ template <int BO, bool FORCE>
 __global__ void __launch_bounds__(EMD_TG_WARPS * 32)
 k_tile_gather(const float2 *__restrict__ u, int n, int nt, int n_orb_pad,
               const int *__restrict__ tile_nat, const int *__restrict__ tile_off,
-              const int *__restrict__ te_off, const unsigned short *__restrict__ te_pt,
-              const float *__restrict__ te_p, const float4 *__restrict__ te_q,
+              const int *__restrict__ te_off, const uint2 *__restrict__ te_pp,
+              const float4 *__restrict__ te_q,
               double2 *__restrict__ partial) {
   constexpr int NT = EMD_TG_WARPS * 32;
   constexpr int NA = FORCE ? 6 * BO : 2 * BO;
@@ -302,26 +302,39 @@ k_tile_gather(const float2 *__restrict__ u, int n, int nt, int n_orb_pad,
     for (int k = 0; k < NA; ++k) acc[k] = 0.f;
     const int e1 = off[sl + 1];
     for (int e = off[sl] + lane; e < e1; e += 32) {
-      const int q = __ldg(te_pt + tb + e);
       if (FORCE) {
         const float4 w = __ldg(te_q + tb + e);
+        const float4 *v4 = reinterpret_cast<const float4 *>(us + __float_as_int(w.w) * BO);
 #pragma unroll
-        for (int j = 0; j < BO; ++j) {
-          const float2 v = us[q * BO + j];
-          acc[6 * j + 0] += w.x * v.x;
-          acc[6 * j + 1] += w.x * v.y;
-          acc[6 * j + 2] += w.y * v.x;
-          acc[6 * j + 3] += w.y * v.y;
-          acc[6 * j + 4] += w.z * v.x;
-          acc[6 * j + 5] += w.z * v.y;
+        for (int h = 0; h < (BO + 1) / 2; ++h) {
+          const float4 v = BO == 1 ? make_float4(us[__float_as_int(w.w)].x,
+                                                 us[__float_as_int(w.w)].y, 0.f, 0.f)
+                                   : v4[h];
+#pragma unroll
+          for (int jj = 0; jj < (BO == 1 ? 1 : 2); ++jj) {
+            const int j = 2 * h + jj;
+            const float vx = jj ? v.z : v.x, vy = jj ? v.w : v.y;
+            acc[6 * j + 0] += w.x * vx;
+            acc[6 * j + 1] += w.x * vy;
+            acc[6 * j + 2] += w.y * vx;
+            acc[6 * j + 3] += w.y * vy;
+            acc[6 * j + 4] += w.z * vx;
+            acc[6 * j + 5] += w.z * vy;
+          }
         }
       } else {
-        const float pv = __ldg(te_p + tb + e);
+        const uint2 rec = __ldg(te_pp + tb + e);
+        const float pv = __uint_as_float(rec.y);
+        const float4 *v4 = reinterpret_cast<const float4 *>(us + rec.x * BO);
 #pragma unroll
-        for (int j = 0; j < BO; ++j) {
-          const float2 v = us[q * BO + j];
-          acc[2 * j] += pv * v.x;
-          acc[2 * j + 1] += pv * v.y;
+        for (int h = 0; h < (BO + 1) / 2; ++h) {
+          const float4 v = BO == 1 ? make_float4(us[rec.x].x, us[rec.x].y, 0.f, 0.f) : v4[h];
+#pragma unroll
+          for (int jj = 0; jj < (BO == 1 ? 1 : 2); ++jj) {
+            const int j = 2 * h + jj;
+            acc[2 * j] += pv * (jj ? v.z : v.x);
+            acc[2 * j + 1] += pv * (jj ? v.w : v.y);
+          }
         }
       }
     }
@@ -411,8 +424,8 @@ void tile_gather_t(const OrbLayout &o, const TableSet &t, const void *u, double2
   const int nt = (o.n + EMD_TILE - 1) / EMD_TILE;
   dim3 grid(nt * nt * nt, o.n_blk);
   k_tile_gather<BO, FORCE><<<grid, EMD_TG_WARPS * 32, 0, st>>>(
-      (const float2 *)u, o.n, nt, o.n_orb_pad, t.tile_nat, t.tile_off, t.te_off, t.te_pt,
-      t.te_p, t.te_q, partial);
+      (const float2 *)u, o.n, nt, o.n_orb_pad, t.tile_nat, t.tile_off, t.te_off, t.te_pp,
+      t.te_q, partial);
 }
 
 }  // namespace

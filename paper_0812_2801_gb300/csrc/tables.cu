@@ -104,8 +104,7 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
               SpeciesDev sp, float margin, const int *tile_cnt, const int *tile_ent,
               const double *gtab, const int *glo,
               int *pt_cnt, int *pt_J, double *pt_p, float *pt_pf, int2 *pt4,
-              double *g_ion, int *te_off, unsigned short *te_pt, float *te_p,
-              float4 *te_q, int *err) {
+              double *g_ion, int *te_off, uint2 *te_pp, float4 *te_q, int *err) {
   __shared__ int cand[EMD_TILE_CAND_MAX];
   __shared__ float cfs[EMD_TILE_CAND_MAX][3];
   __shared__ int run_start[EMD_TILE_ATOM_MAX + 1];
@@ -275,9 +274,8 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
         const int e = off + __popc(m & ((1u << lane) - 1u));
         if (e < EMD_TE_CAP) {
           const size_t q = (size_t)t * EMD_TE_CAP + e;
-          te_pt[q] = (unsigned short)threadIdx.x;
-          te_p[q] = psumf;
-          te_q[q] = make_float4(pdx, pdy, pdz, psumf);
+          te_pp[q] = make_uint2(threadIdx.x, __float_as_uint(psumf));
+          te_q[q] = make_float4(pdx, pdy, pdz, __int_as_float((int)threadIdx.x));
         } else {
           atomicOr(err, EMD_ERRBIT_TILE);
         }
@@ -736,13 +734,13 @@ void emd_launch_tables(const GridInfo &g, const SpeciesDev &sp, int n_atoms,
     k_point_table<true><<<ntiles, 512, 0, st>>>(g.n, g.n3, g.h, g.L, t.Rw, sp, margin_pt,
                                                 t.tile_cnt, t.tile_ent, t.gtab, t.glo,
                                                 t.pt_cnt, t.pt_J, t.pt_p, t.pt_pf, t.pt4,
-                                                t.g_ion, t.te_off, t.te_pt, t.te_p, t.te_q,
+                                                t.g_ion, t.te_off, t.te_pp, t.te_q,
                                                 err);
   else
     k_point_table<false><<<ntiles, 512, 0, st>>>(g.n, g.n3, g.h, g.L, t.Rw, sp, margin_pt,
                                                  t.tile_cnt, t.tile_ent, t.gtab, t.glo,
                                                  t.pt_cnt, t.pt_J, t.pt_p, t.pt_pf, t.pt4,
-                                                 t.g_ion, t.te_off, t.te_pt, t.te_p, t.te_q,
+                                                 t.g_ion, t.te_off, t.te_pp, t.te_q,
                                                  err);
   if (n_atoms > 0 && !t.te_off) {
     dim3 grid(n_atoms, EMD_SPLIT);

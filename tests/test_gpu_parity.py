@@ -289,3 +289,18 @@ def test_fp32_stage_small_grid_wrapped_rows(bo, order):
         got = emd.emd_apply_hamiltonian(g.handle, u)
         g.close()
         assert rel(got, ref) < 3e-6, variant
+
+
+def test_fp32_energy_terms_match_oracle(small):
+    """complex64 orbitals: every energy term (the kinetic one from T psi by the
+    stage kernel, accumulated in double-float) against the oracle's FP64
+    energies of the same complex64 values."""
+    s = small
+    s32 = inputs.SystemInput(**{**s.__dict__,
+                                "psi": s.psi.astype(np.complex64).astype(np.complex128)})
+    g = emd.System(s32, emd.EMD_FP32_ORBITALS)
+    eg = g.energy()
+    g.close()
+    eo = O.energies(O.init_state(s32))
+    for k in ("kin_e", "nl", "es", "xc", "sr", "kin_ion", "total"):
+        assert abs(eg[k] - eo[k]) <= 2e-6 * max(abs(eo[k]), 1e-3), (k, eg[k], eo[k])
