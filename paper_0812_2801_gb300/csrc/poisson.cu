@@ -86,6 +86,100 @@ __device__ __forceinline__ double2 cmuli(double2 a, int sign) {
   return sign > 0 ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
 }
 
+// One radix-R Stockham stage on L lines of length n in shared memory (x -> y),
+// R a compile-time constant so the R inputs of a butterfly stay in registers.
+template <int R>
+__device__ __forceinline__ void fft_stage(const double2 *b0, double2 *b1, int n, int L,
+                                          int Ns, const double2 *tw, const double2 *root,
+                                          int sign) {
+  const int m = n / R;
+  for (int t = threadIdx.x; t < L * m; t += blockDim.x) {
+    const int l = t / m, j = t - l * m;
+    const double2 *x = b0 + l * n;
+    double2 *y = b1 + l * n;
+    const int jm = j % Ns;
+    const int base = (j / Ns) * Ns * R + jm;
+    double2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      double2 a = x[j + r * m];
+      if (r > 0 && jm > 0) {
+        double2 w = tw[jm * R + r];
+        if (sign > 0) w.y = -w.y;
+        a = cmul(a, w);
+      }
+      v[r] = a;
+    }
+    if (R == 4) {
+      const double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+      const double2 t2 = cadd(v[1], v[3]), t3 = cmuli(csub(v[1], v[3]), sign);
+      y[base] = cadd(t0, t2);
+      y[base + Ns] = cadd(t1, t3);
+      y[base + 2 * Ns] = csub(t0, t2);
+      y[base + 3 * Ns] = csub(t1, t3);
+    } else if (R == 2) {
+      y[base] = cadd(v[0], v[1]);
+      y[base + Ns] = csub(v[0], v[1]);
+    } else if (R == 3) {
+      const double c3 = 0.86602540378443864676;  // sqrt(3)/2
+      const double2 sm_ = cadd(v[1], v[2]), df = csub(v[1], v[2]);
+      const double2 a = make_double2(v[0].x - 0.5 * sm_.x, v[0].y - 0.5 * sm_.y);
+      double2 b = cmuli(df, sign);
+      b.x *= c3;
+      b.y *= c3;
+      y[base] = cadd(v[0], sm_);
+      y[base + Ns] = cadd(a, b);
+      y[base + 2 * Ns] = csub(a, b);
+    } else {
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        double2 acc = v[0];
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          double2 w = root[(r * k) % R];
+          if (sign > 0) w.y = -w.y;
+          acc = cadd(acc, cmul(v[r], w));
+        }
+        y[base + k * Ns] = acc;
+      }
+    }
+  }
+}
+
+// Any other radix (7, 11, 13): the same stage with the R inputs in a local
+// array (rare grid sizes; keeps the common radices' register use low).
+__device__ __noinline__ void fft_stage_any(int R, const double2 *b0, double2 *b1, int n,
+                                           int L, int Ns, const double2 *tw,
+                                           const double2 *root, int sign) {
+  const int m = n / R;
+  for (int t = threadIdx.x; t < L * m; t += blockDim.x) {
+    const int l = t / m, j = t - l * m;
+    const double2 *x = b0 + l * n;
+    double2 *y = b1 + l * n;
+    const int jm = j % Ns;
+    const int base = (j / Ns) * Ns * R + jm;
+    double2 v[kMaxRadix];
+    for (int r = 0; r < R; ++r) {
+      double2 a = x[j + r * m];
+      if (r > 0 && jm > 0) {
+        double2 w = tw[jm * R + r];
+        if (sign > 0) w.y = -w.y;
+        a = cmul(a, w);
+      }
+      v[r] = a;
+    }
+    for (int k = 0; k < R; ++k) {
+      double2 acc = v[0];
+      for (int r = 1; r < R; ++r) {
+        double2 w = root[(r * k) % R];
+        if (sign > 0) w.y = -w.y;
+        acc = cadd(acc, cmul(v[r], w));
+      }
+      y[base + k * Ns] = acc;
+    }
+  }
+}
+
 // One pass: 1-D FFTs of length n along the contiguous axis of [a][b][n],
 // output transposed to [k][a][b].  IN_REAL: input is a real array.
 // OUT_REAL: write the real part times `scale` to a real array.
@@ -113,56 +207,14 @@ k_fft_pass(const void *in, void *out, FftPlan pl, const double2 *tab,
   int Ns = 1;
   for (int s = 0; s < pl.ns; ++s) {
     const int R = pl.rad[s];
-    const int m = n / R;
     const double2 *tw = tab + pl.tw_off[s];
     const double2 *root = tab + pl.root_off[s];
-    for (int t = threadIdx.x; t < L * m; t += blockDim.x) {
-      const int l = t / m, j = t - l * m;
-      const double2 *x = b0 + l * n;
-      double2 *y = b1 + l * n;
-      const int jm = j % Ns;
-      const int base = (j / Ns) * Ns * R + jm;
-      double2 v[kMaxRadix];
-      for (int r = 0; r < R; ++r) {
-        double2 a = x[j + r * m];
-        if (r > 0 && jm > 0) {
-          double2 w = tw[jm * R + r];
-          if (sign > 0) w.y = -w.y;
-          a = cmul(a, w);
-        }
-        v[r] = a;
-      }
-      if (R == 4) {
-        const double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-        const double2 t2 = cadd(v[1], v[3]), t3 = cmuli(csub(v[1], v[3]), sign);
-        y[base] = cadd(t0, t2);
-        y[base + Ns] = cadd(t1, t3);
-        y[base + 2 * Ns] = csub(t0, t2);
-        y[base + 3 * Ns] = csub(t1, t3);
-      } else if (R == 2) {
-        y[base] = cadd(v[0], v[1]);
-        y[base + Ns] = csub(v[0], v[1]);
-      } else if (R == 3) {
-        const double c3 = 0.86602540378443864676;  // sqrt(3)/2
-        const double2 sm_ = cadd(v[1], v[2]), df = csub(v[1], v[2]);
-        const double2 a = make_double2(v[0].x - 0.5 * sm_.x, v[0].y - 0.5 * sm_.y);
-        double2 b = cmuli(df, sign);
-        b.x *= c3;
-        b.y *= c3;
-        y[base] = cadd(v[0], sm_);
-        y[base + Ns] = cadd(a, b);
-        y[base + 2 * Ns] = csub(a, b);
-      } else {
-        for (int k = 0; k < R; ++k) {
-          double2 acc = v[0];
-          for (int r = 1; r < R; ++r) {
-            double2 w = root[(r * k) % R];
-            if (sign > 0) w.y = -w.y;
-            acc = cadd(acc, cmul(v[r], w));
-          }
-          y[base + k * Ns] = acc;
-        }
-      }
+    switch (R) {
+      case 4: fft_stage<4>(b0, b1, n, L, Ns, tw, root, sign); break;
+      case 2: fft_stage<2>(b0, b1, n, L, Ns, tw, root, sign); break;
+      case 3: fft_stage<3>(b0, b1, n, L, Ns, tw, root, sign); break;
+      case 5: fft_stage<5>(b0, b1, n, L, Ns, tw, root, sign); break;
+      default: fft_stage_any(R, b0, b1, n, L, Ns, tw, root, sign); break;
     }
     __syncthreads();
     double2 *tmp = b0;
@@ -184,8 +236,27 @@ k_fft_pass(const void *in, void *out, FftPlan pl, const double2 *tab,
 }
 
 // v(G) = 4 pi n(G) / |G|^2 (G != 0), v(0) = 0; also folds in 1/N^3 of the
-// unnormalised inverse transform.
-__global__ void k_poisson_kernel(double2 *a, int n, double L) {
+// unnormalised inverse transform.  |G|^2 = (2 pi / L)^2 s with the integer
+// s = mx^2 + my^2 + mz^2, and inv_s[s] = 1 / s (inv_s[0] = 0) is a table per
+// grid size, so v(G) = c inv_s[s] n(G), c = 4 pi / ((2 pi / L)^2 N^3).
+__global__ void k_poisson_kernel(double2 *a, int n, double c, const double *inv_s) {
+  const size_t n3 = (size_t)n * n * n;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  const int kx = i % n, ky = (i / n) % n, kz = i / ((size_t)n * n);
+  const int mx = 2 * kx < n ? kx : kx - n;
+  const int my = 2 * ky < n ? ky : ky - n;
+  const int mz = 2 * kz < n ? kz : kz - n;
+  const double f = c * inv_s[mx * mx + my * my + mz * mz];
+  double2 v = a[i];
+  v.x *= f;
+  v.y *= f;
+  a[i] = v;
+}
+
+// The same multiplication with 4 pi / |G|^2 evaluated in place (no table):
+// used by the allocation-free entry point.
+__global__ void k_poisson_kernel_direct(double2 *a, int n, double L) {
   const size_t n3 = (size_t)n * n * n;
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n3) return;
@@ -299,6 +370,7 @@ struct PlanCache {
   int dev = -1, n = -1;
   FftPlan plan;
   double2 *tab = nullptr;
+  double *inv_s = nullptr;   // 1 / s for s = 0 .. 3 (n/2)^2, inv_s[0] = 0
 };
 std::mutex g_plan_mu;
 std::vector<PlanCache *> g_plans;
@@ -319,6 +391,18 @@ const PlanCache *get_plan(int n) {
   if (cudaMemcpy(c->tab, tab.data(), tab.size() * sizeof(double2),
                  cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(c->tab);
+    delete c;
+    return nullptr;
+  }
+  const int smax = 3 * (n / 2) * (n / 2);
+  std::vector<double> inv(smax + 1);
+  inv[0] = 0.0;
+  for (int q = 1; q <= smax; ++q) inv[q] = 1.0 / (double)q;
+  if (cudaMalloc(&c->inv_s, inv.size() * sizeof(double)) != cudaSuccess ||
+      cudaMemcpy(c->inv_s, inv.data(), inv.size() * sizeof(double),
+                 cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(c->tab);
+    if (c->inv_s) cudaFree(c->inv_s);
     delete c;
     return nullptr;
   }
@@ -348,7 +432,9 @@ void emd_launch_poisson(const GridInfo &g, const double *charge, double *v,
   k_fft_pass<true, false><<<blocks, 256, smem, st>>>(charge, wa, p, pc->tab, -1, 1.0);
   k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wa, wb, p, pc->tab, -1, 1.0);
   k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wb, wa, p, pc->tab, -1, 1.0);
-  k_poisson_kernel<<<(g.n3 + 255) / 256, 256, 0, st>>>(wa, g.n, g.L);
+  const double gq = 2.0 * M_PI / g.L;
+  const double cpois = 4.0 * M_PI / (gq * gq) / (double)g.n3;
+  k_poisson_kernel<<<(g.n3 + 255) / 256, 256, 0, st>>>(wa, g.n, cpois, pc->inv_s);
   k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wa, wb, p, pc->tab, +1, 1.0);
   k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wb, wa, p, pc->tab, +1, 1.0);
   k_fft_pass<false, true><<<blocks, 256, smem, st>>>(wa, v, p, pc->tab, +1, 1.0);
@@ -501,7 +587,7 @@ extern "C" int emd_poisson_static(int n, double h, const double *charge,
   k_fft_pass<true, false><<<blocks, 256, smem, st>>>(charge, wa, p, tab, -1, 1.0);
   k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wa, wb, p, tab, -1, 1.0);
   k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wb, wa, p, tab, -1, 1.0);
-  k_poisson_kernel<<<(unsigned)((n3 + 255) / 256), 256, 0, st>>>(wa, n, L);
+  k_poisson_kernel_direct<<<(unsigned)((n3 + 255) / 256), 256, 0, st>>>(wa, n, L);
   k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wa, wb, p, tab, +1, 1.0);
   k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wb, wa, p, tab, +1, 1.0);
   k_fft_pass<false, true><<<blocks, 256, smem, st>>>(wa, v, p, tab, +1, 1.0);
