@@ -196,28 +196,25 @@ def time_md(emd, torch, sysin, precision, steps, warmup, profile=True):
 
 def time_e2e(emd, torch, sysin, precision, steps):
     """Through the public API with host buffers: every step uploads orbitals
-    and ions from pinned memory, propagates one MD step and reads back the
-    orbitals, forces and energy."""
+    (complex64, the precision the system keeps them in) and ions from pinned
+    memory, propagates one MD step and reads back the orbitals, forces and
+    energy."""
     import numpy as np
     s = sysin
-    psi_pin = torch.empty(s.psi.shape, dtype=torch.complex128, pin_memory=True)
+    psi_pin = torch.empty(s.psi.shape, dtype=torch.complex64, pin_memory=True)
     psi_pin.numpy()[...] = s.psi
-    out_pin = torch.empty(s.psi.shape, dtype=torch.complex128, pin_memory=True)
+    out_pin = torch.empty(s.psi.shape, dtype=torch.complex64, pin_memory=True)
     R = np.ascontiguousarray(s.R)
     V = np.ascontiguousarray(s.V)
     h = emd.emd_init_system(emd.config_for(s, precision))
     psi_np = psi_pin.numpy()
     out_np = out_pin.numpy()
-    import ctypes
-    lib = emd.load()
-    DP = ctypes.POINTER(ctypes.c_double)
 
     def one():
         emd.emd_set_ions(h, R, V)
-        emd.emd_set_orbitals(h, psi_np)
+        emd.emd_set_orbitals_c64(h, psi_np)
         emd.emd_propagate(h, 1, s.dt, s.mu)
-        emd._check(lib.emd_get_state(h, None, None,
-                                     out_np.view(np.float64).ctypes.data_as(DP), None))
+        emd.emd_get_orbitals_c64(h, s.n_orb, s.n, out=out_np)
         emd.emd_get_forces(h, s.n_atoms)
         emd.emd_get_energy(h)
 
@@ -229,8 +226,8 @@ def time_e2e(emd, torch, sysin, precision, steps):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     emd.emd_destroy(h)
-    bi = s.psi.nbytes + R.nbytes + V.nbytes
-    bo = s.psi.nbytes + 3 * 8 * s.n_atoms + 9 * 8
+    bi = psi_np.nbytes + R.nbytes + V.nbytes
+    bo = psi_np.nbytes + 3 * 8 * s.n_atoms + 9 * 8
     return dt, bi, bo
 
 
@@ -428,8 +425,8 @@ def main():
                  "speedup_fp32_over_fp64": value / ws / v64},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo,
-                "note": "per step: set_ions + set_orbitals (pinned host, complex128), "
-                        "propagate 1 MD step, get_state(psi) + get_forces + get_energy"},
+                "note": "per step: set_ions + set_orbitals_c64 (pinned host, complex64), "
+                        "propagate 1 MD step, get_orbitals_c64 + get_forces + get_energy"},
         "batched": batched,
         "adjoint": adjoint,
         "gpu_launches": r32["launches"],

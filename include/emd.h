@@ -149,6 +149,17 @@ int emd_set_ions(emd_system *s, int n_atoms, const double *R, const double *V);
  * eq. Ehr_ic: initial condition). */
 int emd_set_orbitals(emd_system *s, const double *psi);
 
+/* The same with complex64 host arrays (float32 interleaved (re, im), same
+ * canonical layout), for callers that keep orbitals in single precision:
+ * half the bytes over the host link.  For EMD_FP32_ORBITALS systems the
+ * stored orbitals are identical to those set from the complex128 values
+ * rounded to complex64.  No counterpart in the paper (host I/O). */
+int emd_set_orbitals_c64(emd_system *s, const float *psi);
+
+/* Orbitals of the current state as complex64 (float32 interleaved (re, im),
+ * canonical [n_orb][N][N][N], host).  EMD_FP64 systems round to float32. */
+int emd_get_orbitals_c64(emd_system *s, float *psi);
+
 /* Advance n_steps MD steps of length dt with the electronic mass-like
  * parameter mu (mu = 1: plain Ehrenfest).  field: NULL, or n_steps
  * amplitudes e_n (host) of a uniform field along z in the length gauge,

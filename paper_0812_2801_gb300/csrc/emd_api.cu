@@ -616,6 +616,51 @@ static int download_orbitals(emd_system *s, const void *src, int n_vec,
   return launch_check("download_orbitals");
 }
 
+// complex64 host arrays: the same staging, half the bytes over the link
+static int upload_orbitals_c64(emd_system *s, const float *psi, void *dst) {
+  const size_t n3 = s->g.n3;
+  const int n_vec = s->o.n_orb;
+  for (int b = 0; b * s->o.bo < n_vec; ++b) {
+    const int nv = std::min(s->o.bo, n_vec - b * s->o.bo);
+    CK(cudaMemcpyAsync(s->stage_buf, psi + 2 * (size_t)b * s->o.bo * n3,
+                       (size_t)nv * n3 * 8, cudaMemcpyHostToDevice, s->st));
+    char *d = (char *)dst + (size_t)b * n3 * s->o.bo *
+                                (s->o.prec == EMD_FP64 ? 16 : 8);
+    emd_launch_pack_c64(s->o, (const float2 *)s->stage_buf, d, nv, s->st);
+  }
+  return launch_check("upload_orbitals_c64");
+}
+
+int emd_set_orbitals_c64(emd_system *s, const float *psi) {
+  g_err.clear();
+  if (!s || !psi) return fail(EMD_EINVAL, "NULL argument");
+  CK(cudaMemsetAsync(s->psi, 0, s->orb_bytes, s->st));
+  int r = upload_orbitals_c64(s, psi, s->psi);
+  if (r) return r;
+  s->orbs_set = 1;
+  if (s->ions_set) return restart_dynamics(s);
+  CK(cudaStreamSynchronize(s->st));
+  return EMD_OK;
+}
+
+int emd_get_orbitals_c64(emd_system *s, float *psi) {
+  g_err.clear();
+  if (!s || !psi) return fail(EMD_EINVAL, "NULL argument");
+  int r = read_err_flag(s);
+  if (r) return r;
+  const size_t n3 = s->g.n3;
+  for (int b = 0; b * s->o.bo < s->o.n_orb; ++b) {
+    const int nv = std::min(s->o.bo, s->o.n_orb - b * s->o.bo);
+    const char *d = (const char *)s->psi + (size_t)b * n3 * s->o.bo *
+                                               (s->o.prec == EMD_FP64 ? 16 : 8);
+    emd_launch_unpack_c64(s->o, d, (float2 *)s->stage_buf, nv, s->st);
+    CK(cudaMemcpyAsync(psi + 2 * (size_t)b * s->o.bo * n3, s->stage_buf,
+                       (size_t)nv * n3 * 8, cudaMemcpyDeviceToHost, s->st));
+  }
+  CK(cudaStreamSynchronize(s->st));
+  return launch_check("emd_get_orbitals_c64");
+}
+
 int emd_set_orbitals(emd_system *s, const double *psi) {
   g_err.clear();
   if (!s || !psi) return fail(EMD_EINVAL, "NULL argument");

@@ -213,6 +213,11 @@ void emd_launch_pack(const OrbLayout &o, const double2 *canon, void *u,
                      int n_vec, cudaStream_t st);
 void emd_launch_unpack(const OrbLayout &o, const void *u, double2 *canon,
                        int n_vec, cudaStream_t st);
+// the same with complex64 host-side canonical arrays
+void emd_launch_pack_c64(const OrbLayout &o, const float2 *canon, void *u, int n_vec,
+                         cudaStream_t st);
+void emd_launch_unpack_c64(const OrbLayout &o, const void *u, float2 *canon, int n_vec,
+                           cudaStream_t st);
 void emd_launch_abs2_sum(const double2 *c, int n, double *out,
                          cudaStream_t st);
 

@@ -1189,8 +1189,9 @@ __global__ void k_nl_force_sum(const double *part, int n_atoms, int n_blk,
   F[i] = s;
 }
 
-template <typename T, int BO>
-__global__ void k_pack(const double2 *__restrict__ canon,
+// canonical [n_vec][n3] complex (C = double2 or float2) <-> orbital layout
+template <typename T, int BO, typename C>
+__global__ void k_pack(const C *__restrict__ canon,
                        typename cplx<T>::type *__restrict__ u, size_t n3,
                        int n_vec, int n_blk_vec) {
   typedef typename cplx<T>::type V;
@@ -1203,7 +1204,7 @@ __global__ void k_pack(const double2 *__restrict__ canon,
   const int A = b * BO + j;
   V v;
   if (A < n_vec) {
-    const double2 s = canon[(size_t)A * n3 + p];
+    const C s = canon[(size_t)A * n3 + p];
     v.x = (T)s.x;
     v.y = (T)s.y;
   } else {
@@ -1213,16 +1214,19 @@ __global__ void k_pack(const double2 *__restrict__ canon,
   u[i] = v;
 }
 
-template <typename T, int BO>
+template <typename T, int BO, typename C>
 __global__ void k_unpack(const typename cplx<T>::type *__restrict__ u,
-                         double2 *__restrict__ canon, size_t n3, int n_vec) {
+                         C *__restrict__ canon, size_t n3, int n_vec) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)n_vec * n3) return;
   const int A = i / n3;
   const size_t p = i % n3;
   const int b = A / BO, j = A % BO;
   const typename cplx<T>::type v = u[((size_t)b * n3 + p) * BO + j];
-  canon[i] = make_double2((double)v.x, (double)v.y);
+  C c;
+  c.x = v.x;
+  c.y = v.y;
+  canon[i] = c;
 }
 
 __global__ void __launch_bounds__(256)
@@ -1425,24 +1429,29 @@ void nlf_t(const OrbLayout &o, const TableSet &t, int n_atoms, const void *u,
                                             coef, inv_rc2, part);
 }
 
-template <typename T, int BO>
-void pack_t(const OrbLayout &o, const double2 *canon, void *u, int n_vec,
-            cudaStream_t st) {
+template <typename T, int BO, typename C>
+void pack_t(const OrbLayout &o, const C *canon, void *u, int n_vec, cudaStream_t st) {
   typedef typename cplx<T>::type V;
   const int nbv = (n_vec + BO - 1) / BO;
   const size_t tot = (size_t)nbv * o.n3 * BO;
-  k_pack<T, BO><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+  k_pack<T, BO, C><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
       canon, (V *)u, (size_t)o.n3, n_vec, nbv);
 }
 
-template <typename T, int BO>
-void unpack_t(const OrbLayout &o, const void *u, double2 *canon, int n_vec,
-              cudaStream_t st) {
+template <typename T, int BO, typename C>
+void unpack_t(const OrbLayout &o, const void *u, C *canon, int n_vec, cudaStream_t st) {
   typedef typename cplx<T>::type V;
   const size_t tot = (size_t)n_vec * o.n3;
-  k_unpack<T, BO><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+  k_unpack<T, BO, C><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
       (const V *)u, canon, (size_t)o.n3, n_vec);
 }
+
+#define EMD_DISPATCH_BO_C(T, C, FN, ...)             \
+  switch (o.bo) {                                    \
+    case 1: FN<T, 1, C>(__VA_ARGS__); break;         \
+    case 2: FN<T, 2, C>(__VA_ARGS__); break;         \
+    case 4: FN<T, 4, C>(__VA_ARGS__); break;         \
+  }
 
 }  // namespace
 
@@ -1527,9 +1536,9 @@ void emd_launch_pack(const OrbLayout &o, const double2 *canon, void *u,
                      int n_vec, cudaStream_t st) {
   emd_note_launches(1);
   if (o.prec == EMD_FP64) {
-    EMD_DISPATCH_BO(double, pack_t, o, canon, u, n_vec, st)
+    EMD_DISPATCH_BO_C(double, double2, pack_t, o, canon, u, n_vec, st)
   } else {
-    EMD_DISPATCH_BO(float, pack_t, o, canon, u, n_vec, st)
+    EMD_DISPATCH_BO_C(float, double2, pack_t, o, canon, u, n_vec, st)
   }
 }
 
@@ -1537,9 +1546,29 @@ void emd_launch_unpack(const OrbLayout &o, const void *u, double2 *canon,
                        int n_vec, cudaStream_t st) {
   emd_note_launches(1);
   if (o.prec == EMD_FP64) {
-    EMD_DISPATCH_BO(double, unpack_t, o, u, canon, n_vec, st)
+    EMD_DISPATCH_BO_C(double, double2, unpack_t, o, u, canon, n_vec, st)
   } else {
-    EMD_DISPATCH_BO(float, unpack_t, o, u, canon, n_vec, st)
+    EMD_DISPATCH_BO_C(float, double2, unpack_t, o, u, canon, n_vec, st)
+  }
+}
+
+void emd_launch_pack_c64(const OrbLayout &o, const float2 *canon, void *u, int n_vec,
+                         cudaStream_t st) {
+  emd_note_launches(1);
+  if (o.prec == EMD_FP64) {
+    EMD_DISPATCH_BO_C(double, float2, pack_t, o, canon, u, n_vec, st)
+  } else {
+    EMD_DISPATCH_BO_C(float, float2, pack_t, o, canon, u, n_vec, st)
+  }
+}
+
+void emd_launch_unpack_c64(const OrbLayout &o, const void *u, float2 *canon, int n_vec,
+                           cudaStream_t st) {
+  emd_note_launches(1);
+  if (o.prec == EMD_FP64) {
+    EMD_DISPATCH_BO_C(double, float2, unpack_t, o, u, canon, n_vec, st)
+  } else {
+    EMD_DISPATCH_BO_C(float, float2, unpack_t, o, u, canon, n_vec, st)
   }
 }
 

@@ -69,6 +69,8 @@ def load() -> ctypes.CDLL:
     lib.emd_init_system.argtypes = [ctypes.POINTER(emd_config), ctypes.POINTER(vp)]
     lib.emd_set_ions.argtypes = [vp, ip, _DPTR, _DPTR]
     lib.emd_set_orbitals.argtypes = [vp, _DPTR]
+    lib.emd_set_orbitals_c64.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.emd_get_orbitals_c64.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.emd_propagate.argtypes = [vp, ip, dp, dp, _DPTR]
     lib.emd_get_forces.argtypes = [vp, _DPTR]
     lib.emd_get_energy.argtypes = [vp, ctypes.POINTER(emd_energy)]
@@ -134,6 +136,23 @@ def emd_set_ions(h, R: np.ndarray, V: np.ndarray) -> None:
 def emd_set_orbitals(h, psi: np.ndarray) -> None:
     psi = _c128(psi)
     _check(load().emd_set_orbitals(h, psi.view(np.float64).ctypes.data_as(_DPTR)))
+
+
+def emd_set_orbitals_c64(h, psi: np.ndarray) -> None:
+    """Orbitals from a complex64 array [n_orb, N, N, N]."""
+    psi = np.ascontiguousarray(psi, dtype=np.complex64)
+    _check(load().emd_set_orbitals_c64(
+        h, psi.view(np.float32).ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+
+def emd_get_orbitals_c64(h, n_orb: int, n: int, out: Optional[np.ndarray] = None) -> np.ndarray:
+    """Orbitals of the current state as complex64 [n_orb, N, N, N] (into out
+    if given, which must be C-contiguous complex64 of that shape)."""
+    if out is None:
+        out = np.empty((n_orb, n, n, n), dtype=np.complex64)
+    _check(load().emd_get_orbitals_c64(
+        h, out.view(np.float32).ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out
 
 
 def emd_propagate(h, n_steps: int, dt: float, mu: float,

@@ -304,3 +304,33 @@ def test_fp32_energy_terms_match_oracle(small):
     eo = O.energies(O.init_state(s32))
     for k in ("kin_e", "nl", "es", "xc", "sr", "kin_ion", "total"):
         assert abs(eg[k] - eo[k]) <= 2e-6 * max(abs(eo[k]), 1e-3), (k, eg[k], eo[k])
+
+
+def test_complex64_host_io(small):
+    """emd_set_orbitals_c64 / emd_get_orbitals_c64: a complex64 system set
+    from complex64 host values holds exactly the complex128 path's rounded
+    orbitals (same trajectory bitwise); FP64 systems widen and round."""
+    s = small
+    psi64 = s.psi.astype(np.complex64)
+    a = emd.System(s, emd.EMD_FP32_ORBITALS)
+    b = emd.emd_init_system(emd.config_for(s, emd.EMD_FP32_ORBITALS))
+    emd.emd_set_ions(b, s.R, s.V)
+    emd.emd_set_orbitals_c64(b, psi64)
+    assert np.array_equal(emd.emd_get_orbitals_c64(b, s.n_orb, s.n), psi64)
+    a.propagate(3, dt=0.04, mu=1.0)
+    emd.emd_propagate(b, 3, 0.04, 1.0)
+    Ra, Va, psia, rhoa = a.state()
+    Rb, Vb, psib, rhob = emd.emd_get_state(b, s.n_atoms, s.n_orb, s.n)
+    assert np.array_equal(psia, psib) and np.array_equal(Ra, Rb) and np.array_equal(rhoa, rhob)
+    assert np.array_equal(emd.emd_get_orbitals_c64(b, s.n_orb, s.n), psib.astype(np.complex64))
+    a.close()
+    emd.emd_destroy(b)
+    d = emd.emd_init_system(emd.config_for(s, emd.EMD_FP64))
+    emd.emd_set_ions(d, s.R, s.V)
+    emd.emd_set_orbitals_c64(d, psi64)
+    _, _, psid, _ = emd.emd_get_state(d, s.n_atoms, s.n_orb, s.n)
+    assert np.array_equal(psid, psi64.astype(np.complex128))
+    emd.emd_propagate(d, 1, 0.04, 1.0)
+    _, _, psid, _ = emd.emd_get_state(d, s.n_atoms, s.n_orb, s.n)
+    assert np.array_equal(emd.emd_get_orbitals_c64(d, s.n_orb, s.n), psid.astype(np.complex64))
+    emd.emd_destroy(d)
