@@ -47,6 +47,25 @@ BYTES_PER_UPDATE = {"f32": 24, "f64": 48}
 TRAFFIC_PER_LAUNCH = {"f32": 3.515e9, "f64": None}
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """max of x over the ranks of the default process group (x itself when
+    there is none); device: where the reduction tensor lives (cuda for NCCL,
+    cpu for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, ws: int, seconds_max: float) -> float:
+    """Weak scaling: every rank processes units_per_rank; the job's rate is
+    all ranks' units over the slowest rank's time."""
+    return ws * units_per_rank / seconds_max
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -378,20 +397,18 @@ def main():
     with ClockSampler(local) as clk:
         r32 = time_md(emd, torch, s, emd.EMD_FP32_ORBITALS, args.steps, args.warmup)
     barrier()
-    ms = r32["ms"]
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * upd_per_step * args.steps / (ms * 1e-3)
+    ms = max_over_ranks(r32["ms"], device="cuda")
+    value = whole_job_rate(upd_per_step * args.steps, ws, ms * 1e-3)
 
     # FP64 form on the same workload
     r64 = time_md(emd, torch, s, emd.EMD_FP64, args.fp64_steps, 1)
     v64 = upd_per_step * args.fp64_steps / (r64["ms"] * 1e-3)
 
     # end to end through the C ABI with host buffers
+    barrier()
     e2e_dt, bi, bo = time_e2e(emd, torch, s, emd.EMD_FP32_ORBITALS, args.e2e_steps)
-    e2e_val = ws * upd_per_step * args.e2e_steps / e2e_dt
+    e2e_dt = max_over_ranks(e2e_dt, device="cuda")
+    e2e_val = whole_job_rate(upd_per_step * args.e2e_steps, ws, e2e_dt)
 
     batched = None if args.no_batched else time_batched(emd, torch, args.batched_steps)
     adjoint = None if (args.no_adjoint or ws > 1) else time_adjoint(emd, torch)
