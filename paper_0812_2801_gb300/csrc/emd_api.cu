@@ -114,7 +114,8 @@ struct emd_system {
   void *hc = nullptr;
   int c_valid = 0;
   double *V = nullptr, *F = nullptr, *F_loc = nullptr, *F_nl = nullptr,
-         *F_sr = nullptr, *e_sr = nullptr, *nl_part = nullptr, *lf_part = nullptr;
+         *F_sr = nullptr, *e_sr = nullptr, *nl_part = nullptr, *lf_part = nullptr,
+         *sr_part = nullptr;
   double *partials = nullptr;
   int n_partials = 0;
   double *scal = nullptr;
@@ -269,7 +270,7 @@ void forces(emd_system *s, int k, double field, double dt, int update_v) {
                         -2.0 * s->sp.h_kb * s->cfg.occ, s->sp.inv_rc2,
                         s->nl_part, s->F_nl, s->st);
   emd_launch_short_range(s->sp, s->n_atoms, s->ts[k].Rw, s->g.L, s->F_sr,
-                         s->e_sr, s->st);
+                         s->e_sr, s->sr_part, s->st);
   emd_launch_vv_velocities(s->n_atoms, s->F_loc, s->F_nl, s->F_sr, field,
                            s->sp.z, s->F, s->V, dt, s->sp.mass, update_v,
                            s->st);
@@ -540,6 +541,7 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
   TRY(A((void **)&s->F_nl, na * 3 * 8));
   TRY(A((void **)&s->F_sr, na * 3 * 8));
   TRY(A((void **)&s->e_sr, na * 8));
+  TRY(A((void **)&s->sr_part, (size_t)na * EMD_SR_SPLIT * 4 * 8));
   TRY(A((void **)&s->nl_part, (size_t)na * o.n_blk * 3 * 8));
   TRY(A((void **)&s->lf_part, (size_t)na * EMD_SPLIT * 3 * 8));
   s->n_partials = std::max(1024, (int)((n3 + 255) / 256));
@@ -1646,7 +1648,7 @@ int emd_get_energy(emd_system *s, emd_energy *out) {
                           s->ts[cur].v_loc, s->partials, nb, s->st);
   emd_launch_sum(s->partials, nb, s->scal + 2, s->st);
   emd_launch_short_range(s->sp, s->n_atoms, s->ts[cur].Rw, s->g.L, s->F_sr,
-                         s->e_sr, s->st);
+                         s->e_sr, s->sr_part, s->st);
   emd_launch_sum(s->e_sr, s->n_atoms, s->scal + 3, s->st);
   emd_launch_dot_partials(s->g.n3, s->rho, s->eps_xc, nullptr, nullptr,
                           s->partials, nb, s->st);

@@ -11,6 +11,7 @@
 #define EMD_MAX_HALF_ORDER 6    // fd_order / 2 <= 6
 #define EMD_TE_CAP (EMD_TILE * EMD_TILE * EMD_TILE * EMD_PT_KMAX)
 #define EMD_GT_EXT 64
+#define EMD_SR_SPLIT 8          // CTAs per atom for the short-range ion term
 #define EMD_SPLIT 16            // CTAs per atom for table building and local forces
 
 // error bits raised by kernels (device flag, read by emd_get_*)
@@ -145,8 +146,8 @@ void emd_launch_local_force(const GridInfo &g, const SpeciesDev &sp,
                             int n_atoms, const TableSet &t, const double *v_es_a,
                             const double *v_es_b, double *part, double *F,
                             cudaStream_t st);
-void emd_launch_short_range(const SpeciesDev &sp, int n_atoms, const double *R,
-                            double L, double *F, double *e_part,
+void emd_launch_short_range(const SpeciesDev &sp, int n_atoms, const double *Rw,
+                            double L, double *F, double *e_part, double *part,
                             cudaStream_t st);
 void emd_launch_vv_positions(int n_atoms, const double *R, const double *V,
                              const double *F, double dt, double mass,

@@ -91,12 +91,12 @@ __device__ __forceinline__ double2 cmuli(double2 a, int sign) {
 template <int R>
 __device__ __forceinline__ void fft_stage(const double2 *b0, double2 *b1, int n, int L,
                                           int Ns, const double2 *tw, const double2 *root,
-                                          int sign) {
+                                          int sign, int stride) {
   const int m = n / R;
   for (int t = threadIdx.x; t < L * m; t += blockDim.x) {
     const int l = t / m, j = t - l * m;
-    const double2 *x = b0 + l * n;
-    double2 *y = b1 + l * n;
+    const double2 *x = b0 + l * stride;
+    double2 *y = b1 + l * stride;
     const int jm = j % Ns;
     const int base = (j / Ns) * Ns * R + jm;
     double2 v[R];
@@ -150,12 +150,12 @@ __device__ __forceinline__ void fft_stage(const double2 *b0, double2 *b1, int n,
 // array (rare grid sizes; keeps the common radices' register use low).
 __device__ __noinline__ void fft_stage_any(int R, const double2 *b0, double2 *b1, int n,
                                            int L, int Ns, const double2 *tw,
-                                           const double2 *root, int sign) {
+                                           const double2 *root, int sign, int stride) {
   const int m = n / R;
   for (int t = threadIdx.x; t < L * m; t += blockDim.x) {
     const int l = t / m, j = t - l * m;
-    const double2 *x = b0 + l * n;
-    double2 *y = b1 + l * n;
+    const double2 *x = b0 + l * stride;
+    double2 *y = b1 + l * stride;
     const int jm = j % Ns;
     const int base = (j / Ns) * Ns * R + jm;
     double2 v[kMaxRadix];
@@ -210,11 +210,11 @@ k_fft_pass(const void *in, void *out, FftPlan pl, const double2 *tab,
     const double2 *tw = tab + pl.tw_off[s];
     const double2 *root = tab + pl.root_off[s];
     switch (R) {
-      case 4: fft_stage<4>(b0, b1, n, L, Ns, tw, root, sign); break;
-      case 2: fft_stage<2>(b0, b1, n, L, Ns, tw, root, sign); break;
-      case 3: fft_stage<3>(b0, b1, n, L, Ns, tw, root, sign); break;
-      case 5: fft_stage<5>(b0, b1, n, L, Ns, tw, root, sign); break;
-      default: fft_stage_any(R, b0, b1, n, L, Ns, tw, root, sign); break;
+      case 4: fft_stage<4>(b0, b1, n, L, Ns, tw, root, sign, n); break;
+      case 2: fft_stage<2>(b0, b1, n, L, Ns, tw, root, sign, n); break;
+      case 3: fft_stage<3>(b0, b1, n, L, Ns, tw, root, sign, n); break;
+      case 5: fft_stage<5>(b0, b1, n, L, Ns, tw, root, sign, n); break;
+      default: fft_stage_any(R, b0, b1, n, L, Ns, tw, root, sign, n); break;
     }
     __syncthreads();
     double2 *tmp = b0;
@@ -232,6 +232,132 @@ k_fft_pass(const void *in, void *out, FftPlan pl, const double2 *tab,
       static_cast<double *>(out)[o] = v.x * scale;
     else
       static_cast<double2 *>(out)[o] = v;
+  }
+}
+
+// Real-data passes for even grids (n = 2m).  A pass transforms the A x B
+// lines of an [A][B][len] array along the contiguous axis and writes the
+// result transposed, [k][A][B].  MODE 0: complex to complex, length pl.n.
+// MODE 1 (real to complex): a real line x of length 2m is read as the m
+// complex values z_j = x_2j + i x_2j+1, transformed with the length-m plan,
+// and untangled into the half spectrum X_k, k = 0..m:
+//   X_k = E_k + W^k O_k,  E_k = (Z_k + conj Z_{m-k}) / 2,
+//   O_k = (Z_k - conj Z_{m-k}) / (2i),  W = exp(-2 pi i / 2m),  Z_m = Z_0.
+// MODE 2 (complex to real, the unnormalised inverse of a Hermitian spectrum
+// given by X_0..X_m): Z''_k = (X_k + conj X_{m-k}) + i conj(W^k) (X_k -
+// conj X_{m-k}) for k < m, an inverse length-m transform gives z, and
+// x_2j = Re z_j, x_2j+1 = Im z_j are written to the real array [B][A][x].
+template <int MODE>
+__global__ void __launch_bounds__(256)
+k_fft_pass_r(const void *in, void *out, FftPlan pl, const double2 *tab,
+             const double2 *rtw, int A, int B, int sign) {
+  extern __shared__ double2 sm[];
+  const int n = pl.n, L = pl.lines;
+  const int m = n;                        // MODE 1/2: the half length
+  const int lin = MODE == 2 ? m + 1 : n;  // complex values read per line
+  const int nlines = A * B;
+  const int l0 = blockIdx.x * L;
+  double2 *b0 = sm, *b1 = sm + L * (n + 1);
+  const int stride = n + 1;
+  if (MODE == 2) {
+    for (int t = threadIdx.x; t < L * lin; t += blockDim.x) {
+      const int l = t / lin, i = t - l * lin, line = l0 + l;
+      b1[l * stride + i] = line < nlines
+                               ? static_cast<const double2 *>(in)[(size_t)line * lin + i]
+                               : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < L * m; t += blockDim.x) {
+      const int l = t / m, k = t - l * m;
+      const double2 xk = b1[l * stride + k], xr = b1[l * stride + (m - k)];
+      const double2 cr = make_double2(xr.x, -xr.y);            // conj X_{m-k}
+      const double2 sp = cadd(xk, cr), df = csub(xk, cr);
+      const double2 w = rtw[k];                                 // W^k
+      const double2 wc = make_double2(w.x, -w.y);               // conj W^k
+      const double2 t2 = cmul(wc, df);
+      b0[l * stride + k] = make_double2(sp.x - t2.y, sp.y + t2.x);   // sp + i t2
+    }
+  } else {
+    for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
+      const int l = t / n, i = t - l * n, line = l0 + l;
+      b0[l * stride + i] = line < nlines
+                               ? static_cast<const double2 *>(in)[(size_t)line * n + i]
+                               : make_double2(0.0, 0.0);
+    }
+  }
+  __syncthreads();
+  int Ns = 1;
+  for (int s = 0; s < pl.ns; ++s) {
+    const int R = pl.rad[s];
+    const double2 *tw = tab + pl.tw_off[s];
+    const double2 *root = tab + pl.root_off[s];
+    switch (R) {
+      case 4: fft_stage<4>(b0, b1, n, L, Ns, tw, root, sign, stride); break;
+      case 2: fft_stage<2>(b0, b1, n, L, Ns, tw, root, sign, stride); break;
+      case 3: fft_stage<3>(b0, b1, n, L, Ns, tw, root, sign, stride); break;
+      case 5: fft_stage<5>(b0, b1, n, L, Ns, tw, root, sign, stride); break;
+      default: fft_stage_any(R, b0, b1, n, L, Ns, tw, root, sign, stride); break;
+    }
+    __syncthreads();
+    double2 *tmp = b0;
+    b0 = b1;
+    b1 = tmp;
+    Ns *= R;
+  }
+  if (MODE == 0) {
+    for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
+      const int k = t / L, l = t - k * L, line = l0 + l;
+      if (line >= nlines) continue;
+      const int a = line / B, b = line - a * B;
+      static_cast<double2 *>(out)[((size_t)k * A + a) * B + b] = b0[l * stride + k];
+    }
+  } else if (MODE == 1) {
+    for (int t = threadIdx.x; t < L * (m + 1); t += blockDim.x) {
+      const int k = t / L, l = t - k * L, line = l0 + l;
+      if (line >= nlines) continue;
+      const double2 zk = b0[l * stride + (k == m ? 0 : k)];
+      const double2 zr = b0[l * stride + (k == 0 ? 0 : m - k)];
+      const double2 cr = make_double2(zr.x, -zr.y);            // conj Z_{m-k}
+      const double2 e = make_double2(0.5 * (zk.x + cr.x), 0.5 * (zk.y + cr.y));
+      const double2 dd = csub(zk, cr);
+      const double2 o = make_double2(0.5 * dd.y, -0.5 * dd.x);  // dd / (2i)
+      const double2 xk = cadd(e, cmul(rtw[k], o));
+      const int a = line / B, b = line - a * B;
+      static_cast<double2 *>(out)[((size_t)k * A + a) * B + b] = xk;
+    }
+  } else {
+    for (int t = threadIdx.x; t < L * m; t += blockDim.x) {
+      const int l = t / m, j = t - l * m, line = l0 + l;
+      if (line >= nlines) continue;
+      const int a = line / B, b = line - a * B;
+      static_cast<double2 *>(out)[((size_t)b * A + a) * m + j] = b0[l * stride + j];
+    }
+  }
+}
+
+// [kz][ky][kx] (kx in 0..m) -> v(G) = c inv_s[s] n(G) written to
+// [kx][ky][kz], through 32 x 32 shared-memory tiles of each (kz, kx) plane
+__global__ void __launch_bounds__(256)
+k_poisson_transpose(const double2 *__restrict__ a, double2 *__restrict__ b, int n, int nh,
+                    double c, const double *__restrict__ inv_s) {
+  __shared__ double2 tile[32][33];
+  const int ky = blockIdx.z;
+  const int kx0 = blockIdx.x * 32, kz0 = blockIdx.y * 32;
+  const int my = 2 * ky < n ? ky : ky - n;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int kz = kz0 + r, kx = kx0 + threadIdx.x;
+    if (kz < n && kx < nh) {
+      const int mz = 2 * kz < n ? kz : kz - n;
+      const int mx = kx;   // kx <= n / 2 (the Nyquist plane has |mx| = n / 2 either way)
+      const double f = c * inv_s[mx * mx + my * my + mz * mz];
+      const double2 v = a[((size_t)kz * n + ky) * nh + kx];
+      tile[r][threadIdx.x] = make_double2(f * v.x, f * v.y);
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int kx = kx0 + r, kz = kz0 + threadIdx.x;
+    if (kz < n && kx < nh) b[((size_t)kx * n + ky) * n + kz] = tile[threadIdx.x][r];
   }
 }
 
@@ -286,9 +412,11 @@ __global__ void k_lda(int n3, const double *rho, const double *vh,
   const double r = rho[i];
   double e = 0.0, v = 0.0;
   if (r >= 1e-30) {
-    const double ex = -0.75 * cbrt(3.0 * r / M_PI);
+    // one cube root: (3 r / pi)^(1/3) = c1 r^(1/3), r_s = c2 / r^(1/3)
+    const double t = cbrt(r);
+    const double ex = -0.75 * (0.98474502184269654115 * t);   // (3/pi)^(1/3)
     const double vx = (4.0 / 3.0) * ex;
-    const double rs = cbrt(3.0 / (4.0 * M_PI * r));
+    const double rs = 0.62035049089940001667 / t;             // (3/(4 pi))^(1/3)
     double ec, vc;
     if (rs >= 1.0) {
       const double gam = -0.1423, b1 = 1.0529, b2 = 0.3334;
@@ -371,6 +499,7 @@ struct PlanCache {
   FftPlan plan;
   double2 *tab = nullptr;
   double *inv_s = nullptr;   // 1 / s for s = 0 .. 3 (n/2)^2, inv_s[0] = 0
+  double2 *rtw = nullptr;    // even n: W^k = exp(-2 pi i k / n), k = 0 .. n/2
 };
 std::mutex g_plan_mu;
 std::vector<PlanCache *> g_plans;
@@ -393,6 +522,18 @@ const PlanCache *get_plan(int n) {
     cudaFree(c->tab);
     delete c;
     return nullptr;
+  }
+  if (n % 2 == 0) {
+    std::vector<double2> w(n / 2 + 1);
+    for (int k = 0; k <= n / 2; ++k) w[k] = unit_root(k, n);
+    if (cudaMalloc(&c->rtw, w.size() * sizeof(double2)) != cudaSuccess ||
+        cudaMemcpy(c->rtw, w.data(), w.size() * sizeof(double2), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+      cudaFree(c->tab);
+      if (c->rtw) cudaFree(c->rtw);
+      delete c;
+      return nullptr;
+    }
   }
   const int smax = 3 * (n / 2) * (n / 2);
   std::vector<double> inv(smax + 1);
@@ -420,20 +561,45 @@ void emd_fft_plan_check(int n, int *ok) {
   *ok = make_plan(n, p, t);
 }
 
-int emd_fft_prepare(int n) { return get_plan(n) != nullptr ? 0 : 1; }
+int emd_fft_prepare(int n) {
+  if (get_plan(n) == nullptr) return 1;
+  if (n % 2 == 0 && get_plan(n / 2) == nullptr) return 1;
+  return 0;
+}
 
 void emd_launch_poisson(const GridInfo &g, const double *charge, double *v,
                         double2 *wa, double2 *wb, cudaStream_t st) {
-  emd_note_launches(7);
   const PlanCache *pc = get_plan(g.n);
+  const double gq = 2.0 * M_PI / g.L;
+  const double cpois = 4.0 * M_PI / (gq * gq) / (double)g.n3;
+  const int n = g.n;
+  if (n % 2 == 0) {
+    // real data: half-length transforms along x, half spectrum in kx
+    emd_note_launches(7);
+    const int m = n / 2, nh = m + 1;
+    const PlanCache *ph = get_plan(m);
+    const FftPlan &pf = pc->plan, &pm = ph->plan;
+    const size_t smf = 2 * (size_t)pf.lines * (n + 1) * sizeof(double2);
+    const size_t smm = 2 * (size_t)pm.lines * (m + 1) * sizeof(double2);
+    const int bx = (n * n + pm.lines - 1) / pm.lines;     // lines along x
+    const int bh = (nh * n + pf.lines - 1) / pf.lines;    // lines along y or z
+    k_fft_pass_r<1><<<bx, 256, smm, st>>>(charge, wa, pm, ph->tab, pc->rtw, n, n, -1);
+    k_fft_pass_r<0><<<bh, 256, smf, st>>>(wa, wb, pf, pc->tab, nullptr, nh, n, -1);
+    k_fft_pass_r<0><<<bh, 256, smf, st>>>(wb, wa, pf, pc->tab, nullptr, n, nh, -1);
+    k_poisson_transpose<<<dim3((nh + 31) / 32, (n + 31) / 32, n), dim3(32, 8), 0, st>>>(
+        wa, wb, n, nh, cpois, pc->inv_s);
+    k_fft_pass_r<0><<<bh, 256, smf, st>>>(wb, wa, pf, pc->tab, nullptr, nh, n, +1);
+    k_fft_pass_r<0><<<bh, 256, smf, st>>>(wa, wb, pf, pc->tab, nullptr, n, nh, +1);
+    k_fft_pass_r<2><<<bx, 256, smm, st>>>(wb, v, pm, ph->tab, pc->rtw, n, n, +1);
+    return;
+  }
+  emd_note_launches(7);
   const FftPlan &p = pc->plan;
   const int blocks = (g.n * g.n + p.lines - 1) / p.lines;
   const size_t smem = 2 * (size_t)p.lines * g.n * sizeof(double2);
   k_fft_pass<true, false><<<blocks, 256, smem, st>>>(charge, wa, p, pc->tab, -1, 1.0);
   k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wa, wb, p, pc->tab, -1, 1.0);
   k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wb, wa, p, pc->tab, -1, 1.0);
-  const double gq = 2.0 * M_PI / g.L;
-  const double cpois = 4.0 * M_PI / (gq * gq) / (double)g.n3;
   k_poisson_kernel<<<(g.n3 + 255) / 256, 256, 0, st>>>(wa, g.n, cpois, pc->inv_s);
   k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wa, wb, p, pc->tab, +1, 1.0);
   k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wb, wa, p, pc->tab, +1, 1.0);

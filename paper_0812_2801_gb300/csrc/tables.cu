@@ -644,20 +644,24 @@ __global__ void k_local_force_sum(const double *part, int n_atoms, int nsplit,
 }
 
 // Short-range ion-ion term E_sr = 1/2 sum' Z^2 erfc(d/s)/d (s = sqrt2 a, d <
-// 12 bohr, all images) and its force.  One block per atom J, threads over
-// (atom K, image) pairs, fixed-order block sum.
+// 12 bohr, all images) and its force.  Grid (atom J, split): the (atom K,
+// image) pairs of J are cut into EMD_SR_SPLIT contiguous ranges, each CTA
+// writes an FP64 partial (fixed-order block sum), and k_short_range_sum adds
+// the partials in split order.
 __global__ void __launch_bounds__(256)
 k_short_range(SpeciesDev sp, int n_atoms, const double *Rw, double L, int nmax,
-              double *F, double *e_part) {
+              double *part) {
   __shared__ double red[8 * 4];
-  const int J = blockIdx.x;
+  const int J = blockIdx.x, split = blockIdx.y, nsplit = gridDim.y;
   const double s = sqrt(2.0) * sp.a_loc;
   const double zz = sp.z * sp.z;
   const double rcut = 12.0;
   const double k2 = 2.0 / (s * sqrt(M_PI));
   const int side = 2 * nmax + 1, nimg = side * side * side;
+  const int total = n_atoms * nimg, per = (total + nsplit - 1) / nsplit;
+  const int q0 = split * per, q1 = min(total, q0 + per);
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int q = threadIdx.x; q < n_atoms * nimg; q += blockDim.x) {
+  for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
     const int K = q / nimg, im = q % nimg;
     const int nx = im % side - nmax, ny = (im / side) % side - nmax,
               nz = im / (side * side) - nmax;
@@ -676,12 +680,21 @@ k_short_range(SpeciesDev sp, int n_atoms, const double *Rw, double L, int nmax,
     acc[3] += fm * dv2;
   }
   emd_block_sum<4>(acc, red);
-  if (threadIdx.x == 0) {
-    e_part[J] = 0.5 * zz * acc[0];
-    F[3 * J] = acc[1];
-    F[3 * J + 1] = acc[2];
-    F[3 * J + 2] = acc[3];
-  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) part[((size_t)J * nsplit + split) * 4 + k] = acc[k];
+}
+
+__global__ void k_short_range_sum(const double *part, int n_atoms, int nsplit, double zz,
+                                  double *F, double *e_part) {
+  const int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= n_atoms) return;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = 0; k < nsplit; ++k)
+    for (int c = 0; c < 4; ++c) a[c] += part[((size_t)J * nsplit + k) * 4 + c];
+  e_part[J] = 0.5 * zz * a[0];
+  F[3 * J] = a[1];
+  F[3 * J + 1] = a[2];
+  F[3 * J + 2] = a[3];
 }
 
 // R(t+dt) = R + V dt + F dt^2 / (2M), in the reference's rounding order.
@@ -786,12 +799,17 @@ void emd_launch_local_force_hvp(const GridInfo &g, const SpeciesDev &sp,
 }
 
 void emd_launch_short_range(const SpeciesDev &sp, int n_atoms, const double *Rw,
-                            double L, double *F, double *e_part,
+                            double L, double *F, double *e_part, double *part,
                             cudaStream_t st) {
   if (n_atoms <= 0) return;
-  emd_note_launches(1);
-  const int nmax = (int)ceil(12.0 / L) + 1;
-  k_short_range<<<n_atoms, 256, 0, st>>>(sp, n_atoms, Rw, L, nmax, F, e_part);
+  emd_note_launches(2);
+  // pairs within 12 bohr: wrapped positions differ by less than L, so image
+  // shifts up to (12 + L) / L box lengths suffice
+  const int nmax = (int)floor((12.0 + L) / L);
+  dim3 grid(n_atoms, EMD_SR_SPLIT);
+  k_short_range<<<grid, 256, 0, st>>>(sp, n_atoms, Rw, L, nmax, part);
+  k_short_range_sum<<<(n_atoms + 127) / 128, 128, 0, st>>>(part, n_atoms, EMD_SR_SPLIT,
+                                                          sp.z * sp.z, F, e_part);
 }
 
 void emd_launch_vv_positions(int n_atoms, const double *R, const double *V,
