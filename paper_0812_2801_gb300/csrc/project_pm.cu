@@ -323,19 +323,33 @@ k_tile_gather(const float2 *__restrict__ u, int n, int nt, int n_orb_pad,
           }
         }
       } else {
-        const uint2 rec = __ldg(te_pp + tb + e);
-        const float pv = __uint_as_float(rec.y);
-        const float4 *v4 = reinterpret_cast<const float4 *>(us + rec.x * BO);
+        // up to EU entries of this lane in flight: records first, then the
+        // tile values, then the multiply-adds (in entry order)
+        constexpr int EU = 4;
+        uint2 rec[EU];
 #pragma unroll
-        for (int h = 0; h < (BO + 1) / 2; ++h) {
-          const float4 v = BO == 1 ? make_float4(us[rec.x].x, us[rec.x].y, 0.f, 0.f) : v4[h];
+        for (int u = 0; u < EU; ++u)
+          rec[u] = e + 32 * u < e1 ? __ldg(te_pp + tb + e + 32 * u) : make_uint2(0u, 0u);
+        float4 vv[EU][(BO + 1) / 2];
 #pragma unroll
-          for (int jj = 0; jj < (BO == 1 ? 1 : 2); ++jj) {
-            const int j = 2 * h + jj;
-            acc[2 * j] += pv * (jj ? v.z : v.x);
-            acc[2 * j + 1] += pv * (jj ? v.w : v.y);
-          }
+        for (int u = 0; u < EU; ++u)
+#pragma unroll
+          for (int h = 0; h < (BO + 1) / 2; ++h)
+            vv[u][h] = BO == 1 ? make_float4(us[rec[u].x].x, us[rec[u].x].y, 0.f, 0.f)
+                               : reinterpret_cast<const float4 *>(us + rec[u].x * BO)[h];
+#pragma unroll
+        for (int u = 0; u < EU; ++u) {
+          const float pv = __uint_as_float(rec[u].y);   // 0 past the slot's end
+#pragma unroll
+          for (int h = 0; h < (BO + 1) / 2; ++h)
+#pragma unroll
+            for (int jj = 0; jj < (BO == 1 ? 1 : 2); ++jj) {
+              const int j = 2 * h + jj;
+              acc[2 * j] += pv * (jj ? vv[u][h].z : vv[u][h].x);
+              acc[2 * j + 1] += pv * (jj ? vv[u][h].w : vv[u][h].y);
+            }
         }
+        e += 32 * (EU - 1);
       }
     }
     warp_sum<NA>(acc);
