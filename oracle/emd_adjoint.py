@@ -89,7 +89,7 @@ class TorchStep:
         return torch.fft.ifftn(torch.fft.fftn(rho) * self.kern).real
 
     def lda(self, rho):
-        P = O.PZ81
+        P = O.PZ81_C1
         r = torch.clamp(rho, min=1e-30)
         ex = -0.75 * (3.0 * r / math.pi) ** (1.0 / 3.0)
         vx = (4.0 / 3.0) * ex

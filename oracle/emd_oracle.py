@@ -17,8 +17,8 @@ follows.  The method computed here is:
   its degree-4 Taylor polynomial (Sec. 5.1), in the fictitious time of
   eq. transf, i.e. each half step is exp(-i tau H) with tau = dt / (2 mu);
   H(t+dt) uses the ionic part at R(t+dt) and a Hartree+xc potential
-  extrapolated from the previous steps (Sec. 5.1: "interpolation from
-  previous steps"; quadratic extrapolation);
+  extrapolated from the previous steps (Sec. 5.1 builds H(t+dt) from earlier
+  steps without fixing the order; quadratic extrapolation);
 * ions: velocity Verlet (Sec. 5.1) with F = -dE_KS/dR at fixed orbitals
   (eq. new_EoM_b), taken as the exact derivative of the discrete energy;
 * density rho = 2 sum_A |phi_A|^2 (eq. density), Hartree potential from a
@@ -213,8 +213,33 @@ PZ81 = dict(gamma=-0.1423, beta1=1.0529, beta2=0.3334,
             A=0.0311, B=-0.048, C=0.0020, D=-0.0116)
 
 
+def pz81_continuous(P: dict = PZ81) -> dict:
+    """PZ81 with C and D of the r_s < 1 branch fixed by continuity at r_s = 1.
+
+    Matching the value and the first derivative of the two branches at
+    r_s = 1 gives, with q = 1 + beta1 + beta2,
+        B + D = gamma / q
+        A + C + D = -gamma (beta1 / 2 + beta2) / q^2
+    The published C and D are these values rounded to four decimals.  With
+    the rounded values eps_c jumps by 3.2e-5 Ha at r_s = 1, so the discrete
+    E_KS of eq. E_KS is not differentiable there: each grid point whose
+    density crosses 3 / (4 pi) changes E by about rho h^3 * 3.2e-5 while H
+    (its derivative elsewhere) does not see it, and the energy of eq. E_new
+    drifts at a rate set by how often points cross, not by dt.  Continuous
+    C and D make H the derivative of E_KS everywhere.
+    """
+    q = 1.0 + P["beta1"] + P["beta2"]
+    D = P["gamma"] / q - P["B"]
+    C = -P["gamma"] * (0.5 * P["beta1"] + P["beta2"]) / (q * q) - P["A"] - D
+    return {**P, "C": C, "D": D}
+
+
+PZ81_C1 = pz81_continuous(PZ81)
+
+
 def lda_pz81(rho: np.ndarray):
-    """Unpolarised Perdew-Zunger LDA (Sec. 5): returns (eps_xc, v_xc).
+    """Unpolarised Perdew-Zunger LDA (Sec. 5) with the continuous C, D of
+    ``pz81_continuous``: returns (eps_xc, v_xc).
 
     eps_x = -(3/4)(3 rho/pi)^(1/3), v_x = (4/3) eps_x.
     r_s >= 1: eps_c = gamma / (1 + beta1 sqrt(r_s) + beta2 r_s)
@@ -230,7 +255,7 @@ def lda_pz81(rho: np.ndarray):
     ex = -0.75 * np.cbrt(3.0 * r / math.pi)
     vx = (4.0 / 3.0) * ex
     rs = np.cbrt(3.0 / (4.0 * math.pi * r))
-    P = PZ81
+    P = PZ81_C1
     ec = np.empty_like(r)
     vc = np.empty_like(r)
     hi = rs >= 1.0

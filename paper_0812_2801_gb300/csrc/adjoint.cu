@@ -117,7 +117,7 @@ __device__ double fxc_pz81(double r) {
   const double drs = -rs / (3.0 * r);
   double dvc;
   if (rs >= 1.0) {
-    const double gam = -0.1423, b1 = 1.0529, b2 = 0.3334;
+    using namespace pz81;
     const double s = sqrt(rs);
     const double q = 1.0 + b1 * s + b2 * rs;
     const double nn = 1.0 + (7.0 / 6.0) * b1 * s + (4.0 / 3.0) * b2 * rs;
@@ -125,7 +125,7 @@ __device__ double fxc_pz81(double r) {
     const double dn = (7.0 / 6.0) * b1 / (2.0 * s) + (4.0 / 3.0) * b2;
     dvc = gam * (dn * q - 2.0 * nn * dq) / (q * q * q);
   } else {
-    const double A = 0.0311, C = 0.0020, D = -0.0116;
+    using namespace pz81;
     dvc = A / rs + (2.0 / 3.0) * C * (log(rs) + 1.0) + (2.0 * D - C) / 3.0;
   }
   return dvx + dvc * drs;

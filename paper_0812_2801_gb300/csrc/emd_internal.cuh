@@ -15,6 +15,21 @@
 #define EMD_SPLIT 16            // CTAs per atom for table building and local forces
 
 // error bits raised by kernels (device flag, read by emd_get_*)
+// Perdew-Zunger (1981) correlation of the unpolarised uniform gas, the LDA
+// of Sec. 5: eps_c = gam / (1 + b1 sqrt(r_s) + b2 r_s) for r_s >= 1 and
+// A ln r_s + B + C r_s ln r_s + D r_s below.  C and D follow from continuity
+// of eps_c and d eps_c / d r_s at r_s = 1 (the published four-decimal values
+// are these rounded); with the rounded ones eps_c jumps by 3.2e-5 Ha at
+// r_s = 1 and E_KS is not differentiable where a grid point's density
+// crosses 3 / (4 pi), which shows up as an energy drift independent of dt.
+namespace pz81 {
+constexpr double gam = -0.1423, b1 = 1.0529, b2 = 0.3334;
+constexpr double A = 0.0311, B = -0.048;
+constexpr double q1 = 1.0 + b1 + b2;
+constexpr double D = gam / q1 - B;                                  // eps_c
+constexpr double C = -gam * (0.5 * b1 + b2) / (q1 * q1) - A - D;    // slope
+}  // namespace pz81
+
 #define EMD_ERRBIT_PT   1       // per-point list overflow
 #define EMD_ERRBIT_TILE 2       // per-tile candidate overflow
 #define EMD_ERRBIT_AT   4       // per-atom table overflow

@@ -419,13 +419,13 @@ __global__ void k_lda(int n3, const double *rho, const double *vh,
     const double rs = 0.62035049089940001667 / t;             // (3/(4 pi))^(1/3)
     double ec, vc;
     if (rs >= 1.0) {
-      const double gam = -0.1423, b1 = 1.0529, b2 = 0.3334;
+      using namespace pz81;
       const double s = sqrt(rs);
       const double q = 1.0 + b1 * s + b2 * rs;
       ec = gam / q;
       vc = gam * (1.0 + (7.0 / 6.0) * b1 * s + (4.0 / 3.0) * b2 * rs) / (q * q);
     } else {
-      const double A = 0.0311, B = -0.048, C = 0.0020, D = -0.0116;
+      using namespace pz81;
       const double lx = log(rs);
       ec = A * lx + B + C * rs * lx + D * rs;
       vc = A * lx + (B - A / 3.0) + (2.0 / 3.0) * C * rs * lx +

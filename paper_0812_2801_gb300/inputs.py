@@ -203,6 +203,15 @@ def precision_c96(mu: float = 10.0) -> SystemInput:
                         mu=mu, dt=dt, n_steps=1000)
 
 
+def conservation_c48(mu: float = 10.0) -> SystemInput:
+    """8 atoms (sc 2^3, 6.0 bohr), 16 orbitals, 48^3 grid at 0.25 bohr, order 8:
+    the 96^3 workload's local structure in a box of 2^3 sites; its density
+    peaks near 0.25, so grid points cross r_s = 1 as the orbitals move."""
+    R = jitter(lattice_sites("sc", 2, 6.0), seed=1)
+    return build_system("conservation-8at-48^3", 48, 0.25, 8, R, 2, 3,
+                        mu=mu, dt=0.05 * math.sqrt(mu), n_steps=24)
+
+
 def field_c64(n_steps: int = 200) -> SystemInput:
     """16 atoms (bcc 2x2x2, a = 9.6), 32 orbitals, 64^3 at 0.3, order 6, field."""
     R = jitter(lattice_sites("bcc", 2, 9.6), seed=1)

@@ -393,21 +393,48 @@ def test_pz81_constants_exchange_and_continuity():
     P = golden_pz()
     for k in ("gamma", "beta1", "beta2", "A", "B", "C", "D"):
         assert O.PZ81[k] == P[k]
+    # the continuous C, D round to the published four-decimal values
+    Pc = O.PZ81_C1
+    for k in ("gamma", "beta1", "beta2", "A", "B"):
+        assert Pc[k] == P[k]
+    assert abs(Pc["C"] - P["C"]) < 5e-5 and Pc["C"] != P["C"]
+    assert abs(Pc["D"] - P["D"]) < 5e-5 and Pc["D"] != P["D"]
     for rs in (0.5, 1.0, 2.0, 5.0):
         rho = 3.0 / (4 * math.pi * rs ** 3)
         eps, _ = O.lda_pz81(np.array([rho]))
-        P_ = O.PZ81
         if rs >= 1:
-            ec = P_["gamma"] / (1 + P_["beta1"] * math.sqrt(rs) + P_["beta2"] * rs)
+            ec = P["gamma"] / (1 + P["beta1"] * math.sqrt(rs) + P["beta2"] * rs)
         else:
-            ec = P_["A"] * math.log(rs) + P_["B"] + P_["C"] * rs * math.log(rs) + P_["D"] * rs
+            ec = Pc["A"] * math.log(rs) + Pc["B"] + Pc["C"] * rs * math.log(rs) + Pc["D"] * rs
         assert abs(eps[0] - ec - P["eps_x_times_rs"] / rs) < 1e-12
-    # the two branches of the fit meet at r_s = 1 (value and potential)
+    # eps_c and v_xc are continuous at r_s = 1 (v continuous <=> d eps/d r_s
+    # continuous, given eps continuous): across rho1 (1 +- 1e-9) both move by
+    # O(1e-9) only.  The published rounding leaves jumps of 3.2e-5 and 2.7e-5.
     rho1 = 3.0 / (4 * math.pi)
     lo = O.lda_pz81(np.array([rho1 * (1 + 1e-9)]))
     hi = O.lda_pz81(np.array([rho1 * (1 - 1e-9)]))
-    assert abs(lo[0][0] - hi[0][0]) < 1e-4
-    assert abs(lo[1][0] - hi[1][0]) < 2e-3
+    assert abs(lo[0][0] - hi[0][0]) < 1e-9
+    assert abs(lo[1][0] - hi[1][0]) < 1e-9
+    # and the slope of v across r_s = 1 differs by O(1) only (no kink blowing up)
+    d = 1e-6
+    slope = [(O.lda_pz81(np.array([rho1 * (1 + s * d + d)]))[1][0]
+              - O.lda_pz81(np.array([rho1 * (1 + s * d - d)]))[1][0]) / (2 * d * rho1)
+             for s in (-2.0, 2.0)]
+    assert abs(slope[0] - slope[1]) < 0.05 * abs(slope[0])
+
+
+def test_lda_energy_continuous_along_a_path_through_rs_one():
+    """E_xc = h^3 sum rho eps_xc along rho(s) = rho1 (1 + s), s in [-1e-3, 1e-3]
+    on a single point: with continuous C, D its derivative equals h^3 v_xc
+    rho1 on both sides of r_s = 1, so the integral of v along the path equals
+    the change of E (no hidden jump)."""
+    rho1 = 3.0 / (4 * math.pi)
+    s = np.linspace(-1e-3, 1e-3, 20001)
+    rho = rho1 * (1 + s)
+    eps, v = O.lda_pz81(rho)
+    e = rho * eps
+    work = np.trapezoid(v, rho)
+    assert abs((e[-1] - e[0]) - work) < 1e-12
 
 
 def test_lda_potential_is_derivative_of_energy_density():
