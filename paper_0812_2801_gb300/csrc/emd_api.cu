@@ -43,20 +43,30 @@ int fail(int code, const char *fmt, ...) {
       return fail(EMD_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
-double fd_weight(int order, int k) {
-  // central second-derivative weights (Fornberg), k = 0..order/2
-  static const double w2[] = {-2.0, 1.0};
-  static const double w4[] = {-5.0 / 2.0, 4.0 / 3.0, -1.0 / 12.0};
-  static const double w6[] = {-49.0 / 18.0, 3.0 / 2.0, -3.0 / 20.0, 1.0 / 90.0};
-  static const double w8[] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0,
-                              -1.0 / 560.0};
+// central second-derivative weights (Fornberg), k = 0..order/2, as integer
+// numerators over the common denominator fd_den(order): c_k = fd_num / fd_den.
+// The numerators are exact in float and sum to zero (num_0 + 2 sum num_k = 0).
+double fd_num(int order, int k) {
+  static const double n2[] = {-2.0, 1.0};
+  static const double n4[] = {-30.0, 16.0, -1.0};
+  static const double n6[] = {-490.0, 270.0, -27.0, 2.0};
+  static const double n8[] = {-14350.0, 8064.0, -1008.0, 128.0, -9.0};
   switch (order) {
-    case 2: return w2[k];
-    case 4: return w4[k];
-    case 6: return w6[k];
-    default: return w8[k];
+    case 2: return n2[k];
+    case 4: return n4[k];
+    case 6: return n6[k];
+    default: return n8[k];
   }
 }
+double fd_den(int order) {
+  switch (order) {
+    case 2: return 1.0;
+    case 4: return 12.0;
+    case 6: return 180.0;
+    default: return 5040.0;
+  }
+}
+double fd_weight(int order, int k) { return fd_num(order, k) / fd_den(order); }
 
 }  // namespace
 
@@ -277,7 +287,7 @@ void forces(emd_system *s, int k, double field, double dt, int update_v) {
 }
 
 int reduce_max_veff(emd_system *s, double *out);
-void kinetic_fp32(emd_system *s, int *np);
+double kinetic_fp32(emd_system *s, int *np);
 
 // After new orbitals or ions: rho(0), v_Hxc(0), F(0); history restarts.
 int restart_dynamics(emd_system *s) {
@@ -329,14 +339,22 @@ void negate_grid(double *v, int n3, cudaStream_t st) {
   emd_note_launches(1);
   k_negate<<<(n3 + 255) / 256, 256, 0, st>>>(v, n3);
 }
-// complex64: partial sums of Re<psi|T psi> (T psi by the stage kernel with
-// diagonal w_0, no potential and zero projector coefficients, into ua)
-void kinetic_fp32(emd_system *s, int *np) {
+// complex64: partial sums of Re<psi|S psi>, S = sum over axes of the
+// stencil with the integer weights fd_num (S psi by the stage kernel with
+// diagonal 3 num_0, no potential and zero projector coefficients, into ua).
+// T = -S / (2 fd_den h^2); the returned factor turns the sum into <psi|T psi>.
+// Integer weights are exact in float, so S annihilates constants exactly;
+// float-rounded w_k = -c_k / (2 h^2) would shift T by a constant of order
+// 1e-6 Ha and bias the kinetic energy by that times the electron count.
+double kinetic_fp32(emd_system *s, int *np) {
+  const int order = 2 * s->o.half_order;
   emd_note_launches(1);
   k_fill4<<<(s->g.n3 + 255) / 256, 256, 0, s->st>>>(s->veff1d, s->g.n3,
-                                                     (float)s->o.w[0]);
+                                                     (float)(3.0 * fd_num(order, 0)));
   OrbLayout o = s->o;
   o.stage_variant = 0;
+  o.w[0] = 3.0 * fd_num(order, 0);
+  for (int k = 1; k <= o.half_order; ++k) o.w[k] = fd_num(order, k);
   StageArgs a;
   a.u_in = s->psi;
   a.psi0 = s->psi;
@@ -349,6 +367,7 @@ void kinetic_fp32(emd_system *s, int *np) {
   a.apply_only = 1;
   emd_launch_stage(o, a, s->st);
   emd_launch_cdot_re_c64(s->o, s->psi, s->ua, s->partials, np, s->st);
+  return -1.0 / (2.0 * fd_den(order) * s->g.h * s->g.h);
 }
 int reduce_max_veff(emd_system *s, double *out) {
   emd_note_launches(1);
@@ -1633,8 +1652,9 @@ int emd_get_energy(emd_system *s, emd_energy *out) {
   const int cur = s->cur;
   const double h3 = s->g.h * s->g.h * s->g.h;
   int np = 0;
+  double kin_scale = 1.0;
   if (s->o.prec == EMD_FP32_ORBITALS)
-    kinetic_fp32(s, &np);
+    kin_scale = kinetic_fp32(s, &np);
   else
     emd_launch_kinetic_partials(s->o, s->psi, s->partials, &np, s->st);
   emd_launch_sum(s->partials, np, s->scal + 0, s->st);
@@ -1668,7 +1688,7 @@ int emd_get_energy(emd_system *s, emd_energy *out) {
   r = read_err_flag(s);
   if (r) return r;
   const double occ = s->cfg.occ;
-  out->kin_e = occ * h3 * hs[0];
+  out->kin_e = occ * h3 * kin_scale * hs[0];
   out->nl = occ * s->sp.h_kb * hs[1];
   out->sr = s->n_atoms ? hs[3] : 0.0;
   const double self = s->n_atoms * s->sp.z * s->sp.z /

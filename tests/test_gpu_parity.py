@@ -302,8 +302,56 @@ def test_fp32_energy_terms_match_oracle(small):
     eg = g.energy()
     g.close()
     eo = O.energies(O.init_state(s32))
-    for k in ("kin_e", "nl", "es", "xc", "sr", "kin_ion", "total"):
-        assert abs(eg[k] - eo[k]) <= 2e-6 * max(abs(eo[k]), 1e-3), (k, eg[k], eo[k])
+    # es and xc come from rho summed in double-float (~1e-13), kin_e from a
+    # float stencil with exact integer weights, nl from float projector values
+    tol = {"kin_e": 3e-7, "nl": 2e-6, "es": 1e-10, "xc": 1e-10, "sr": 1e-10,
+           "kin_ion": 1e-12, "total": 1e-6}
+    for k, r in tol.items():
+        assert abs(eg[k] - eo[k]) <= r * max(abs(eo[k]), 1e-3), (k, eg[k], eo[k])
+
+
+def test_fp32_kinetic_energy_of_plane_waves():
+    """P1 closed form: a periodic plane wave e^{ik.r} is an eigenvector of
+    the FD kinetic operator with eigenvalue 1/2 sum_a -(c_0 + 2 sum_j c_j
+    cos(j k_a h)) / h^2, and plane waves are orthonormal on the grid, so an
+    orbital sum_m a_m e^{ik_m.r} / sqrt(L^3) has kinetic energy
+    sum_m |a_m|^2 lambda_m.  Orbitals are random superpositions of the modes
+    |m_a| <= 2 (generic values, so float rounding does not repeat from point
+    to point).  A complex64 kinetic operator whose weights do not annihilate
+    constants (float-rounded c_k / h^2 shift it by ~1.5e-6 Ha at order 8,
+    h = 0.25, i.e. ~1e-6 of this energy) fails the bound."""
+    n, h, order = 24, 0.25, 8
+    s = inputs.small_system(n=n, h=h, fd_order=order, n_atoms=2, seed=5, n_orb=4)
+    L = n * h
+    x = np.arange(n) * h
+    c = O.fd_coefficients(order)
+
+    def lam1(k):
+        return 0.5 * -(c[0] + 2 * sum(c[j] * np.cos(j * k * h)
+                                      for j in range(1, len(c)))) / h ** 2
+
+    modes = [(a, b, d) for a in range(-2, 3) for b in range(-2, 3) for d in range(-2, 3)]
+    rng = np.random.default_rng(17)
+    psi, exact = [], 0.0
+    for _ in range(s.n_orb):
+        amp = rng.normal(size=len(modes)) + 1j * rng.normal(size=len(modes))
+        amp /= np.linalg.norm(amp)
+        u = np.zeros((n, n, n), dtype=np.complex128)
+        for a_m, m in zip(amp, modes):
+            kv = [2 * np.pi * mi / L for mi in m]
+            u += a_m * np.exp(1j * (kv[0] * x[:, None, None] + kv[1] * x[None, :, None]
+                                    + kv[2] * x[None, None, :]))
+            exact += s.occ * abs(a_m) ** 2 * sum(lam1(k) for k in kv)
+        psi.append(u / np.sqrt(L ** 3))
+    s.psi = np.ascontiguousarray(np.array(psi))
+    g = emd.System(s, emd.EMD_FP64)
+    got64 = g.energy()["kin_e"]
+    g.close()
+    assert abs(got64 - exact) < 1e-12 * exact, (got64, exact)
+    g = emd.System(s, emd.EMD_FP32_ORBITALS)
+    got = g.energy()["kin_e"]
+    g.close()
+    assert abs(got - exact) < 2e-7 * exact, (got, exact)
 
 
 def test_complex64_host_io(small):
