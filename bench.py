@@ -41,9 +41,9 @@ UNIT = "updates/s"
 # u_out); the potential and projector lists are shared across an orbital
 # block and not counted.
 BYTES_PER_UPDATE = {"f32": 24, "f64": 48}
-# dram__bytes_read.sum + dram__bytes_write.sum of one Horner-stage launch
-# (profiles/horner_stage_c96.md), per precision, for the kernel as built;
-# None until a capture exists for it.
+# dram__bytes_read.sum + dram__bytes_write.sum of one Horner-stage launch on
+# the 96^3 workload (one ncu capture), per precision, for the kernel as
+# built; None until a capture exists for it.
 TRAFFIC_PER_LAUNCH = {"f32": 3.515e9, "f64": None}
 
 
@@ -358,6 +358,51 @@ def time_adjoint(emd, torch, n_steps=200, ckpt=20):
             "unit": UNIT}
 
 
+def time_large(emd, torch, steps, warmup):
+    """The 160^3 workload (512 atoms, 1024 orbitals, order 8, complex64,
+    mu 50, dt 0.354): input built with GEMMs on the device, uploaded as
+    complex64, then `steps` MD steps timed with CUDA events."""
+    from paper_0812_2801_gb300 import inputs
+    t0 = time.perf_counter()
+    s = inputs.large_c160(device="cuda")
+    build_s = time.perf_counter() - t0
+    h = emd.emd_init_system(emd.config_for(s, emd.EMD_FP32_ORBITALS))
+    emd.emd_set_ions(h, s.R, s.V)
+    emd.emd_set_orbitals_c64(h, s.psi)
+    n_orb = s.n_orb
+    s.psi = None                      # 33.5 GB of host memory
+    for _ in range(warmup):
+        emd.emd_propagate(h, 1, s.dt, s.mu)
+    e0 = emd.emd_get_energy(h)
+    torch.cuda.synchronize()
+    emd.emd_set_option(h, emd.EMD_OPT_PROFILE, 1)
+    emd.emd_kernel_stats(h, emd.EMD_KERNEL_HORNER)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record()
+    for _ in range(steps):
+        emd.emd_propagate(h, 1, s.dt, s.mu)
+    stop.record()
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(stop)
+    k_ms, k_n = emd.emd_kernel_stats(h, emd.EMD_KERNEL_HORNER)
+    emd.emd_set_option(h, emd.EMD_OPT_PROFILE, 0)
+    e1 = emd.emd_get_energy(h)
+    emd.emd_destroy(h)
+    n3 = s.n ** 3
+    upd = 8.0 * n_orb * n3 * steps
+    stage_s = k_ms * 1e-3 / max(1, k_n)
+    peak, _ = measured_peaks()
+    achieved = BYTES_PER_UPDATE["f32"] * n_orb * n3 / stage_s / 1e9
+    return {"workload": "large-512at-160^3: 512 atoms, 1024 orbitals, 160^3 at 0.3 bohr, "
+                        "order 8, mu 50, dt 0.354, complex64",
+            "value": upd / (ms * 1e-3), "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms / steps, "horner_stage_avg_ms": stage_s * 1e3,
+            "horner_stage_frac_hbm": achieved / peak,
+            "energy_change_rel": abs(e1["total"] - e0["total"]) / abs(e0["total"]),
+            "input_build_s": build_s}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -370,6 +415,8 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=12)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--large-steps", type=int, default=0,
+                    help="also time the 160^3 / 1024-orbital workload (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -412,6 +459,7 @@ def main():
 
     batched = None if args.no_batched else time_batched(emd, torch, args.batched_steps)
     adjoint = None if (args.no_adjoint or ws > 1) else time_adjoint(emd, torch)
+    large = time_large(emd, torch, args.large_steps, 2) if args.large_steps > 0 else None
 
     peak, peak_kind = measured_peaks()
     stage_avg_s = r32["stage_ms"] * 1e-3 / max(1, r32["stage_launches"])
@@ -446,6 +494,7 @@ def main():
                         "propagate 1 MD step, get_orbitals_c64 + get_forces + get_energy"},
         "batched": batched,
         "adjoint": adjoint,
+        "large": large,
         "gpu_launches": r32["launches"],
         "clocks": clk.summary(),
         "energy_total": r32["energy"]["total"],

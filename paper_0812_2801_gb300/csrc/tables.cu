@@ -237,12 +237,21 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
       }
       if (in_p) {
         if (F32) {
-          const float pv = (float)sp.c_p * expf(-d2f * (float)sp.inv_2rc2);
+          // displacement and d^2 in FP64, then rounded once: the float atom
+          // coordinate (float)(R + image L) is off by up to half an ulp of L,
+          // the same shift for every point of the sphere, and the projector
+          // force sum_r p d psi cancels strongly, so that shift would show up
+          // at ~1e-4 of the forces
+          const double ex = emd_disp(x, h, Rw[3 * J + 0], img % 3 - 1, L);
+          const double ey = emd_disp(y, h, Rw[3 * J + 1], (img / 3) % 3 - 1, L);
+          const double ez = emd_disp(z, h, Rw[3 * J + 2], img / 9 - 1, L);
+          const float pv =
+              (float)sp.c_p * expf(-(float)(emd_norm2(ex, ey, ez) * sp.inv_2rc2));
           const float w = pv * (float)sp.inv_rc2;
           psumf += pv;
-          pdx += w * dxf;
-          pdy += w * dyf;
-          pdz += w * dzf;
+          pdx += w * (float)ex;
+          pdy += w * (float)ey;
+          pdz += w * (float)ez;
         } else {
           psum += sp.c_p * exp(-d2 * sp.inv_2rc2);
         }

@@ -24,7 +24,9 @@ and, for the complex64 form against the complex128 form:
 * ``state_errors``    at those samples, per result of the complex64 system
                       against the complex128 one at the same state: forces,
                       density (max |drho| / max rho) and each energy term
-                      (|dE_term| / |E_term|)
+                      (|dE_term| / |E_term|), split into the part due to
+                      rounding the orbitals to complex64 and the part due to
+                      the complex64 kernels
 
 Everything runs through the C ABI; this module only schedules calls and
 reduces the returned host arrays.
@@ -58,17 +60,26 @@ def _drift(E: np.ndarray, steps: np.ndarray) -> dict:
             "slope_rel_1000": abs(slope) * 1000.0 / e0}
 
 
-def _state_errors(step: int, s32, s64) -> dict:
-    """Errors of the complex64 system ``s32`` against ``s64`` at one state."""
-    e32, e64 = s32.energy(), s64.energy()
-    rho32 = s32.state(want_psi=False, want_rho=True)[3]
-    rho64 = s64.state(want_psi=False, want_rho=True)[3]
-    out = {"step": step,
-           "forces": _rel_force_err(s32.forces(), s64.forces()),
-           "rho": float(np.max(np.abs(rho32 - rho64)) / np.max(np.abs(rho64)))}
-    for k in ("kin_e", "nl", "es", "xc", "sr", "ks", "total"):
-        out[k] = abs(e32[k] - e64[k]) / max(abs(e64[k]), 1e-300)
+def _errors(a, b) -> dict:
+    """Relative errors of system ``a`` against system ``b`` (same state)."""
+    ea, eb = a.energy(), b.energy()
+    rho_a = a.state(want_psi=False, want_rho=True)[3]
+    rho_b = b.state(want_psi=False, want_rho=True)[3]
+    out = {"forces": _rel_force_err(a.forces(), b.forces()),
+           "rho": float(np.max(np.abs(rho_a - rho_b)) / np.max(np.abs(rho_b)))}
+    for k in ("kin_e", "nl", "es", "xc", "ks", "total"):
+        out[k] = abs(ea[k] - eb[k]) / max(abs(eb[k]), 1e-300)
     return out
+
+
+def _state_errors(step: int, s32, s64r, s64) -> dict:
+    """Errors at one state of the complex128 run: ``s32`` (complex64 system
+    loaded with it) and ``s64r`` (complex128 system loaded with the same
+    orbitals rounded to complex64) against ``s64``.  ``all`` is the complex64
+    form's error; ``rounding`` the part due to storing the orbitals in
+    complex64 at all; ``eval`` the part due to the complex64 kernels."""
+    return {"step": step, "all": _errors(s32, s64), "rounding": _errors(s64r, s64),
+            "eval": _errors(s32, s64r)}
 
 
 def compare(sysin, n_steps: int, every: int = 10, state_every: int = 100) -> dict:
@@ -79,12 +90,14 @@ def compare(sysin, n_steps: int, every: int = 10, state_every: int = 100) -> dic
     s64 = emd.System(sysin, emd.EMD_FP64)
     s32 = emd.System(sysin, emd.EMD_FP32_ORBITALS)
     probe = emd.System(sysin, emd.EMD_FP32_ORBITALS)
+    probe64 = emd.System(sysin, emd.EMD_FP64)
+    emd.emd_set_orbitals_c64(probe64.handle, sysin.psi.astype(np.complex64))
     t = [0]
     E64 = [s64.energy()["total"]]
     E32 = [s32.energy()["total"]]
     f_traj = [_rel_force_err(s32.forces(), s64.forces())]
     f_state = [(0, _rel_force_err(probe.forces(), s64.forces()))]
-    state_errors = [_state_errors(0, probe, s64)]
+    state_errors = [_state_errors(0, probe, probe64, s64)]
     n_elec = [s32.energy()["n_elec"]]
     ms64 = ms32 = 0.0
     done = 0
@@ -112,10 +125,12 @@ def compare(sysin, n_steps: int, every: int = 10, state_every: int = 100) -> dic
             R, V, psi, _ = s64.state(want_psi=True, want_rho=False)
             emd.emd_set_ions(probe.handle, R, V)
             emd.emd_set_orbitals(probe.handle, psi)
+            emd.emd_set_ions(probe64.handle, R, V)
+            emd.emd_set_orbitals_c64(probe64.handle, psi.astype(np.complex64))
             f_state.append((done, _rel_force_err(probe.forces(), F64)))
-            state_errors.append(_state_errors(done, probe, s64))
+            state_errors.append(_state_errors(done, probe, probe64, s64))
             del psi
-    for s in (s64, s32, probe):
+    for s in (s64, s32, probe, probe64):
         s.close()
     steps = np.asarray(t)
     E64, E32 = np.asarray(E64), np.asarray(E32)
