@@ -138,20 +138,27 @@ int emd_init_system(const emd_config *cfg, emd_system **out);
 /* Set ions: R[n_atoms][3], V[n_atoms][3] (host, float64; x, y, z).
  * n_atoms must equal cfg.n_atoms.  Positions may lie outside the box; they
  * are folded with X - L floor(X/L) wherever a grid support is built.
- * Recomputes the ionic potential; if orbitals are set, also rho, v_Hxc and
- * F(0) and restarts the v_Hxc history. */
+ * Recomputes the ionic potential.  If orbitals are set, rho, v_Hxc and F(0)
+ * are recomputed and the v_Hxc history restarted by the next call that
+ * reads them (propagate, get_forces, get_energy, get_state, get_potentials,
+ * get_projections, apply_hamiltonian), so set_ions followed by set_orbitals
+ * pays for one recomputation; errors of that recomputation are returned by
+ * that call. */
 int emd_set_ions(emd_system *s, int n_atoms, const double *R, const double *V);
 
 /* Set orbitals: psi is complex128 interleaved (re, im), canonical layout
  * [n_orb][N][N][N] (host).  Orbitals should be orthonormal under
- * <a|b> = h^3 sum conj(a) b; they are not modified.  Recomputes rho, v_Hxc,
- * F(0) (if ions are set) and restarts the v_Hxc history (Sec. 2,
- * eq. Ehr_ic: initial condition). */
+ * <a|b> = h^3 sum conj(a) b; they are not modified.  If ions are set, rho,
+ * v_Hxc and F(0) are recomputed and the v_Hxc history restarted (Sec. 2,
+ * eq. Ehr_ic: initial condition) by the next call that reads them, as for
+ * emd_set_ions.  Returns after the host array has been read. */
 int emd_set_orbitals(emd_system *s, const double *psi);
 
 /* The same with complex64 host arrays (float32 interleaved (re, im), same
  * canonical layout), for callers that keep orbitals in single precision:
- * half the bytes over the host link.  For EMD_FP32_ORBITALS systems the
+ * half the bytes over the host link, copied block by block on a second
+ * stream so that the link and the repacking overlap (page-locked psi lets
+ * the copies run asynchronously).  For EMD_FP32_ORBITALS systems the
  * stored orbitals are identical to those set from the complex128 values
  * rounded to complex64.  No counterpart in the paper (host I/O). */
 int emd_set_orbitals_c64(emd_system *s, const float *psi);

@@ -110,6 +110,11 @@ struct emd_system {
   size_t orb_bytes = 0;
   void *psi = nullptr, *ua = nullptr, *ub = nullptr;
   double2 *stage_buf = nullptr;   // canonical staging for one orbital block
+  // complex64 host I/O: copies on their own stream (created on first use),
+  // alternating between the two halves of stage_buf; events: start, half
+  // k filled (1 + k), half k free again (3 + k)
+  cudaStream_t cst = nullptr;
+  cudaEvent_t cev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double *veff1 = nullptr, *veff2 = nullptr;
   float *veff1f = nullptr, *veff2f = nullptr;
   float4 *veff1d = nullptr, *veff2d = nullptr;   // complex64: (w_0 + v_eff) x4
@@ -131,6 +136,9 @@ struct emd_system {
   double *scal = nullptr;
   int *err = nullptr;
   int ions_set = 0, orbs_set = 0;
+  // set by emd_set_ions / emd_set_orbitals*: rho, v_Hxc (history restarted),
+  // projections and F(0) are recomputed by the next call that reads them
+  int needs_restart = 0;
   int frozen_ions = 0, profile = 0, check_stable = 1, proj_atom_major = 1;
   double2 *proj_part = nullptr;   // point-major projection partials
   void *hc_zero = nullptr;          // complex64: zero projector coefficients
@@ -299,6 +307,14 @@ int restart_dynamics(emd_system *s) {
   int r = launch_check("restart_dynamics");
   if (r) return r;
   return reduce_max_veff(s, &s->v_max);
+}
+
+// The derived state of a set_ions / set_orbitals, computed once before the
+// first call that reads it (two setters in a row pay for one restart).
+int ensure_state(emd_system *s) {
+  if (!s->needs_restart) return EMD_OK;
+  s->needs_restart = 0;
+  return restart_dynamics(s);
 }
 
 double kinetic_lambda_max(int order) {
@@ -601,7 +617,10 @@ int emd_set_ions(emd_system *s, int n_atoms, const double *R, const double *V) {
   if (r) return r;
   negate_grid(t.v_loc, s->g.n3, s->st);
   s->ions_set = 1;
-  if (s->orbs_set) return restart_dynamics(s);
+  if (s->orbs_set) {
+    s->needs_restart = 1;
+    s->c_valid = 0;
+  }
   CK(cudaStreamSynchronize(s->st));
   return launch_check("emd_set_ions");
 }
@@ -637,17 +656,38 @@ static int download_orbitals(emd_system *s, const void *src, int n_vec,
   return launch_check("download_orbitals");
 }
 
-// complex64 host arrays: the same staging, half the bytes over the link
+static int copy_pipe(emd_system *s) {
+  if (s->cst) return EMD_OK;
+  if (cudaStreamCreateWithFlags(&s->cst, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(EMD_ECUDA, "copy stream creation failed");
+  for (cudaEvent_t &e : s->cev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return fail(EMD_ECUDA, "event creation failed");
+  return EMD_OK;
+}
+
+// complex64 host arrays: one orbital block per half of stage_buf; the copy
+// of block b + 1 (copy stream) overlaps the pack of block b (s->st)
 static int upload_orbitals_c64(emd_system *s, const float *psi, void *dst) {
+  int r = copy_pipe(s);
+  if (r) return r;
   const size_t n3 = s->g.n3;
   const int n_vec = s->o.n_orb;
+  float2 *half[2] = {(float2 *)s->stage_buf, (float2 *)s->stage_buf + (size_t)s->o.bo * n3};
+  CK(cudaEventRecord(s->cev[0], s->st));
+  CK(cudaStreamWaitEvent(s->cst, s->cev[0], 0));
   for (int b = 0; b * s->o.bo < n_vec; ++b) {
+    const int k = b & 1;
     const int nv = std::min(s->o.bo, n_vec - b * s->o.bo);
-    CK(cudaMemcpyAsync(s->stage_buf, psi + 2 * (size_t)b * s->o.bo * n3,
-                       (size_t)nv * n3 * 8, cudaMemcpyHostToDevice, s->st));
+    if (b >= 2) CK(cudaStreamWaitEvent(s->cst, s->cev[3 + k], 0));
+    CK(cudaMemcpyAsync(half[k], psi + 2 * (size_t)b * s->o.bo * n3,
+                       (size_t)nv * n3 * 8, cudaMemcpyHostToDevice, s->cst));
+    CK(cudaEventRecord(s->cev[1 + k], s->cst));
+    CK(cudaStreamWaitEvent(s->st, s->cev[1 + k], 0));
     char *d = (char *)dst + (size_t)b * n3 * s->o.bo *
                                 (s->o.prec == EMD_FP64 ? 16 : 8);
-    emd_launch_pack_c64(s->o, (const float2 *)s->stage_buf, d, nv, s->st);
+    emd_launch_pack_c64(s->o, half[k], d, nv, s->st);
+    CK(cudaEventRecord(s->cev[3 + k], s->st));
   }
   return launch_check("upload_orbitals_c64");
 }
@@ -659,7 +699,8 @@ int emd_set_orbitals_c64(emd_system *s, const float *psi) {
   int r = upload_orbitals_c64(s, psi, s->psi);
   if (r) return r;
   s->orbs_set = 1;
-  if (s->ions_set) return restart_dynamics(s);
+  s->c_valid = 0;
+  if (s->ions_set) s->needs_restart = 1;
   CK(cudaStreamSynchronize(s->st));
   return EMD_OK;
 }
@@ -669,15 +710,25 @@ int emd_get_orbitals_c64(emd_system *s, float *psi) {
   if (!s || !psi) return fail(EMD_EINVAL, "NULL argument");
   int r = read_err_flag(s);
   if (r) return r;
+  r = copy_pipe(s);
+  if (r) return r;
   const size_t n3 = s->g.n3;
+  float2 *half[2] = {(float2 *)s->stage_buf, (float2 *)s->stage_buf + (size_t)s->o.bo * n3};
+  // the unpack of block b + 1 (s->st) overlaps the copy of block b
   for (int b = 0; b * s->o.bo < s->o.n_orb; ++b) {
+    const int k = b & 1;
     const int nv = std::min(s->o.bo, s->o.n_orb - b * s->o.bo);
+    if (b >= 2) CK(cudaStreamWaitEvent(s->st, s->cev[3 + k], 0));
     const char *d = (const char *)s->psi + (size_t)b * n3 * s->o.bo *
                                                (s->o.prec == EMD_FP64 ? 16 : 8);
-    emd_launch_unpack_c64(s->o, d, (float2 *)s->stage_buf, nv, s->st);
-    CK(cudaMemcpyAsync(psi + 2 * (size_t)b * s->o.bo * n3, s->stage_buf,
-                       (size_t)nv * n3 * 8, cudaMemcpyDeviceToHost, s->st));
+    emd_launch_unpack_c64(s->o, d, half[k], nv, s->st);
+    CK(cudaEventRecord(s->cev[1 + k], s->st));
+    CK(cudaStreamWaitEvent(s->cst, s->cev[1 + k], 0));
+    CK(cudaMemcpyAsync(psi + 2 * (size_t)b * s->o.bo * n3, half[k],
+                       (size_t)nv * n3 * 8, cudaMemcpyDeviceToHost, s->cst));
+    CK(cudaEventRecord(s->cev[3 + k], s->cst));
   }
+  CK(cudaStreamSynchronize(s->cst));
   CK(cudaStreamSynchronize(s->st));
   return launch_check("emd_get_orbitals_c64");
 }
@@ -689,7 +740,8 @@ int emd_set_orbitals(emd_system *s, const double *psi) {
   int r = upload_orbitals(s, psi, s->o.n_orb, s->psi);
   if (r) return r;
   s->orbs_set = 1;
-  if (s->ions_set) return restart_dynamics(s);
+  s->c_valid = 0;
+  if (s->ions_set) s->needs_restart = 1;
   CK(cudaStreamSynchronize(s->st));
   return EMD_OK;
 }
@@ -726,6 +778,8 @@ int check_propagate(emd_system *s, double dt, double mu) {
     return fail(EMD_ESTATE, "set ions and orbitals before propagating");
   if (!(dt > 0.0) || !(mu > 0.0) || !std::isfinite(dt) || !std::isfinite(mu))
     return fail(EMD_EINVAL, "dt and mu must be finite and > 0");
+  int r = ensure_state(s);   // v_max for the bound below
+  if (r) return r;
   const double tau = 0.5 * (dt / mu);
   if (s->check_stable) {
     const double lam = 1.5 * kinetic_lambda_max(s->cfg.fd_order) / (s->g.h * s->g.h) +
@@ -1635,7 +1689,9 @@ int emd_propagate_adjoint(emd_system *s, int n_steps, double dt, double mu,
 int emd_get_forces(emd_system *s, double *F) {
   g_err.clear();
   if (!s || (!F && s->n_atoms)) return fail(EMD_EINVAL, "NULL argument");
-  int r = read_err_flag(s);
+  int r = ensure_state(s);
+  if (r) return r;
+  r = read_err_flag(s);
   if (r) return r;
   if (s->n_atoms) {
     CK(cudaMemcpyAsync(F, s->F, 3 * s->n_atoms * 8, cudaMemcpyDeviceToHost, s->st));
@@ -1649,6 +1705,8 @@ int emd_get_energy(emd_system *s, emd_energy *out) {
   if (!s || !out) return fail(EMD_EINVAL, "NULL argument");
   if (!s->ions_set || !s->orbs_set)
     return fail(EMD_ESTATE, "set ions and orbitals first");
+  int r0 = ensure_state(s);
+  if (r0) return r0;
   const int cur = s->cur;
   const double h3 = s->g.h * s->g.h * s->g.h;
   int np = 0;
@@ -1711,7 +1769,9 @@ int emd_get_energy(emd_system *s, emd_energy *out) {
 int emd_get_state(emd_system *s, double *R, double *V, double *psi, double *rho) {
   g_err.clear();
   if (!s) return fail(EMD_EINVAL, "NULL system");
-  int r = read_err_flag(s);
+  int r = ensure_state(s);
+  if (r) return r;
+  r = read_err_flag(s);
   if (r) return r;
   if (R && s->n_atoms)
     CK(cudaMemcpyAsync(R, s->ts[s->cur].R, 3 * s->n_atoms * 8,
@@ -1732,6 +1792,8 @@ int emd_get_potentials(emd_system *s, double *v_loc, double *v_h, double *v_xc,
                        double *g_ion) {
   g_err.clear();
   if (!s) return fail(EMD_EINVAL, "NULL system");
+  int r = ensure_state(s);
+  if (r) return r;
   const size_t b = (size_t)s->g.n3 * 8;
   if (v_loc) CK(cudaMemcpyAsync(v_loc, s->ts[s->cur].v_loc, b, cudaMemcpyDeviceToHost, s->st));
   if (v_h) CK(cudaMemcpyAsync(v_h, s->v_h, b, cudaMemcpyDeviceToHost, s->st));
@@ -1745,6 +1807,8 @@ int emd_get_projections(emd_system *s, double *c) {
   g_err.clear();
   if (!s || !c) return fail(EMD_EINVAL, "NULL argument");
   if (!s->orbs_set || !s->ions_set) return fail(EMD_ESTATE, "set ions and orbitals first");
+  int r = ensure_state(s);
+  if (r) return r;
   if (!s->c_valid) {
     project(s, s->psi, s->cur);
     s->c_valid = 1;
@@ -1763,8 +1827,10 @@ int emd_apply_hamiltonian(emd_system *s, int n_vec, const double *psi,
   if (n_vec < 1 || n_vec > s->o.n_orb)
     return fail(EMD_EINVAL, "n_vec must be in [1, n_orb]");
   if (!s->ions_set || !s->orbs_set) return fail(EMD_ESTATE, "set ions and orbitals first");
+  int r = ensure_state(s);
+  if (r) return r;
   CK(cudaMemsetAsync(s->ua, 0, s->orb_bytes, s->st));
-  int r = upload_orbitals(s, psi, n_vec, s->ua);
+  r = upload_orbitals(s, psi, n_vec, s->ua);
   if (r) return r;
   OrbLayout o = s->o;
   o.n_blk = (n_vec + o.bo - 1) / o.bo;
@@ -1827,6 +1893,12 @@ void emd_destroy(emd_system *s) {
   if (!s) return;
   if (s->st) cudaStreamSynchronize(s->st);
   else cudaDeviceSynchronize();
+  if (s->cst) {
+    cudaStreamSynchronize(s->cst);
+    cudaStreamDestroy(s->cst);
+  }
+  for (cudaEvent_t e : s->cev)
+    if (e) cudaEventDestroy(e);
   for (void *p : s->allocs) cudaFree(p);
   if (s->adj) {
     for (void *p : s->adj->mem) cudaFree(p);

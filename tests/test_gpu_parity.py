@@ -384,6 +384,64 @@ def test_fp32_kinetic_energy_of_plane_waves():
     assert abs(got - exact) < 2e-7 * exact, (got, exact)
 
 
+def test_setters_in_any_order_give_the_same_state():
+    """set_ions / set_orbitals mark the derived state (rho, v_Hxc, c, F) for
+    recomputation at the next reading call: the order of the setters, a
+    repeated set_ions with other positions in between, and reading calls in
+    between give bitwise the same forces, energy, density and trajectory."""
+    s = inputs.small_system(n=20, h=0.3, fd_order=6, n_atoms=3, seed=5, n_orb=6)
+    R2 = s.R + 0.37
+
+    def run(order):
+        h = emd.emd_init_system(emd.config_for(s, emd.EMD_FP32_ORBITALS))
+        for op in order:
+            if op == "ions":
+                emd.emd_set_ions(h, s.R, s.V)
+            elif op == "ions2":
+                emd.emd_set_ions(h, R2, s.V)
+            elif op == "orbs":
+                emd.emd_set_orbitals(h, s.psi)
+            elif op == "energy":
+                emd.emd_get_energy(h)
+        F = emd.emd_get_forces(h, s.n_atoms)
+        E = emd.emd_get_energy(h)
+        emd.emd_propagate(h, 2, 0.05, 1.0)
+        R, V, psi, rho = emd.emd_get_state(h, s.n_atoms, s.n_orb, s.n)
+        emd.emd_destroy(h)
+        return F, E, R, psi, rho
+
+    ref = run(["ions", "orbs"])
+    for order in (["orbs", "ions"], ["ions2", "orbs", "ions"],
+                  ["ions", "orbs", "energy", "ions2", "ions"]):
+        got = run(order)
+        assert np.array_equal(got[0], ref[0]), order
+        assert got[1] == ref[1], order
+        for a, b in zip(got[2:], ref[2:]):
+            assert np.array_equal(a, b), order
+
+
+def test_complex64_host_io_three_blocks():
+    """Three orbital blocks (10 orbitals, bo = 4): the pipelined complex64
+    upload and download reuse each half of the staging buffer; round trip
+    and the complex128 upload of the same values agree bitwise."""
+    s = inputs.small_system(n=20, h=0.3, fd_order=6, n_atoms=5, seed=9)
+    assert s.n_orb == 10
+    psi64 = s.psi.astype(np.complex64)
+    a = emd.emd_init_system(emd.config_for(s, emd.EMD_FP32_ORBITALS, block_orbitals=4))
+    b = emd.emd_init_system(emd.config_for(s, emd.EMD_FP32_ORBITALS, block_orbitals=4))
+    for h in (a, b):
+        emd.emd_set_ions(h, s.R, s.V)
+    emd.emd_set_orbitals_c64(a, psi64)
+    emd.emd_set_orbitals(b, psi64.astype(np.complex128))
+    assert np.array_equal(emd.emd_get_orbitals_c64(a, s.n_orb, s.n), psi64)
+    emd.emd_propagate(a, 2, 0.04, 1.0)
+    emd.emd_propagate(b, 2, 0.04, 1.0)
+    assert np.array_equal(emd.emd_get_orbitals_c64(a, s.n_orb, s.n),
+                          emd.emd_get_orbitals_c64(b, s.n_orb, s.n))
+    emd.emd_destroy(a)
+    emd.emd_destroy(b)
+
+
 def test_complex64_host_io(small):
     """emd_set_orbitals_c64 / emd_get_orbitals_c64: a complex64 system set
     from complex64 host values holds exactly the complex128 path's rounded
