@@ -49,6 +49,7 @@ extern "C" {
 #define EMD_ESTATE    5   /* call out of order (e.g. propagate before
                              orbitals and ions are set)                   */
 #define EMD_ETABLE    6   /* a per-point or per-tile atom list overflowed */
+#define EMD_ENOTCONV  7   /* emd_ground_state: tolerance not reached        */
 
 /* orbital storage precision */
 #define EMD_FP64           0  /* complex128 orbitals, FP64 stencil          */
@@ -291,6 +292,45 @@ void emd_batch_destroy(emd_batch *b);
  * capture.  Errors: EMD_EINVAL, EMD_ECUDA. */
 int emd_poisson_static(int n, double h, const double *charge, double *v,
                        void *cuda_stream);
+
+/* Kohn-Sham ground state at the current ions (Sec. 4.1, eqs. EoM_BO_a and
+ * EoM_BO_b): orthonormal orbitals that satisfy H_KS[rho] phi_A =
+ * sum_B Lambda_AB phi_B with rho built from them and fill the n_orb lowest
+ * eigenstates of that H, i.e. phi_gs(R) of eq. EoM_BO_2, the start on the
+ * BO surface of the paper's runs.  The paper gives no algorithm; here each
+ * self-consistency iteration
+ *   1. filters the orbitals with the Chebyshev polynomial of degree
+ *      `degree` (1..64) of H[rho_in] on [largest Ritz value, spectral upper
+ *      bound] (the bound of emd_propagate's stability check), scaled to 1
+ *      at the lowest Ritz value;
+ *   2. replaces them by the Rayleigh-Ritz vectors of the filtered set
+ *      (generalized eigenproblem of h^3 X^H H X against h^3 X^H X);
+ *   3. forms rho_out and mixes rho_in with it (Anderson over the last six
+ *      iterations, step `mix` in (0, 1]);
+ * and stops when h^3 sum |rho_out - rho_in| < tol * n_electrons or after
+ * max_scf iterations.  The current orbitals are the starting guess (an
+ * orthonormal set of atom-centred functions will do).  On return the
+ * orbitals are the last Ritz vectors in ascending order, eigenvalues (if not
+ * NULL, host, n_orb doubles) their Ritz values, info (if not NULL) the
+ * iteration count, final residual, occ * sum of the Ritz values and the
+ * gap to the first unoccupied Ritz value (the subspace carries
+ * max(4, n_orb/10) buffer states above the occupied ones); rho,
+ * v_Hxc and F are recomputed from the new orbitals by the next call that
+ * reads them (as after emd_set_orbitals).  The subspace products use cuBLAS
+ * (in the orbital precision) and the n_orb x n_orb eigenproblem cuSOLVER (in
+ * FP64).  Errors: EMD_EINVAL, EMD_ESTATE (ions or orbitals not set),
+ * EMD_ENOTCONV (tolerance not reached; the orbitals are the last iterate),
+ * EMD_ECUDA (including a subspace that lost rank). */
+typedef struct {
+  int iterations;
+  double residual;       /* h^3 sum |rho_out - rho_in| / n_electrons */
+  double band_energy;    /* occ * sum of the Ritz values              */
+  double gap;            /* lowest unoccupied minus highest occupied
+                            Ritz value (from the buffer states); the
+                            integer occupations need it > 0          */
+} emd_gs_info;
+int emd_ground_state(emd_system *s, int max_scf, double tol, int degree,
+                     double mix, double *eigenvalues, emd_gs_info *info);
 
 /* Release all device memory and the handle.  NULL is accepted. */
 void emd_destroy(emd_system *s);

@@ -17,7 +17,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libemd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["emd_api.cu", "hpsi.cu", "tables.cu", "poisson.cu", "adjoint.cu", "project_pm.cu"]
+SOURCES = ["emd_api.cu", "hpsi.cu", "tables.cu", "poisson.cu", "adjoint.cu", "project_pm.cu",
+           "groundstate.cu"]
 
 
 def nvcc() -> str:
@@ -62,7 +63,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         with concurrent.futures.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
             list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
-        run([nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart"])
+        run([nvcc()] + ARCH + ["-shared", "-o", LIB] + objs +
+            ["-lcudart", "-lcublas", "-lcusolver"])
     return LIB
 
 

@@ -18,6 +18,8 @@
 #include <string>
 #include <utility>
 #include <vector>
+#include <cublas_v2.h>
+#include <cusolverDn.h>
 #include "emd_internal.cuh"
 
 namespace {
@@ -148,6 +150,7 @@ struct emd_system {
   long long prof_launches = 0;
   std::vector<void *> allocs;
   struct Adjoint *adj = nullptr;
+  struct GroundStateWork *gsw = nullptr;
 };
 
 namespace {
@@ -1862,6 +1865,401 @@ int emd_apply_hamiltonian(emd_system *s, int n_vec, const double *psi,
   return read_err_flag(s);
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Ground state at fixed ions (Sec. 4.1, eqs. EoM_BO_a, EoM_BO_b): Chebyshev-
+// filtered subspace iteration with Rayleigh-Ritz and Anderson mixing of rho.
+// ---------------------------------------------------------------------------
+
+struct GroundStateWork {
+  static constexpr int kHist = 6;          // Anderson history
+  OrbLayout og;                            // the subspace: n_orb + buffer states
+  int n_occ = 0;
+  void *A = nullptr, *B = nullptr, *C = nullptr;   // three sets in layout og
+  double2 *c = nullptr;                    // projections of the subspace
+  void *hc = nullptr;
+  double2 *part = nullptr;                 // per-tile projection partials
+  cublasHandle_t blas = nullptr;
+  cusolverDnHandle_t solver = nullptr;
+  void *S = nullptr, *Hs = nullptr, *V = nullptr;   // m x m, orbital precision
+  double2 *Sz = nullptr, *Hz = nullptr;             // m x m, FP64
+  double *w = nullptr;                              // Ritz values
+  double2 *work = nullptr;
+  int lwork = 0;
+  int *dinfo = nullptr;
+  double *rho_in = nullptr, *rho_out = nullptr;
+  double *hr[kHist] = {}, *hf[kHist] = {};          // rho_in and F = rho_out - rho_in
+  std::vector<void *> mem;
+};
+
+namespace {
+
+void gs_release(GroundStateWork *g) {
+  if (!g) return;
+  if (g->blas) cublasDestroy(g->blas);
+  if (g->solver) cusolverDnDestroy(g->solver);
+  for (void *p : g->mem) cudaFree(p);
+  delete g;
+}
+
+// Buffer states above the occupied ones: the Chebyshev filter damps the
+// spectrum above the largest Ritz value of the whole subspace, so the
+// occupied edge needs states above it (otherwise an occupied state missing
+// from the start rotates in only slowly).
+int gs_buffer_states(int n_orb) { return std::max(4, (n_orb + 9) / 10); }
+
+int gs_setup(emd_system *s) {
+  if (s->gsw) return EMD_OK;
+  GroundStateWork *g = new GroundStateWork();
+  g->n_occ = s->o.n_orb;
+  g->og = s->o;
+  g->og.n_orb = s->o.n_orb + gs_buffer_states(s->o.n_orb);
+  g->og.n_blk = (g->og.n_orb + g->og.bo - 1) / g->og.bo;
+  g->og.n_orb_pad = g->og.n_blk * g->og.bo;
+  const int m = g->og.n_orb;
+  const size_t n3 = s->g.n3;
+  const size_t esz = s->o.prec == EMD_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t set_bytes = (size_t)g->og.n_blk * n3 * g->og.bo * esz;
+  const int nt = (s->g.n + EMD_TILE - 1) / EMD_TILE;
+  const size_t ntiles = (size_t)nt * nt * nt;
+  const size_t na = std::max(1, s->n_atoms);
+  auto A = [&](void **p, size_t b) {
+    if (cudaMalloc(p, b) != cudaSuccess) return false;
+    g->mem.push_back(*p);
+    return true;
+  };
+  bool ok = cublasCreate(&g->blas) == CUBLAS_STATUS_SUCCESS &&
+            cusolverDnCreate(&g->solver) == CUSOLVER_STATUS_SUCCESS;
+  ok = ok && A(&g->A, set_bytes) && A(&g->B, set_bytes) && A(&g->C, set_bytes) &&
+       A((void **)&g->c, na * g->og.n_orb_pad * sizeof(double2)) &&
+       A(&g->hc, na * g->og.n_orb_pad * esz) &&
+       A((void **)&g->part, ntiles * EMD_TILE_ATOM_MAX * g->og.n_orb_pad * sizeof(double2)) &&
+       A(&g->S, (size_t)m * m * esz) && A(&g->Hs, (size_t)m * m * esz) &&
+       A(&g->V, (size_t)m * m * esz) && A((void **)&g->Sz, (size_t)m * m * 16) &&
+       A((void **)&g->Hz, (size_t)m * m * 16) && A((void **)&g->w, (size_t)m * 8) &&
+       A((void **)&g->dinfo, sizeof(int)) && A((void **)&g->rho_in, n3 * 8) &&
+       A((void **)&g->rho_out, n3 * 8);
+  for (int k = 0; ok && k < GroundStateWork::kHist; ++k)
+    ok = A((void **)&g->hr[k], n3 * 8) && A((void **)&g->hf[k], n3 * 8);
+  if (ok)
+    ok = cusolverDnZhegvd_bufferSize(g->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                                     CUBLAS_FILL_MODE_LOWER, m, (cuDoubleComplex *)g->Hz, m,
+                                     (cuDoubleComplex *)g->Sz, m, g->w,
+                                     &g->lwork) == CUSOLVER_STATUS_SUCCESS;
+  ok = ok && A((void **)&g->work, (size_t)std::max(1, g->lwork) * 16);
+  if (!ok) {
+    gs_release(g);
+    return fail(EMD_ENOMEM, "ground-state workspace: allocation or library set-up failed");
+  }
+  s->gsw = g;
+  return EMD_OK;
+}
+
+// u_out = H u_in over the subspace (layout og), H with the potential in
+// veff1 (and its complex64 forms) and the projectors of the current set
+void gs_apply(emd_system *s, const void *u_in, void *u_out) {
+  GroundStateWork *g = s->gsw;
+  const double h3 = s->g.h * s->g.h * s->g.h;
+  if (s->o.prec == EMD_FP32_ORBITALS)
+    emd_launch_project_tile(g->og, s->ts[s->cur], s->n_atoms, u_in, h3, s->sp.h_kb, g->c,
+                            g->hc, g->part, s->st);
+  else
+    emd_launch_project(g->og, s->ts[s->cur], s->n_atoms, u_in, h3, s->sp.h_kb, g->c, g->hc,
+                       s->st);
+  StageArgs a;
+  a.u_in = u_in;
+  a.psi0 = u_in;
+  a.u_out = u_out;
+  a.v_eff = s->o.prec == EMD_FP64 ? (const void *)s->veff1 : (const void *)s->veff1f;
+  if (s->o.prec != EMD_FP64) a.v_diag = s->veff1d;
+  a.tab = &s->ts[s->cur];
+  a.hc = g->hc;
+  a.a = 0.0;
+  a.apply_only = 1;
+  emd_launch_stage(g->og, a, s->st);
+}
+
+// veff1 = v_loc + v_H[rho] + v_xc[rho]; hist[0] holds v_H + v_xc
+void gs_potential(emd_system *s, const double *rho) {
+  emd_launch_poisson(s->g, rho, s->v_h, s->fft_a, s->fft_b, s->st);
+  emd_launch_lda(s->g.n3, rho, s->v_h, s->eps_xc, s->v_xc, s->hist[0], s->st);
+  emd_launch_veff(s->g, s->ts[s->cur].v_loc, s->hist, 1, 0.0, s->veff1, s->veff1f, s->st,
+                  s->o.prec == EMD_FP64 ? nullptr : s->veff1d, s->o.w[0]);
+}
+
+void gs_pack(const OrbLayout &o, const void *canon, void *u, int n_vec, cudaStream_t st) {
+  if (o.prec == EMD_FP64) emd_launch_pack(o, (const double2 *)canon, u, n_vec, st);
+  else emd_launch_pack_c64(o, (const float2 *)canon, u, n_vec, st);
+}
+
+void gs_unpack(const OrbLayout &o, const void *u, void *canon, int n_vec, cudaStream_t st) {
+  if (o.prec == EMD_FP64) emd_launch_unpack(o, u, (double2 *)canon, n_vec, st);
+  else emd_launch_unpack_c64(o, u, (float2 *)canon, n_vec, st);
+}
+
+// A <- Chebyshev polynomial of degree m of H applied to A, damping [a, b]
+// and scaled to 1 at a0 < a (three-term recurrence in the scaled form of
+// Zhou and Saad); B and C are work sets.
+void gs_filter(emd_system *s, int m, double a, double b, double a0) {
+  GroundStateWork *g = s->gsw;
+  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+  double sigma = e / (a0 - c);
+  const double gamma = 2.0 / sigma;
+  const size_t nel = (size_t)g->og.n_blk * s->g.n3 * g->og.bo;
+  const size_t bytes = nel * (s->o.prec == EMD_FP64 ? sizeof(double2) : sizeof(float2));
+  void *X = g->A, *Y = g->B, *W = g->C;
+  gs_apply(s, X, W);
+  emd_launch_cheb(s->o.prec, nel, W, X, Y, sigma / e, c, 0.0, s->st);
+  for (int i = 2; i <= m; ++i) {
+    const double sigma2 = 1.0 / (gamma - sigma);
+    gs_apply(s, Y, W);
+    emd_launch_cheb(s->o.prec, nel, W, Y, X, 2.0 * sigma2 / e, c, sigma * sigma2, s->st);
+    std::swap(X, Y);
+    sigma = sigma2;
+  }
+  if (Y != g->A) cudaMemcpyAsync(g->A, Y, bytes, cudaMemcpyDeviceToDevice, s->st);
+}
+
+// A <- Rayleigh-Ritz vectors of span(A) (h^3-orthonormal, ascending Ritz
+// values into eps); on return B holds them canonically (column-major
+// n3 x m), so the occupied ones are its first n_occ columns.
+int gs_rayleigh_ritz(emd_system *s, std::vector<double> &eps) {
+  GroundStateWork *g = s->gsw;
+  const OrbLayout &og = g->og;
+  const int m = og.n_orb;
+  const int n3 = s->g.n3;
+  const double h3 = s->g.h * s->g.h * s->g.h;
+  const bool f64 = s->o.prec == EMD_FP64;
+  cublasSetStream(g->blas, s->st);
+  cusolverDnSetStream(g->solver, s->st);
+  gs_apply(s, g->A, g->B);
+  gs_unpack(og, g->A, g->C, m, s->st);      // X (canonical) in C
+  gs_unpack(og, g->B, g->A, m, s->st);      // H X (canonical) in A
+  bool ok;
+  if (f64) {
+    const cuDoubleComplex al = {h3, 0.0}, be = {0.0, 0.0};
+    const cuDoubleComplex *X = (const cuDoubleComplex *)g->C;
+    ok = cublasZgemm(g->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, m, n3, &al, X, n3, X, n3, &be,
+                     (cuDoubleComplex *)g->Sz, m) == CUBLAS_STATUS_SUCCESS &&
+         cublasZgemm(g->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, m, n3, &al, X, n3,
+                     (const cuDoubleComplex *)g->A, n3, &be, (cuDoubleComplex *)g->Hz,
+                     m) == CUBLAS_STATUS_SUCCESS;
+  } else {
+    const cuComplex al = {(float)h3, 0.f}, be = {0.f, 0.f};
+    const cuComplex *X = (const cuComplex *)g->C;
+    ok = cublasCgemm(g->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, m, n3, &al, X, n3, X, n3, &be,
+                     (cuComplex *)g->S, m) == CUBLAS_STATUS_SUCCESS &&
+         cublasCgemm(g->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, m, n3, &al, X, n3,
+                     (const cuComplex *)g->A, n3, &be, (cuComplex *)g->Hs,
+                     m) == CUBLAS_STATUS_SUCCESS;
+    emd_launch_widen((size_t)m * m, (const float2 *)g->S, g->Sz, s->st);
+    emd_launch_widen((size_t)m * m, (const float2 *)g->Hs, g->Hz, s->st);
+  }
+  if (!ok) return fail(EMD_ECUDA, "subspace product (cuBLAS) failed");
+  if (cusolverDnZhegvd(g->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                       CUBLAS_FILL_MODE_LOWER, m, (cuDoubleComplex *)g->Hz, m,
+                       (cuDoubleComplex *)g->Sz, m, g->w, (cuDoubleComplex *)g->work,
+                       g->lwork, g->dinfo) != CUSOLVER_STATUS_SUCCESS)
+    return fail(EMD_ECUDA, "subspace eigenproblem (cuSOLVER) failed");
+  int info = 0;
+  eps.resize(m);
+  CK(cudaMemcpyAsync(&info, g->dinfo, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemcpyAsync(eps.data(), g->w, (size_t)m * 8, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  if (info != 0)
+    return fail(EMD_ECUDA, "subspace eigenproblem: info %d (the filtered set lost rank)",
+                info);
+  // X V (V = eigenvectors, in Hz) into B (canonical), packed into A
+  if (f64) {
+    const cuDoubleComplex one = {1.0, 0.0}, zero = {0.0, 0.0};
+    ok = cublasZgemm(g->blas, CUBLAS_OP_N, CUBLAS_OP_N, n3, m, m, &one,
+                     (const cuDoubleComplex *)g->C, n3, (const cuDoubleComplex *)g->Hz, m,
+                     &zero, (cuDoubleComplex *)g->B, n3) == CUBLAS_STATUS_SUCCESS;
+  } else {
+    const cuComplex one = {1.f, 0.f}, zero = {0.f, 0.f};
+    emd_launch_narrow((size_t)m * m, g->Hz, (float2 *)g->V, s->st);
+    ok = cublasCgemm(g->blas, CUBLAS_OP_N, CUBLAS_OP_N, n3, m, m, &one,
+                     (const cuComplex *)g->C, n3, (const cuComplex *)g->V, m, &zero,
+                     (cuComplex *)g->B, n3) == CUBLAS_STATUS_SUCCESS;
+  }
+  if (!ok) return fail(EMD_ECUDA, "subspace rotation (cuBLAS) failed");
+  gs_pack(og, g->B, g->A, m, s->st);
+  return launch_check("ground state Rayleigh-Ritz");
+}
+
+// density of the occupied Ritz vectors (the first n_occ columns of the
+// canonical set in B), packed into C with the occupied blocks only
+void gs_density(emd_system *s, double *rho) {
+  GroundStateWork *g = s->gsw;
+  OrbLayout oo = g->og;
+  oo.n_orb = g->n_occ;
+  oo.n_blk = (g->n_occ + oo.bo - 1) / oo.bo;
+  oo.n_orb_pad = oo.n_blk * oo.bo;
+  gs_pack(oo, g->B, g->C, g->n_occ, s->st);
+  emd_launch_density(oo, g->C, s->cfg.occ, rho, s->st);
+}
+
+// Anderson mixing: with F_i = rho_out_i - rho_in_i over the stored
+// iterations, c minimises |sum c_i F_i| subject to sum c_i = 1, and
+// rho_in <- sum c_i (rho_in_i + mix F_i).  B holds <F_i, F_j>.
+void gs_anderson_coefficients(const double (&B)[GroundStateWork::kHist][GroundStateWork::kHist],
+                              const std::vector<int> &act, int newest, std::vector<double> &c) {
+  const int m = (int)act.size();
+  std::vector<double> M(m * m), x(m, 1.0);
+  double dmax = 0.0;
+  for (int i = 0; i < m; ++i) dmax = std::max(dmax, B[act[i]][act[i]]);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j)
+      M[i * m + j] = B[act[i]][act[j]] + (i == j ? 1e-12 * dmax : 0.0);
+  bool ok = dmax > 0.0;
+  for (int k = 0; ok && k < m; ++k) {       // Gaussian elimination, partial pivoting
+    int p = k;
+    for (int i = k + 1; i < m; ++i)
+      if (std::fabs(M[i * m + k]) > std::fabs(M[p * m + k])) p = i;
+    if (!(std::fabs(M[p * m + k]) > 0.0)) {
+      ok = false;
+      break;
+    }
+    if (p != k) {
+      for (int j = 0; j < m; ++j) std::swap(M[k * m + j], M[p * m + j]);
+      std::swap(x[k], x[p]);
+    }
+    for (int i = k + 1; i < m; ++i) {
+      const double f = M[i * m + k] / M[k * m + k];
+      for (int j = k; j < m; ++j) M[i * m + j] -= f * M[k * m + j];
+      x[i] -= f * x[k];
+    }
+  }
+  for (int k = m - 1; ok && k >= 0; --k) {
+    double v = x[k];
+    for (int j = k + 1; j < m; ++j) v -= M[k * m + j] * x[j];
+    x[k] = v / M[k * m + k];
+  }
+  double sum = 0.0;
+  for (int i = 0; ok && i < m; ++i) sum += x[i];
+  ok = ok && std::isfinite(sum) && std::fabs(sum) > 0.0;
+  c.assign(m, 0.0);
+  if (!ok) {                                // plain mixing with the newest pair
+    for (int i = 0; i < m; ++i) c[i] = act[i] == newest ? 1.0 : 0.0;
+    return;
+  }
+  for (int i = 0; i < m; ++i) c[i] = x[i] / sum;
+}
+
+}  // namespace
+
+extern "C" {
+
+int emd_ground_state(emd_system *s, int max_scf, double tol, int degree, double mix,
+                     double *eigenvalues, emd_gs_info *info) {
+  g_err.clear();
+  if (!s) return fail(EMD_EINVAL, "NULL system");
+  if (!s->ions_set || !s->orbs_set) return fail(EMD_ESTATE, "set ions and orbitals first");
+  if (max_scf < 1 || !(tol > 0.0) || degree < 1 || degree > 64 || !(mix > 0.0) || mix > 1.0)
+    return fail(EMD_EINVAL, "need max_scf >= 1, tol > 0, 1 <= degree <= 64, 0 < mix <= 1");
+  int r = gs_setup(s);
+  if (r) return r;
+  GroundStateWork *g = s->gsw;
+  const int n_occ = g->n_occ, m = g->og.n_orb;
+  const int n3 = s->g.n3;
+  const double h3 = s->g.h * s->g.h * s->g.h;
+  const double n_e = s->cfg.occ * n_occ;
+  const int nb = std::min(s->n_partials, 1024);
+  constexpr int K = GroundStateWork::kHist;
+  s->c_valid = 0;
+  s->needs_restart = 1;                     // whatever happens, derived state is stale
+  // starting subspace: the current orbitals and random buffer states
+  gs_unpack(s->o, s->psi, g->B, n_occ, s->st);
+  emd_launch_fill_random(s->o.prec, g->B, (size_t)n3, n_occ, m, 0x5eedu, s->st);
+  gs_pack(g->og, g->B, g->A, m, s->st);
+  emd_launch_density(s->o, s->psi, s->cfg.occ, g->rho_in, s->st);
+  gs_potential(s, g->rho_in);
+  std::vector<double> eps;
+  r = gs_rayleigh_ritz(s, eps);
+  if (r) return r;
+  double B[K][K] = {};
+  std::vector<int> act;
+  double res = 0.0;
+  int it = 0;
+  bool converged = false;
+  const double lam_kin = 1.5 * kinetic_lambda_max(s->cfg.fd_order) / (s->g.h * s->g.h);
+  for (it = 1; it <= max_scf; ++it) {
+    double vmax = 0.0;
+    r = reduce_max_veff(s, &vmax);
+    if (r) return r;
+    const double b = lam_kin + std::max(0.0, vmax) + std::max(0.0, s->sp.h_kb);
+    const double a0 = eps.front(), a = eps.back();
+    if (!(a < b) || !(a0 < a)) return fail(EMD_ECUDA, "Ritz values outside the filter bounds");
+    gs_filter(s, degree, a, b, a0);
+    r = gs_rayleigh_ritz(s, eps);
+    if (r) return r;
+    gs_density(s, g->rho_out);
+    emd_launch_absdiff_partials(n3, g->rho_out, g->rho_in, s->partials, nb, s->st);
+    emd_launch_sum(s->partials, nb, s->scal + 8, s->st);
+    double l1 = 0.0;
+    CK(cudaMemcpyAsync(&l1, s->scal + 8, 8, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    res = h3 * l1 / n_e;
+    if (!std::isfinite(res)) return fail(EMD_ECUDA, "ground state: non-finite density");
+    if (res < tol) {
+      converged = true;
+      break;
+    }
+    // store (rho_in, F) in the oldest slot and mix
+    const int k = (it - 1) % K;
+    CK(cudaMemcpyAsync(g->hr[k], g->rho_in, (size_t)n3 * 8, cudaMemcpyDeviceToDevice, s->st));
+    EmdComb f{};
+    f.p[0] = g->rho_out;
+    f.w[0] = 1.0;
+    f.p[1] = g->rho_in;
+    f.w[1] = -1.0;
+    f.m = 2;
+    emd_launch_comb(n3, f, g->hf[k], s->st);
+    act.erase(std::remove(act.begin(), act.end(), k), act.end());
+    act.push_back(k);
+    for (size_t j = 0; j < act.size(); ++j) {
+      emd_launch_dot_partials(n3, g->hf[k], g->hf[act[j]], nullptr, nullptr, s->partials, nb,
+                              s->st);
+      emd_launch_sum(s->partials, nb, s->scal + 8 + j, s->st);
+    }
+    double dots[K];
+    CK(cudaMemcpyAsync(dots, s->scal + 8, act.size() * 8, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    for (size_t j = 0; j < act.size(); ++j) B[k][act[j]] = B[act[j]][k] = dots[j];
+    std::vector<double> c;
+    gs_anderson_coefficients(B, act, k, c);
+    EmdComb cb{};
+    cb.m = 0;
+    for (size_t j = 0; j < act.size(); ++j) {
+      cb.p[cb.m] = g->hr[act[j]];
+      cb.w[cb.m++] = c[j];
+      cb.p[cb.m] = g->hf[act[j]];
+      cb.w[cb.m++] = c[j] * mix;
+    }
+    emd_launch_comb(n3, cb, g->rho_in, s->st);
+    gs_potential(s, g->rho_in);
+  }
+  // the occupied Ritz vectors become the system's orbitals
+  gs_pack(s->o, g->B, s->psi, n_occ, s->st);
+  r = launch_check("emd_ground_state");
+  if (r) return r;
+  CK(cudaStreamSynchronize(s->st));
+  if (eigenvalues) std::copy(eps.begin(), eps.begin() + n_occ, eigenvalues);
+  if (info) {
+    info->iterations = converged ? it : max_scf;
+    info->residual = res;
+    double sum = 0.0;
+    for (int i = 0; i < n_occ; ++i) sum += eps[i];
+    info->band_energy = s->cfg.occ * sum;
+    info->gap = eps[n_occ] - eps[n_occ - 1];
+  }
+  if (!converged)
+    return fail(EMD_ENOTCONV, "ground state: residual %.3e after %d iterations (tol %.3e)",
+                res, max_scf, tol);
+  return EMD_OK;
+}
+
 int emd_kernel_stats(emd_system *s, int kernel, double *ms_total,
                      long long *launches) {
   g_err.clear();
@@ -1904,6 +2302,7 @@ void emd_destroy(emd_system *s) {
     for (void *p : s->adj->mem) cudaFree(p);
     delete s->adj;
   }
+  gs_release(s->gsw);
   for (auto &ev : s->prof_pending) {
     cudaEventDestroy(ev.first);
     cudaEventDestroy(ev.second);

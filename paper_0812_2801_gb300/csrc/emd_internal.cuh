@@ -194,6 +194,28 @@ void emd_launch_dot_partials(int n3, const double *a, const double *b,
 void emd_launch_sum(const double *partials, int n, double *out,
                     cudaStream_t st);
 
+// groundstate.cu
+// out = alpha (w - c y) - beta out over n complex values of the orbital
+// precision (beta = 0: out only written); out aliases neither w nor y
+void emd_launch_cheb(int prec, size_t n, const void *w, const void *y, void *out,
+                     double alpha, double c, double beta, cudaStream_t st);
+struct EmdComb {
+  const double *p[16];
+  double w[16];
+  int m;
+};
+// out = sum_k w_k p_k over n3 points
+void emd_launch_comb(int n3, const EmdComb &cb, double *out, cudaStream_t st);
+// part[b] = block sums of |a - b|
+void emd_launch_absdiff_partials(int n3, const double *a, const double *b, double *part,
+                                 int nblocks, cudaStream_t st);
+void emd_launch_widen(size_t n, const float2 *a, double2 *b, cudaStream_t st);
+void emd_launch_narrow(size_t n, const double2 *a, float2 *b, cudaStream_t st);
+// columns c0 .. c1-1 of a canonical (n3 x m, column-major) orbital array
+// filled with uniform values in [-1, 1) (counter hash of seed and index)
+void emd_launch_fill_random(int prec, void *canon, size_t n3, int c0, int c1, unsigned seed,
+                            cudaStream_t st);
+
 // hpsi.cu
 struct StageArgs {
   const void *u_in;

@@ -16,6 +16,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libemd.so")
 
 EMD_OK, EMD_EINVAL, EMD_ENOMEM, EMD_ECUDA, EMD_EUNSTABLE, EMD_ESTATE, EMD_ETABLE = range(7)
+EMD_ENOTCONV = 7
 EMD_FP64, EMD_FP32_ORBITALS = 0, 1
 EMD_OPT_FROZEN_IONS, EMD_OPT_PROFILE, EMD_OPT_CHECK_STABLE, EMD_OPT_STAGE_VARIANT = 1, 2, 3, 4
 EMD_OPT_PROJECTION = 5
@@ -49,6 +50,11 @@ class emd_energy(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class emd_gs_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("residual", ctypes.c_double),
+                ("band_energy", ctypes.c_double), ("gap", ctypes.c_double)]
 
 
 _lib = None
@@ -90,6 +96,8 @@ def load() -> ctypes.CDLL:
     lib.emd_batch_propagate.restype = ctypes.c_int
     lib.emd_batch_destroy.argtypes = [vp]
     lib.emd_batch_destroy.restype = None
+    lib.emd_ground_state.argtypes = [vp, ip, dp, ip, dp, _DPTR, ctypes.POINTER(emd_gs_info)]
+    lib.emd_ground_state.restype = ctypes.c_int
     lib.emd_destroy.argtypes = [vp]
     lib.emd_destroy.restype = None
     lib.emd_last_error.restype = ctypes.c_char_p
@@ -171,6 +179,18 @@ def emd_get_energy(h) -> dict:
     e = emd_energy()
     _check(load().emd_get_energy(h, ctypes.byref(e)))
     return e.as_dict()
+
+
+def emd_ground_state(h, n_orb: int, max_scf: int = 200, tol: float = 1e-10,
+                     degree: int = 16, mix: float = 0.5):
+    """Ground state at the current ions (see include/emd.h).  Returns
+    (eigenvalues [n_orb], info dict); raises EmdError, with code
+    EMD_ENOTCONV if the tolerance was not reached."""
+    w = np.zeros(n_orb)
+    info = emd_gs_info()
+    _check(load().emd_ground_state(h, max_scf, tol, degree, mix, _dptr(w), ctypes.byref(info)))
+    return w, {"iterations": info.iterations, "residual": info.residual,
+               "band_energy": info.band_energy, "gap": info.gap}
 
 
 def emd_get_state(h, n_atoms: int, n_orb: int, n: int, want_psi=True, want_rho=True):

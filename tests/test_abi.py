@@ -54,3 +54,8 @@ def test_support_radius_larger_than_box_rejected(lib):
     with pytest.raises(emd.EmdError) as ei:
         emd.emd_init_system(emd.config_for(s))
     assert ei.value.code == emd.EMD_EINVAL
+
+
+def test_ground_state_rejects_null_system_before_device_use(lib):
+    assert lib.emd_ground_state(None, 10, 1e-8, 8, 0.5, None, None) == emd.EMD_EINVAL
+    assert "NULL" in lib.emd_last_error().decode()
