@@ -288,6 +288,24 @@ def sawtooth_point(zc: np.ndarray, L: float) -> np.ndarray:
     return zw - 0.5 * L
 
 
+def dipole(rho: np.ndarray, R: np.ndarray, z_ion: float, h: float) -> np.ndarray:
+    """Dipole of the electrons and ions in the length gauge of a periodic box
+    (the sawtooth coordinate of ``sawtooth_z`` along each axis):
+    D_a = -h^3 sum_r rho(r) (r_a - L/2) + sum_J Z (R_Ja wrapped - L/2),
+    with grid points r_a = i h in [0, L), axes (x, y, z)."""
+    n = rho.shape[0]
+    L = n * h
+    s = np.arange(n) * h - 0.5 * L
+    D = np.empty(3)
+    # canonical layout rho[z][y][x]
+    D[0] = -h ** 3 * np.sum(rho * s[None, None, :])
+    D[1] = -h ** 3 * np.sum(rho * s[None, :, None])
+    D[2] = -h ** 3 * np.sum(rho * s[:, None, None])
+    for a in range(3):
+        D[a] += z_ion * np.sum(sawtooth_point(R[:, a], L))
+    return D
+
+
 # --------------------------------------------------------------------------
 # Hamiltonian (eq. new_EoM_a) and its pieces
 # --------------------------------------------------------------------------

@@ -573,3 +573,27 @@ def test_hamiltonian_is_functional_derivative_of_energy():
     e = 1e-5
     num = (eks(e) - eks(-e)) / (2 * e)
     assert abs(num - ana) < 1e-6 * abs(ana)
+
+
+def test_dipole_of_a_shifted_gaussian_cloud():
+    """A Gaussian electron cloud of charge N at c (sigma = 0.5, tails at the
+    box edge below 1e-15, sampling error of its moments ~e^-55) has
+    electron dipole -N (c - L/2) along each axis (symmetry); shifting it by
+    k grid points moves that by -N k h; a point ion of charge Z at the same
+    centre cancels it when Z = N."""
+    n, h = 32, 0.3
+    L = n * h
+    x = np.arange(n) * h
+    c = np.array([4.2, 5.1, 4.8])           # cloud centre on no grid symmetry
+
+    def cloud(cc):
+        g = [np.exp(-(x - cc[a]) ** 2 / (2 * 0.5 ** 2)) for a in range(3)]
+        rho = g[2][:, None, None] * g[1][None, :, None] * g[0][None, None, :]
+        return rho * 4.0 / (rho.sum() * h ** 3)    # 4 electrons
+
+    D = O.dipole(cloud(c), np.zeros((0, 3)), 4.0, h)
+    # discrete symmetric cloud: first moment equals the centre to ~1e-12
+    assert np.allclose(D, -4.0 * (c - L / 2), atol=1e-9)
+    D2 = O.dipole(cloud(c + np.array([0, 0, 2 * h])), np.zeros((0, 3)), 4.0, h)
+    assert abs((D2[2] - D[2]) - (-4.0 * 2 * h)) < 1e-9
+    assert np.allclose(O.dipole(cloud(c), c[None, :] + L, 4.0, h), 0.0, atol=1e-9)
