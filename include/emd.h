@@ -293,6 +293,15 @@ void emd_batch_destroy(emd_batch *b);
 int emd_poisson_static(int n, double h, const double *charge, double *v,
                        void *cuda_stream);
 
+/* Dipole of the current state, D[3] (host): D_a = -h^3 sum_r rho(r)
+ * (r_a - L/2) + sum_J Z (R_Ja - L/2), grid points r_a = i h in [0, L) and
+ * positions folded into [0, L): the sawtooth coordinate of the field's
+ * length gauge along each axis.  Meaningful for a system well inside the
+ * box (a molecule away from the faces).  Used for the infrared spectrum of
+ * a trajectory (the time derivative of D).  Errors: EMD_EINVAL,
+ * EMD_ESTATE. */
+int emd_get_dipole(emd_system *s, double *D);
+
 /* Kohn-Sham ground state at the current ions (Sec. 4.1, eqs. EoM_BO_a and
  * EoM_BO_b): orthonormal orbitals that satisfy H_KS[rho] phi_A =
  * sum_B Lambda_AB phi_B with rho built from them and fill the n_orb lowest

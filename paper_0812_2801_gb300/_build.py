@@ -18,7 +18,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libemd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["emd_api.cu", "hpsi.cu", "tables.cu", "poisson.cu", "adjoint.cu", "project_pm.cu",
-           "groundstate.cu"]
+           "groundstate.cu", "observables.cu"]
 
 
 def nvcc() -> str:

@@ -2260,6 +2260,33 @@ int emd_ground_state(emd_system *s, int max_scf, double tol, int degree, double 
   return EMD_OK;
 }
 
+int emd_get_dipole(emd_system *s, double *D) {
+  g_err.clear();
+  if (!s || !D) return fail(EMD_EINVAL, "NULL argument");
+  if (!s->ions_set || !s->orbs_set) return fail(EMD_ESTATE, "set ions and orbitals first");
+  int r = ensure_state(s);
+  if (r) return r;
+  const int nb = std::min(s->n_partials / 3, 512);
+  emd_launch_dipole_partials(s->g.n, s->g.h, s->rho, s->partials, nb, s->st);
+  for (int a = 0; a < 3; ++a) emd_launch_sum(s->partials + a * nb, nb, s->scal + 8 + a, s->st);
+  double sums[3];
+  const int na = s->n_atoms;
+  std::vector<double> Rw(3 * std::max(1, na));
+  CK(cudaMemcpyAsync(sums, s->scal + 8, sizeof sums, cudaMemcpyDeviceToHost, s->st));
+  if (na)
+    CK(cudaMemcpyAsync(Rw.data(), s->ts[s->cur].Rw, 3 * na * 8, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  r = launch_check("emd_get_dipole");
+  if (r) return r;
+  const double h3 = s->g.h * s->g.h * s->g.h;
+  for (int a = 0; a < 3; ++a) {
+    double d = -h3 * sums[a];
+    for (int J = 0; J < na; ++J) d += s->sp.z * (Rw[3 * J + a] - 0.5 * s->g.L);
+    D[a] = d;
+  }
+  return read_err_flag(s);
+}
+
 int emd_kernel_stats(emd_system *s, int kernel, double *ms_total,
                      long long *launches) {
   g_err.clear();

@@ -216,6 +216,11 @@ void emd_launch_narrow(size_t n, const double2 *a, float2 *b, cudaStream_t st);
 void emd_launch_fill_random(int prec, void *canon, size_t n3, int c0, int c1, unsigned seed,
                             cudaStream_t st);
 
+// observables.cu
+// part[a * nblocks + b]: block sums of rho (r_a - L/2), a = x, y, z
+void emd_launch_dipole_partials(int n, double h, const double *rho, double *part, int nblocks,
+                                cudaStream_t st);
+
 // hpsi.cu
 struct StageArgs {
   const void *u_in;

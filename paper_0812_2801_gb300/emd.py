@@ -96,6 +96,8 @@ def load() -> ctypes.CDLL:
     lib.emd_batch_propagate.restype = ctypes.c_int
     lib.emd_batch_destroy.argtypes = [vp]
     lib.emd_batch_destroy.restype = None
+    lib.emd_get_dipole.argtypes = [vp, _DPTR]
+    lib.emd_get_dipole.restype = ctypes.c_int
     lib.emd_ground_state.argtypes = [vp, ip, dp, ip, dp, _DPTR, ctypes.POINTER(emd_gs_info)]
     lib.emd_ground_state.restype = ctypes.c_int
     lib.emd_destroy.argtypes = [vp]
@@ -179,6 +181,12 @@ def emd_get_energy(h) -> dict:
     e = emd_energy()
     _check(load().emd_get_energy(h, ctypes.byref(e)))
     return e.as_dict()
+
+
+def emd_get_dipole(h) -> np.ndarray:
+    D = np.zeros(3)
+    _check(load().emd_get_dipole(h, _dptr(D)))
+    return D
 
 
 def emd_ground_state(h, n_orb: int, max_scf: int = 200, tol: float = 1e-10,

@@ -59,6 +59,9 @@ class Species:
 
 
 SI_LIKE = Species()
+# five valence electrons: a homonuclear dimer of it is closed-shell (the
+# sigma and both pi bonding levels filled, like the paper's N2 example)
+N_LIKE = Species(z=5.0, mass=14.0067 * AMU_IN_ME)
 
 
 @dataclasses.dataclass

@@ -384,6 +384,24 @@ def test_fp32_kinetic_energy_of_plane_waves():
     assert abs(got - exact) < 2e-7 * exact, (got, exact)
 
 
+def test_dipole_matches_oracle(small):
+    """emd_get_dipole against the oracle's dipole of the same state, at the
+    start and after 3 MD steps (ions moved, density changed)."""
+    s = small
+    g = emd.System(s)
+    st = O.init_state(s)
+    D = emd.emd_get_dipole(g.handle)
+    Do = O.dipole(st.rho, st.R, s.species.z, s.h)
+    assert np.max(np.abs(D - Do)) < 1e-11 * max(1.0, np.max(np.abs(Do))), (D, Do)
+    g.propagate(3, dt=0.04, mu=1.0)
+    st3 = O.run(s, 3, dt=0.04, mu=1.0)
+    D3 = emd.emd_get_dipole(g.handle)
+    g.close()
+    Do3 = O.dipole(st3.rho, st3.R, s.species.z, s.h)
+    assert np.max(np.abs(D3 - Do3)) < 1e-9 * max(1.0, np.max(np.abs(Do3))), (D3, Do3)
+    assert np.max(np.abs(D3 - D)) > 1e-6          # the state did move
+
+
 def test_setters_in_any_order_give_the_same_state():
     """set_ions / set_orbitals mark the derived state (rho, v_Hxc, c, F) for
     recomputation at the next reading call: the order of the setters, a
