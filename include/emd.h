@@ -174,7 +174,12 @@ int emd_get_orbitals_c64(emd_system *s, float *psi);
  * v_ext = e_n (z - L/2), held during step n, force Z e_n on each ion.
  * Refuses with EMD_EUNSTABLE if tau*lambda_max > 2 sqrt(2), the Taylor-4
  * stability bound on the imaginary axis (lambda_max estimated as the
- * largest FD kinetic eigenvalue + max v_eff + h_kb).  Enqueues only. */
+ * largest FD kinetic eigenvalue + max v_eff + h_kb).  Enqueues only.
+ * With field == NULL, moving ions and EMD_OPT_PROFILE off, runs of 6 or more
+ * steps replay a CUDA graph of 6 steps captured on first use (captured
+ * again when dt, mu, the stage variant, the projection form, the position
+ * set or the v_Hxc history slots no longer match it); the results are
+ * bitwise those of step-by-step propagation. */
 int emd_propagate(emd_system *s, int n_steps, double dt, double mu,
                   const double *field);
 

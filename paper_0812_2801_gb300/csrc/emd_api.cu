@@ -151,6 +151,9 @@ struct emd_system {
   std::vector<void *> allocs;
   struct Adjoint *adj = nullptr;
   struct GroundStateWork *gsw = nullptr;
+  // a batch of this system alone: emd_propagate replays its captured
+  // graph of 6 MD steps for long field-free runs
+  emd_batch *self_batch = nullptr;
 };
 
 namespace {
@@ -857,7 +860,11 @@ struct emd_batch {
   cudaEvent_t fork = nullptr;
   cudaGraphExec_t exec = nullptr;
   double key_dt = 0.0, key_mu = 0.0;
-  std::vector<int> key_cur;
+  // host-side state baked into the captured graph: the position-set parity,
+  // the v_Hxc history slots (rotated by pointer, period 3) and the options
+  // that select kernels
+  std::vector<int> key_cur, key_variant, key_proj;
+  std::vector<const double *> key_hist;
   long long graph_launches = 0;
 };
 
@@ -905,15 +912,27 @@ int batch_capture(emd_batch *b, double dt, double mu) {
   }
   b->key_dt = dt;
   b->key_mu = mu;
-  b->key_cur.resize(b->sys.size());
-  for (size_t i = 0; i < b->sys.size(); ++i) b->key_cur[i] = b->sys[i]->cur;
+  const size_t m = b->sys.size();
+  b->key_cur.resize(m);
+  b->key_variant.resize(m);
+  b->key_proj.resize(m);
+  b->key_hist.resize(m);
+  for (size_t i = 0; i < m; ++i) {
+    b->key_cur[i] = b->sys[i]->cur;
+    b->key_variant[i] = b->sys[i]->o.stage_variant;
+    b->key_proj[i] = b->sys[i]->proj_atom_major;
+    b->key_hist[i] = b->sys[i]->hist[0];
+  }
   return EMD_OK;
 }
 
 bool batch_graph_valid(const emd_batch *b, double dt, double mu) {
   if (!b->exec || b->key_dt != dt || b->key_mu != mu) return false;
   for (size_t i = 0; i < b->sys.size(); ++i)
-    if (b->key_cur[i] != b->sys[i]->cur) return false;
+    if (b->key_cur[i] != b->sys[i]->cur || b->key_hist[i] != b->sys[i]->hist[0] ||
+        b->key_variant[i] != b->sys[i]->o.stage_variant ||
+        b->key_proj[i] != b->sys[i]->proj_atom_major)
+      return false;
   return true;
 }
 }  // namespace
@@ -929,6 +948,16 @@ int emd_propagate(emd_system *s, int n_steps, double dt, double mu,
   if (field)
     for (int i = 0; i < n_steps; ++i)
       if (!std::isfinite(field[i])) return fail(EMD_EINVAL, "non-finite field");
+  // long field-free runs replay a captured graph (launch overhead dominates
+  // small grids); profiling needs one event pair per launch, so it stays eager
+  if (!field && !s->frozen_ions && !s->profile && n_steps >= kGraphSteps) {
+    if (!s->self_batch) {
+      emd_system *one[1] = {s};
+      r = emd_batch_create(1, one, &s->self_batch);
+      if (r) return r;
+    }
+    return emd_batch_propagate(s->self_batch, n_steps, dt, mu);
+  }
   for (int step = 0; step < n_steps; ++step) {
     r = step_once(s, dt, mu, field ? field[step] : 0.0);
     if (r) return r;
@@ -2316,6 +2345,7 @@ int emd_kernel_stats(emd_system *s, int kernel, double *ms_total,
 
 void emd_destroy(emd_system *s) {
   if (!s) return;
+  emd_batch_destroy(s->self_batch);
   if (s->st) cudaStreamSynchronize(s->st);
   else cudaDeviceSynchronize();
   if (s->cst) {

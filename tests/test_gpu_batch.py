@@ -41,6 +41,41 @@ def test_batch_equals_individual_runs(prec):
         assert np.array_equal(f1, f2)
 
 
+def test_batch_replay_after_a_shifted_history_phase():
+    """A call ending in 2 eager steps leaves the position-set parity as it
+    was but rotates the three v_Hxc history slots; the next call must not
+    replay a graph captured at the other rotation.  Also a plain propagate
+    between batch calls, and a changed stage variant."""
+    sysins = replicas()
+    dt, mu = 0.04, 1.0
+    solo = []
+    for s in sysins:
+        g = emd.System(s, emd.EMD_FP32_ORBITALS)
+        g.propagate(14 + 8 + 6 + 1 + 6 + 6, dt=dt, mu=mu)
+        solo.append((g.state()[2], g.forces()))
+        g.close()
+    gs = [emd.System(s, emd.EMD_FP32_ORBITALS) for s in sysins]
+    b = emd.emd_batch_create([g.handle for g in gs])
+    emd.emd_batch_propagate(b, 14, dt, mu)     # 2 eager + 2 graph chunks
+    emd.emd_batch_propagate(b, 8, dt, mu)      # 1 graph chunk + 2 eager
+    emd.emd_batch_propagate(b, 6, dt, mu)      # same parity, other history slots
+    for g in gs:
+        g.propagate(1, dt=dt, mu=mu)           # outside the batch
+    emd.emd_batch_propagate(b, 6, dt, mu)
+    emd.emd_set_option(gs[0].handle, emd.EMD_OPT_STAGE_VARIANT, 1)
+    emd.emd_batch_propagate(b, 6, dt, mu)
+    got = [(g.state()[2], g.forces()) for g in gs]
+    emd.emd_batch_destroy(b)
+    for g in gs:
+        g.close()
+    for k, ((p1, f1), (p2, f2)) in enumerate(zip(solo, got)):
+        if k == 0:   # another kernel for the last 6 steps: same physics
+            assert np.max(np.abs(p1 - p2)) < 1e-5 * np.max(np.abs(p1))
+        else:
+            assert np.array_equal(p1, p2), k
+            assert np.array_equal(f1, f2), k
+
+
 def test_batch_fp64_matches_oracle():
     sysins = replicas()[:2]
     gs = [emd.System(s) for s in sysins]

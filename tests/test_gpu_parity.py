@@ -121,6 +121,25 @@ def test_runs_are_deterministic(small):
     assert np.array_equal(res[0][1], res[1][1])
 
 
+@pytest.mark.parametrize("prec", [emd.EMD_FP64, emd.EMD_FP32_ORBITALS])
+def test_graph_replay_equals_step_by_step(small, prec):
+    """emd_propagate replays a captured 6-step graph for long field-free
+    runs: 20 steps in one call (2 eager steps, 3 graph chunks), 20 calls of
+    one step, and 7 + 13 steps (the second call starts at another history
+    phase) agree bitwise."""
+    s = small
+    res = []
+    for chunks in ((20,), (1,) * 20, (7, 13)):
+        g = emd.System(s, prec)
+        for k in chunks:
+            g.propagate(k, dt=0.04, mu=1.0)
+        res.append((g.state()[2], g.forces()))
+        g.close()
+    for other in res[1:]:
+        assert np.array_equal(res[0][0], other[0])
+        assert np.array_equal(res[0][1], other[1])
+
+
 def test_unstable_time_step_refused():
     """Taylor-4 on the imaginary axis is stable only for tau*lambda <= 2 sqrt 2:
     the 96^3 order-8 workload at mu = 1, dt = 0.05 lies outside."""
