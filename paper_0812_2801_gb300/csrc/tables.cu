@@ -107,6 +107,7 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
               double *g_ion, int *te_off, uint2 *te_pp, float4 *te_q, int *err) {
   __shared__ int cand[EMD_TILE_CAND_MAX];
   __shared__ float cfs[EMD_TILE_CAND_MAX][3];
+  __shared__ float cfl[F32 ? EMD_TILE_CAND_MAX : 1][3];   // low parts of the centres
   __shared__ int run_start[EMD_TILE_ATOM_MAX + 1];
   __shared__ int s_nrun;
   __shared__ int warp_tot[16];
@@ -118,9 +119,13 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
     const int code = tile_ent[t * EMD_TILE_CAND_MAX + i];
     const int J = code / 27, img = code % 27;
     cand[i] = code;
-    cfs[i][0] = (float)(Rw[3 * J + 0] + (img % 3 - 1) * L);
-    cfs[i][1] = (float)(Rw[3 * J + 1] + ((img / 3) % 3 - 1) * L);
-    cfs[i][2] = (float)(Rw[3 * J + 2] + (img / 9 - 1) * L);
+    const double c[3] = {Rw[3 * J + 0] + (img % 3 - 1) * L,
+                         Rw[3 * J + 1] + ((img / 3) % 3 - 1) * L,
+                         Rw[3 * J + 2] + (img / 9 - 1) * L};
+    for (int a = 0; a < 3; ++a) {
+      cfs[i][a] = (float)c[a];
+      if (F32) cfl[i][a] = (float)(c[a] - (double)cfs[i][a]);
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -155,6 +160,11 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
   const float rp2f = (float)rp2, rl2f = (float)rl2, hf = (float)h;
   const float rmax2f = fmaxf(rp2f, rl2f) + margin;
   const float xf = (float)x * hf, yf = (float)y * hf, zf = (float)z * hf;
+  // the grid coordinate as float hi + lo (complex64 projector values)
+  const double gx = (double)x * h, gy = (double)y * h, gz = (double)z * h;
+  const float gxh = (float)gx, gyh = (float)gy, gzh = (float)gz;
+  const float gxl = (float)(gx - (double)gxh), gyl = (float)(gy - (double)gyh),
+              gzl = (float)(gz - (double)gzh);
   const int nrun = s_nrun;
   int cnt = 0;
   double gsum = 0.0;
@@ -237,21 +247,23 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
       }
       if (in_p) {
         if (F32) {
-          // displacement and d^2 in FP64, then rounded once: the float atom
-          // coordinate (float)(R + image L) is off by up to half an ulp of L,
-          // the same shift for every point of the sphere, and the projector
-          // force sum_r p d psi cancels strongly, so that shift would show up
-          // at ~1e-4 of the forces
-          const double ex = emd_disp(x, h, Rw[3 * J + 0], img % 3 - 1, L);
-          const double ey = emd_disp(y, h, Rw[3 * J + 1], (img / 3) % 3 - 1, L);
-          const double ez = emd_disp(z, h, Rw[3 * J + 2], img / 9 - 1, L);
-          const float pv =
-              (float)sp.c_p * expf(-(float)(emd_norm2(ex, ey, ez) * sp.inv_2rc2));
+          // displacement from hi + lo parts of both coordinates: the hi
+          // difference is rounded once from the exact one, so the result is
+          // the displacement to an ulp or two.  A plain float atom coordinate
+          // (float)(R + image L) is off by up to half an ulp of L, the same
+          // shift for every point of the sphere, and the projector force
+          // sum_r p d psi cancels strongly: that shift showed up at ~1e-4 of
+          // the forces.
+          const float ex = (gxh - cfs[e][0]) + (gxl - cfl[e][0]);
+          const float ey = (gyh - cfs[e][1]) + (gyl - cfl[e][1]);
+          const float ez = (gzh - cfs[e][2]) + (gzl - cfl[e][2]);
+          const float pv = (float)sp.c_p *
+                           expf(-(ex * ex + ey * ey + ez * ez) * (float)sp.inv_2rc2);
           const float w = pv * (float)sp.inv_rc2;
           psumf += pv;
-          pdx += w * (float)ex;
-          pdy += w * (float)ey;
-          pdz += w * (float)ez;
+          pdx += w * ex;
+          pdy += w * ey;
+          pdz += w * ez;
         } else {
           psum += sp.c_p * exp(-d2 * sp.inv_2rc2);
         }
