@@ -1018,9 +1018,12 @@ int emd_batch_propagate(emd_batch *b, int n_steps, double dt, double mu) {
       for (size_t i = 0; i < m && rc == EMD_OK; ++i)
         rc = step_once(b->sys[i], dt, mu, 0.0);
   };
+  // a captured chunk assumes the full v_Hxc history and valid projections
+  // of psi (its first step skips re-projecting): step eagerly until both hold
   auto full_history = [&]() {
     for (size_t i = 0; i < m; ++i)
-      if (b->sys[i]->hist_len < 3 || b->sys[i]->frozen_ions) return false;
+      if (b->sys[i]->hist_len < 3 || b->sys[i]->frozen_ions || !b->sys[i]->c_valid)
+        return false;
     return true;
   };
   while (rc == EMD_OK && done_steps < n_steps &&

@@ -125,14 +125,21 @@ def test_runs_are_deterministic(small):
 def test_graph_replay_equals_step_by_step(small, prec):
     """emd_propagate replays a captured 6-step graph for long field-free
     runs: 20 steps in one call (2 eager steps, 3 graph chunks), 20 calls of
-    one step, and 7 + 13 steps (the second call starts at another history
-    phase) agree bitwise."""
+    one step, 7 + 13 steps (the second call starts at another history
+    phase), and 8 + 12 steps with an H application in between agree
+    bitwise."""
     s = small
     res = []
-    for chunks in ((20,), (1,) * 20, (7, 13)):
+    rng = np.random.default_rng(4)
+    probe = rng.normal(size=(2, s.n, s.n, s.n)) + 0j
+    for chunks in ((20,), (1,) * 20, (7, 13), (8, 12)):
         g = emd.System(s, prec)
         for k in chunks:
             g.propagate(k, dt=0.04, mu=1.0)
+            if chunks == (8, 12) and k == 8:
+                # overwrites the projections: the next replay must not
+                # start from them
+                emd.emd_apply_hamiltonian(g.handle, probe)
         res.append((g.state()[2], g.forces()))
         g.close()
     for other in res[1:]:
