@@ -47,3 +47,22 @@ def test_fit_frequency_from_a_far_guess_and_few_periods():
     x = 3.35 + 0.05 * np.cos(w0 * t) + 0.002 * np.cos(2 * w0 * t)
     w = vib.fit_frequency(t, x, 1.2 * w0)
     assert abs(w - w0) < 2e-3 * w0
+
+
+def test_study_systems_are_neutral_closed_shell_inputs():
+    """The N-like dimer: 10 electrons in 5 orthonormal orbitals, bond along
+    z through the box centre; the two-atom cell keeps its centre and sets
+    the bond length."""
+    s = vib.n_dimer(3.3)
+    assert s.n_orb * s.occ == s.n_atoms * s.species.z == 10
+    f = s.psi.reshape(s.n_orb, -1)
+    S = (f.conj() @ f.T) * s.h ** 3
+    assert np.max(np.abs(S - np.eye(s.n_orb))) < 1e-12
+    assert abs(np.linalg.norm(s.R[1] - s.R[0]) - 3.3) < 1e-12
+    assert np.allclose(s.V, 0.0)
+    b = vib.pair_base()
+    p = vib.pair(2.0, b)
+    L = b.n * b.h
+    assert abs(vib.bond_length(p.R[None], L)[0] - 2.0) < 1e-12
+    mid_b = b.R[0] + 0.5 * ((b.R[1] - b.R[0]) - L * np.round((b.R[1] - b.R[0]) / L))
+    assert np.allclose(0.5 * (p.R[0] + p.R[1]), mid_b)
