@@ -8,6 +8,13 @@
 //   4. psi <- T4(-i tau H2) T4(-i tau H1) psi, tau = dt/(2 mu)   (AETRS)
 //   5. rho, v_H, v_xc at t+dt                               (eq. density)
 //   6. F(t+dt) = -dE_KS/dR; V += (F(t) + F(t+dt)) dt/(2M)
+//
+// Also here: host I/O of orbitals (complex128 and complex64, pipelined),
+// the deferred restart after the setters, energies and forces, batches of
+// systems replayed as CUDA graphs (also used by emd_propagate for long
+// runs), the adjoint propagation (driver; kernels in adjoint.cu), the dipole
+// read-out and the ground-state solver (driver; element-wise kernels in
+// groundstate.cu).
 #include <algorithm>
 #include <atomic>
 #include <cstdarg>
@@ -2033,7 +2040,7 @@ void gs_unpack(const OrbLayout &o, const void *u, void *canon, int n_vec, cudaSt
 // A <- Chebyshev polynomial of degree m of H applied to A, damping [a, b]
 // and scaled to 1 at a0 < a (three-term recurrence in the scaled form of
 // Zhou and Saad); B and C are work sets.
-void gs_filter(emd_system *s, int m, double a, double b, double a0) {
+int gs_filter(emd_system *s, int m, double a, double b, double a0) {
   GroundStateWork *g = s->gsw;
   const double e = 0.5 * (b - a), c = 0.5 * (b + a);
   double sigma = e / (a0 - c);
@@ -2050,7 +2057,8 @@ void gs_filter(emd_system *s, int m, double a, double b, double a0) {
     std::swap(X, Y);
     sigma = sigma2;
   }
-  if (Y != g->A) cudaMemcpyAsync(g->A, Y, bytes, cudaMemcpyDeviceToDevice, s->st);
+  if (Y != g->A) CK(cudaMemcpyAsync(g->A, Y, bytes, cudaMemcpyDeviceToDevice, s->st));
+  return launch_check("ground state Chebyshev filter");
 }
 
 // A <- Rayleigh-Ritz vectors of span(A) (h^3-orthonormal, ascending Ritz
@@ -2063,8 +2071,9 @@ int gs_rayleigh_ritz(emd_system *s, std::vector<double> &eps) {
   const int n3 = s->g.n3;
   const double h3 = s->g.h * s->g.h * s->g.h;
   const bool f64 = s->o.prec == EMD_FP64;
-  cublasSetStream(g->blas, s->st);
-  cusolverDnSetStream(g->solver, s->st);
+  if (cublasSetStream(g->blas, s->st) != CUBLAS_STATUS_SUCCESS ||
+      cusolverDnSetStream(g->solver, s->st) != CUSOLVER_STATUS_SUCCESS)
+    return fail(EMD_ECUDA, "cannot bind the subspace libraries to the stream");
   gs_apply(s, g->A, g->B);
   gs_unpack(og, g->A, g->C, m, s->st);      // X (canonical) in C
   gs_unpack(og, g->B, g->A, m, s->st);      // H X (canonical) in A
@@ -2223,7 +2232,8 @@ int emd_ground_state(emd_system *s, int max_scf, double tol, int degree, double 
     const double b = lam_kin + std::max(0.0, vmax) + std::max(0.0, s->sp.h_kb);
     const double a0 = eps.front(), a = eps.back();
     if (!(a < b) || !(a0 < a)) return fail(EMD_ECUDA, "Ritz values outside the filter bounds");
-    gs_filter(s, degree, a, b, a0);
+    r = gs_filter(s, degree, a, b, a0);
+    if (r) return r;
     r = gs_rayleigh_ritz(s, eps);
     if (r) return r;
     gs_density(s, g->rho_out);
