@@ -58,7 +58,9 @@ extern "C" {
 
 /* options for emd_set_option */
 #define EMD_OPT_FROZEN_IONS  1  /* value != 0: ions fixed, no forces/VV      */
-#define EMD_OPT_PROFILE      2  /* value != 0: time Horner-stage launches     */
+#define EMD_OPT_PROFILE      2  /* value != 0: time Horner-stage launches
+                                   (one event pair each; emd_propagate then
+                                   steps without graph replay)              */
 #define EMD_OPT_CHECK_STABLE 3  /* value == 0: skip the stability refusal    */
 #define EMD_OPT_STAGE_VARIANT 4 /* complex64 Horner-stage kernel: 0 one
                                    thread per (orbital column, 2 rows) with
