@@ -59,3 +59,24 @@ def test_support_radius_larger_than_box_rejected(lib):
 def test_ground_state_rejects_null_system_before_device_use(lib):
     assert lib.emd_ground_state(None, 10, 1e-8, 8, 0.5, None, None) == emd.EMD_EINVAL
     assert "NULL" in lib.emd_last_error().decode()
+
+
+def test_binding_constants_match_the_header():
+    text = open(HEADER).read()
+    defs = dict(re.findall(r"#define\s+(EMD_[A-Z0-9_]+)\s+(-?\d+)", text))
+    for name, value in defs.items():
+        if hasattr(emd, name):
+            assert getattr(emd, name) == int(value), name
+    for name in ("EMD_OK", "EMD_EINVAL", "EMD_ESTATE", "EMD_EUNSTABLE", "EMD_ENOTCONV",
+                 "EMD_FP64", "EMD_FP32_ORBITALS", "EMD_OPT_PROFILE", "EMD_OBS_DIPOLE_Z"):
+        assert hasattr(emd, name) and name in defs, name
+
+
+def test_binding_declares_argument_types(lib):
+    """ctypes would pass Python floats and 64-bit pointers wrongly without
+    argtypes: every declared function that takes arguments has them."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    for name, args in re.findall(r"\b(emd_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text):
+        if args.strip() in ("", "void"):
+            continue
+        assert getattr(lib, name).argtypes is not None, name
