@@ -296,7 +296,9 @@ void emd_batch_destroy(emd_batch *b);
  * or different host threads on one device) race; serialise them.  The first
  * call on each device looks up the array's device address (once per device,
  * with that device current); make that first call before any stream
- * capture.  Errors: EMD_EINVAL, EMD_ECUDA. */
+ * capture.  The address is kept for the life of the process, so the entry
+ * point must not be called on a device after cudaDeviceReset on it.
+ * Errors: EMD_EINVAL, EMD_ECUDA. */
 int emd_poisson_static(int n, double h, const double *charge, double *v,
                        void *cuda_stream);
 

@@ -597,3 +597,116 @@ def test_dipole_of_a_shifted_gaussian_cloud():
     D2 = O.dipole(cloud(c + np.array([0, 0, 2 * h])), np.zeros((0, 3)), 4.0, h)
     assert abs((D2[2] - D[2]) - (-4.0 * 2 * h)) < 1e-9
     assert np.allclose(O.dipole(cloud(c), c[None, :] + L, 4.0, h), 0.0, atol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# Projector normalisation (Sec. 5, separable pseudopotential) from the
+# continuum closed forms, and the length-gauge field against the dipole energy
+# --------------------------------------------------------------------------
+
+def test_projector_overlaps_match_continuum_gaussian_integrals():
+    """The projector is a Gaussian of unit norm in the continuum.  Written
+    from that definition, not from the oracle's formula: for two such
+    Gaussians a distance d apart, int p_J p_K d^3r = exp(-d^2 / (4 r_c^2)),
+    which is 1 at d = 0.  The grid sum h^3 sum_r p_J p_K differs from the
+    integral by (i) aliasing, of order exp(-pi^2 r_c^2 / h^2) (Poisson
+    summation of a Gaussian of variance r_c^2/2; here e^-120), and (ii) the
+    cut-off at r_proj = 5 r_c.  The product p_J p_K is exp(-d^2/(4 r_c^2))
+    times a unit Gaussian of variance r_c^2/2 centred midway, d/2 from each
+    centre, so each cut-off removes at most its mass outside a ball of
+    radius x r_c, x = (r_proj - d/2)/r_c: T(x) = erfc(x) + (2/sqrt(pi)) x
+    e^(-x^2) (8e-11 at d = 0).  The test allows twice that plus 1e-12.
+    r_c = 0.7 (not 1) so that a wrong power of r_c changes the result, and
+    the supports stay inside the box (no image sums)."""
+    rc = 0.7
+    sp = I.Species(r_c=rc, r_proj=5.0 * rc)
+    n, h = 44, 0.2
+    L = n * h
+    centre = np.array([0.5 * L + 0.013, 0.5 * L - 0.021, 0.5 * L + 0.007])
+    for d in (0.0, 0.45, 1.1):
+        shift = d * np.array([1.0, 2.0, 2.0]) / 3.0      # unit vector (1,2,2)/3
+        R = np.stack([centre - 0.5 * shift, centre + 0.5 * shift])
+        t = O.atom_tables(R, sp, n, h)
+        pj = np.zeros(n ** 3)
+        pk = np.zeros(n ** 3)
+        pj[t.pmerged[0][0]] = t.pmerged[0][1]
+        pk[t.pmerged[1][0]] = t.pmerged[1][1]
+        ov = h ** 3 * float(pj @ pk)
+        x = (sp.r_proj - 0.5 * d) / rc
+        tail = math.erfc(x) + 2.0 / math.sqrt(math.pi) * x * math.exp(-x * x)
+        exact = math.exp(-d * d / (4.0 * rc * rc))
+        assert abs(ov - exact) < 2.0 * exact * tail + 1e-12, (d, ov, exact, tail)
+
+
+def _field_system():
+    sp = I.Species(r_c=0.6)                     # narrow projector: see the force pin
+    s = I.small_system(n=16, h=0.35, fd_order=4, n_atoms=2, seed=33, species=sp,
+                       n_orb=3)
+    return s
+
+
+def test_field_hamiltonian_is_derivative_of_energy_with_dipole_term():
+    """Length gauge (field along z): the energy of the electrons and ions in a
+    uniform field e is -e D_z, with D_z the dipole of the pinned dipole
+    read-out.  The step's Hamiltonian with a field must then be
+    d(E_KS - e D_z)/d phi^* / f.  The test takes the first step of the oracle
+    with ions held, where H(t+dt) = H(t) (constant extrapolation), and checks
+    (1) that it equals two Taylor halves of H_KS + e s(z), and (2) that this
+    H is the functional derivative of E_KS - e D_z by central differences
+    along a random direction."""
+    s = _field_system()
+    st = O.init_state(s)
+    e_f = 0.37                                   # large: the term must show
+    H = O.Hamiltonian(st.v_loc + st.v_h + st.v_xc + e_f * O.sawtooth_z(s.n, s.h),
+                      st.tables, s.species, s.h, s.fd_order)
+    dt, mu = 0.05, 1.0
+    tau = dt / (2 * mu)
+    got = O.md_step(st, dt, mu, field=e_f, frozen_ions=True).psi
+    assert np.max(np.abs(got - O.taylor4(O.taylor4(st.psi, tau, H), tau, H))) < 1e-14
+
+    rng = np.random.default_rng(5)
+    chi = 0.05 * (rng.normal(size=st.psi.shape[1:]) + 1j * rng.normal(size=st.psi.shape[1:]))
+    A = 2
+    ana = 2 * s.occ * s.h ** 3 * float(np.sum((np.conj(chi) * H.apply(st.psi)[A]).real))
+
+    def energy(eps):
+        psi = st.psi.copy()
+        psi[A] = psi[A] + eps * chi
+        rho, vh, ex, vx = O.electron_potentials(psi, s.occ, s.h)
+        st2 = O.State(**{**st.__dict__, "psi": psi, "rho": rho, "v_h": vh,
+                          "eps_xc": ex, "v_xc": vx})
+        return O.energies(st2)["ks"] - e_f * O.dipole(rho, st.R, s.species.z, s.h)[2]
+
+    eps = 1e-5
+    num = (energy(eps) - energy(-eps)) / (2 * eps)
+    assert abs(num - ana) < 1e-6 * abs(ana)
+
+
+def test_field_forces_are_minus_gradient_of_energy_with_dipole_term():
+    """With a field e the force on the ions is -d(E_KS - e D_z)/dR at fixed
+    orbitals (the ion part of D_z is sum_J Z s(R_Jz)).  The forces the
+    oracle's step computes with a field (F(t+dt) after one step with moving
+    ions) are compared with central differences of that energy at the new
+    state."""
+    s = _field_system()
+    s.V = s.V * 50.0
+    st0 = O.init_state(s)
+    e_f = 0.23
+    st = O.md_step(st0, 0.05, 1.0, field=e_f)
+    dR = 1e-4
+
+    def energy(R):
+        t = O.atom_tables(R, s.species, s.n, s.h)
+        g = O.ion_charge(t, s.species, s.n)
+        st2 = O.State(**{**st.__dict__, "R": R, "tables": t, "g_ion": g,
+                          "v_loc": O.poisson(-g, s.h)})
+        return O.energies(st2)["ks"] - e_f * O.dipole(st.rho, R, s.species.z, s.h)[2]
+
+    scale = np.max(np.abs(st.F))
+    assert scale > 0.5 * s.species.z * e_f       # the field term dominates
+    for j in range(2):
+        for ax in range(3):
+            Rp = st.R.copy(); Rp[j, ax] += dR
+            Rm = st.R.copy(); Rm[j, ax] -= dR
+            fd = -(energy(Rp) - energy(Rm)) / (2 * dR)
+            assert abs(fd - st.F[j, ax]) < 2e-6 * scale + 1e-8, (j, ax, fd, st.F[j, ax])
