@@ -12,6 +12,8 @@
 // Orbital layout: [block][n^3][bo] complex, bo orbitals of a block interleaved
 // per grid point, so one thread updates bo orbitals at one point and shares
 // the potential, the projector list and the index arithmetic between them.
+#include <algorithm>
+
 #include "emd_internal.cuh"
 
 namespace {
@@ -1286,7 +1288,11 @@ void stage_c_tt(const OrbLayout &o, const StageArgs &a, size_t smem, cudaStream_
     attr_done = true;
   }
   const int ntx = (o.n + Z::TX - 1) / Z::TX, nty = (o.n + Z::TY - 1) / Z::TY;
-  const int zc = o.n <= 64 ? o.n : (o.n + 1) / 2 <= 64 ? (o.n + 1) / 2 : 48;
+  // one z-chunk per column unless the columns alone would leave SMs idle:
+  // each chunk restages and re-stencils 2M halo planes
+  const int cols = ntx * nty * o.n_blk;
+  const int nz = std::max(1, std::min((2 * 152 + cols - 1) / cols, o.n / 16));
+  const int zc = (o.n + nz - 1) / nz;
   dim3 grid(ntx * nty, (o.n + zc - 1) / zc, o.n_blk);
   k_stage_c<BO, M, HCS><<<grid, Z::NT, smem, st>>>(
       (const float2 *)a.u_in, (const float2 *)a.psi0, (float2 *)a.u_out,
