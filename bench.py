@@ -44,7 +44,7 @@ BYTES_PER_UPDATE = {"f32": 24, "f64": 48}
 # dram__bytes_read.sum + dram__bytes_write.sum of one Horner-stage launch on
 # the 96^3 workload (one ncu capture), per precision, for the kernel as
 # built; None until a capture exists for it.
-TRAFFIC_PER_LAUNCH = {"f32": 3.515e9, "f64": None}
+TRAFFIC_PER_LAUNCH = {"f32": 3.146e9, "f64": None}
 
 
 def max_over_ranks(x: float, device=None) -> float:
@@ -155,12 +155,17 @@ def cpu_oracle_rate(sysin, n_orb_sample: int, reps: int = 1):
     H = O.Hamiltonian(v_loc + v_h + vxc, tables, s.species, s.h, s.fd_order)
     psi = np.ascontiguousarray(s.psi[:n_orb_sample])
     tau = 0.5 * (s.dt / s.mu)
+    c0 = os.times()
     t0 = time.perf_counter()
     for _ in range(reps):
         out = O.taylor4(O.taylor4(psi, tau, H), tau, H)
     dt = time.perf_counter() - t0
+    c1 = os.times()
     upd = 8.0 * n_orb_sample * s.n ** 3 * reps
-    return upd / dt, dt, os.cpu_count()
+    # cores the oracle kept busy: process CPU time over wall time (numpy's
+    # element-wise work and FFTs run on one thread, its BLAS calls on more)
+    cores = ((c1.user - c0.user) + (c1.system - c0.system)) / dt
+    return upd / dt, dt, round(cores, 2)
 
 
 def run_reference(args):
@@ -221,11 +226,35 @@ def time_md(emd, torch, sysin, precision, steps, warmup, profile=True):
             "energy": e}
 
 
+def energy_drift(emd, torch, sysin, precision, steps, every=20):
+    """Relative change of the conserved energy E = T_ion + E_KS (eq. E_new)
+    over `steps` MD steps of the 96^3 workload, sampled every `every` steps
+    (graph replay between samples)."""
+    sysg = emd.System(sysin, precision)
+    e0 = sysg.energy()["total"]
+    dev, done = 0.0, 0
+    t0 = time.perf_counter()
+    while done < steps:
+        k = min(every, steps - done)
+        sysg.propagate(k)
+        done += k
+        dev = max(dev, abs(sysg.energy()["total"] - e0))
+    e1 = sysg.energy()["total"]
+    wall = time.perf_counter() - t0
+    sysg.close()
+    return {"steps": steps, "mu": sysin.mu, "dt": sysin.dt, "sampled_every": every,
+            "rel_change": abs(e1 - e0) / abs(e0), "max_rel_deviation": dev / abs(e0),
+            "per_1000_steps_linear": abs(e1 - e0) / abs(e0) * 1000.0 / steps,
+            "wall_s": wall}
+
+
 def time_e2e(emd, torch, sysin, precision, steps):
     """Through the public API with host buffers: every step uploads orbitals
     (complex64, the precision the system keeps them in) and ions from pinned
     memory, propagates one MD step and reads back the orbitals, forces and
-    energy."""
+    energy.  Timed with CUDA events on the default stream (every call either
+    synchronises it or enqueues on it), with a per-phase breakdown and the
+    plain pinned-copy bandwidth of one orbital set each way for context."""
     import numpy as np
     s = sysin
     psi_pin = torch.empty(s.psi.shape, dtype=torch.complex64, pin_memory=True)
@@ -236,26 +265,59 @@ def time_e2e(emd, torch, sysin, precision, steps):
     h = emd.emd_init_system(emd.config_for(s, precision))
     psi_np = psi_pin.numpy()
     out_np = out_pin.numpy()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    phase = [0.0, 0.0, 0.0]
 
-    def one():
+    def one(record=False):
+        if record:
+            ev[0].record()
         emd.emd_set_ions(h, R, V)
         emd.emd_set_orbitals_c64(h, psi_np)
+        if record:
+            ev[1].record()
         emd.emd_propagate(h, 1, s.dt, s.mu)
+        if record:
+            ev[2].record()
         emd.emd_get_orbitals_c64(h, s.n_orb, s.n, out=out_np)
         emd.emd_get_forces(h, s.n_atoms)
         emd.emd_get_energy(h)
+        if record:
+            ev[3].record()
+            torch.cuda.synchronize()
+            for k in range(3):
+                phase[k] += ev[k].elapsed_time(ev[k + 1])
 
     one()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record()
     for _ in range(steps):
         one()
+    stop.record()
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    dt = start.elapsed_time(stop) * 1e-3
+    for _ in range(3):
+        one(record=True)
     emd.emd_destroy(h)
+    # plain pinned <-> device copies of one complex64 orbital set
+    dev = torch.empty_like(psi_pin, device="cuda")
+    bw = {}
+    for name, dst, src in (("h2d_GBps", dev, psi_pin), ("d2h_GBps", out_pin, dev)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        start.record()
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        stop.record()
+        torch.cuda.synchronize()
+        bw[name] = 3 * psi_np.nbytes / (start.elapsed_time(stop) * 1e-3) / 1e9
+    del dev
     bi = psi_np.nbytes + R.nbytes + V.nbytes
     bo = psi_np.nbytes + 3 * 8 * s.n_atoms + 9 * 8
-    return dt, bi, bo
+    breakdown = {"set_ms": phase[0] / 3, "propagate_ms": phase[1] / 3, "get_ms": phase[2] / 3}
+    breakdown.update(bw)
+    return dt, bi, bo, breakdown
 
 
 def time_batched(emd, torch, steps, n_replicas=32):
@@ -373,6 +435,7 @@ def time_large(emd, torch, steps, warmup):
     from paper_0812_2801_gb300 import inputs
     t0 = time.perf_counter()
     s = inputs.large_c160(device="cuda")
+    torch.cuda.empty_cache()          # the GEMMs' blocks: the system needs ~115 GB
     build_s = time.perf_counter() - t0
     h = emd.emd_init_system(emd.config_for(s, emd.EMD_FP32_ORBITALS))
     emd.emd_set_ions(h, s.R, s.V)
@@ -418,13 +481,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--batched-steps", type=int, default=12)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
-    ap.add_argument("--large-steps", type=int, default=0,
-                    help="also time the 160^3 / 1024-orbital workload (0: skip)")
+    ap.add_argument("--large-steps", type=int, default=4,
+                    help="timed steps of the 160^3 / 1024-orbital workload (0: skip; "
+                         "one GPU only: ~115 GB on the device, 33.5 GB of host input)")
+    ap.add_argument("--drift-steps", type=int, default=200,
+                    help="steps of the energy-drift run on the 96^3 workload (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -461,19 +527,33 @@ def main():
 
     # end to end through the C ABI with host buffers
     barrier()
-    e2e_dt, bi, bo = time_e2e(emd, torch, s, emd.EMD_FP32_ORBITALS, args.e2e_steps)
+    e2e_dt, bi, bo, e2e_parts = time_e2e(emd, torch, s, emd.EMD_FP32_ORBITALS, args.e2e_steps)
     e2e_dt = max_over_ranks(e2e_dt, device="cuda")
     e2e_val = whole_job_rate(upd_per_step * args.e2e_steps, ws, e2e_dt)
 
     batched = None if args.no_batched else time_batched(emd, torch, args.batched_steps)
     adjoint = None if (args.no_adjoint or ws > 1) else time_adjoint(emd, torch)
-    large = time_large(emd, torch, args.large_steps, 2) if args.large_steps > 0 else None
+    drift = (energy_drift(emd, torch, s, emd.EMD_FP32_ORBITALS, args.drift_steps)
+             if args.drift_steps > 0 and ws == 1 else None)
+    large = (time_large(emd, torch, args.large_steps, 1)
+             if args.large_steps > 0 and ws == 1 else None)
 
     peak, peak_kind = measured_peaks()
     stage_avg_s = r32["stage_ms"] * 1e-3 / max(1, r32["stage_launches"])
     bytes_launch = BYTES_PER_UPDATE["f32"] * s.n_orb * n3
     achieved = bytes_launch / stage_avg_s / 1e9
     stage64_s = r64["stage_ms"] * 1e-3 / max(1, r64["stage_launches"])
+    # FP64 stage: FP64 instructions per update of the stencil kernel at
+    # order p = 2M: 2 (w_0 u) + 12 M (5 + 5 adds and 2 FMAs per neighbour
+    # shell) + 2 (v_eff u) + 2 kappa (projector terms) + 2 (Taylor update),
+    # kappa = mean projectors per point = n_atoms (4/3) pi r_proj^3 / L^3
+    # (continuum estimate; 2.424 here, 2.4246 counted on the grid)
+    M = s.fd_order // 2
+    kappa = s.n_atoms * 4.0 / 3.0 * math.pi * s.species.r_proj ** 3 / s.L ** 3
+    f64_ops = 6 + 12 * M + 2 * kappa
+    f64_peak = 152 * 2 * 2.07e9 / 1e9           # G FP64 instructions/s (nominal)
+    f64_achieved = f64_ops * s.n_orb * n3 / stage64_s / 1e9
+    f64_hbm = BYTES_PER_UPDATE["f64"] * s.n_orb * n3 / stage64_s / 1e9
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -495,11 +575,21 @@ def main():
                      "avg_launch_ms": stage_avg_s * 1e3},
         "fp64": {"value": v64, "unit": UNIT, "ms_per_step": r64["ms"] / args.fp64_steps,
                  "horner_stage_avg_ms": stage64_s * 1e3,
-                 "speedup_fp32_over_fp64": value / ws / v64},
+                 "speedup_fp32_over_fp64": value / ws / v64,
+                 "roofline": {"bound": "alu", "unit": "G FP64 instructions/s",
+                              "achieved": f64_achieved, "peak": f64_peak,
+                              "frac": f64_achieved / f64_peak, "peak_kind": "nominal",
+                              "ops_per_update": f64_ops,
+                              "peak_note": "1.25 TFLOP/s nominal FP64 = 2 FP64 lanes x "
+                                           "152 SMs x 2.07 GHz (an FMA counts once)",
+                              "hbm_achieved_GBps": f64_hbm, "hbm_frac": f64_hbm / peak}},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bi,
-                "d2h_bytes_per_step": bo,
+                "d2h_bytes_per_step": bo, "steps": args.e2e_steps,
+                "ms_per_step": 1e3 * e2e_dt / args.e2e_steps, "breakdown": e2e_parts,
                 "note": "per step: set_ions + set_orbitals_c64 (pinned host, complex64), "
-                        "propagate 1 MD step, get_orbitals_c64 + get_forces + get_energy"},
+                        "propagate 1 MD step, get_orbitals_c64 + get_forces + get_energy; "
+                        "CUDA events"},
+        "drift": drift,
         "batched": batched,
         "adjoint": adjoint,
         "large": large,
