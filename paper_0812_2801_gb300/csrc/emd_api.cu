@@ -488,10 +488,12 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
   o.half_order = c.fd_order / 2;
   o.n_atoms = c.n_atoms;
   o.stage_variant = 0;
-  for (int k = 0; k <= EMD_MAX_HALF_ORDER; ++k) o.w[k] = 0.0;
+  for (int k = 0; k <= EMD_MAX_HALF_ORDER; ++k) o.w[k] = o.num[k] = 0.0;
   o.w[0] = -1.5 * fd_weight(c.fd_order, 0) / (c.h * c.h);
   for (int k = 1; k <= o.half_order; ++k)
     o.w[k] = -0.5 * fd_weight(c.fd_order, k) / (c.h * c.h);
+  for (int k = 0; k <= o.half_order; ++k) o.num[k] = fd_num(c.fd_order, k);
+  o.den = fd_den(c.fd_order);
 
   const size_t n3 = s->g.n3;
   const size_t esz = c.precision == EMD_FP64 ? sizeof(double2) : sizeof(float2);
@@ -549,6 +551,8 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
     t.te_off = nullptr;
     t.te_pp = nullptr;
     t.te_q = nullptr;
+    t.pt4d = nullptr;
+    if (c.precision == EMD_FP64 && o.bo == 2) TRY(A((void **)&t.pt4d, n3 * 3 * sizeof(int4)));
     if (c.precision == EMD_FP32_ORBITALS) {
       TRY(A((void **)&t.te_off, (size_t)ntiles * (EMD_TILE_ATOM_MAX + 1) * 4));
       TRY(A((void **)&t.te_pp, (size_t)ntiles * EMD_TE_CAP * sizeof(uint2)));

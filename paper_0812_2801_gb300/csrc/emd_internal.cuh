@@ -59,6 +59,11 @@ struct TableSet {
   float *pt_pf;     // [EMD_PT_KMAX][n3] the same in FP32 (complex64 path)
   int2 *pt4;        // [n3][4] first four (atom, FP32 p bits) per point, unused
                     // slots (0, 0.0f); entry 0's atom carries count << 16
+  // complex128, bo = 2 (double-float stage): per point 3 x int4 = (J_0 |
+  // count << 16, J_1, J_2, J_3), (p_0 hi, p_0 lo, p_1 hi, p_1 lo), (p_2 hi,
+  // p_2 lo, p_3 hi, p_3 lo) with p in double-float (unused entries 0);
+  // NULL for other layouts
+  int4 *pt4d;
   int *at_cnt;      // [n_atoms]
   int *split_cnt;   // [n_atoms][EMD_SPLIT] hits per range (table building)
   int *at_pt;       // [n_atoms][cap] flat grid index
@@ -88,6 +93,29 @@ struct TableSet {
   double *v_loc;    // [n3] Poisson(-g_ion)
   int cap;
 };
+
+// ---------------------------------------------------------------------------
+// Double-float split of a double by integer operations on its bits:
+// x = hi + lo, hi = x truncated to 24 significant bits, lo = x - hi rounded to
+// 24 bits (|x - hi - lo| <= 2^-47 |x|).  |x| < 2^-126 gives (0, 0), and lo is
+// dropped below |x| < 2^-74 (an absolute error under 1e-29).  Branch-free:
+// the out-of-range cases are selected away.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 emd_df_split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned h = (unsigned)(b >> 32), l = (unsigned)b;
+  const unsigned e = (h >> 20) & 0x7ffu;
+  const unsigned s = h & 0x80000000u;
+  const float hi = __uint_as_float(s | ((e - 896u) << 23) | ((h & 0xfffffu) << 3) | (l >> 29));
+  // the remaining 29 bits r = r1 2^23 + r0 carry weight 2^(e - 1075); r1 and
+  // r0 become exact floats through the 2^23 exponent trick
+  const float f1 = __fsub_rn(__uint_as_float(0x4b000000u | ((l >> 23) & 0x3fu)), 8388608.f);
+  const float f0 = __fsub_rn(__uint_as_float(0x4b000000u | (l & 0x7fffffu)), 8388608.f);
+  const float s1 = __uint_as_float(s | ((e - 925u) << 23));
+  const float s0 = __uint_as_float(s | ((e - 948u) << 23));
+  const float lo = __fmaf_rn(f1, s1, __fmul_rn(f0, s0));
+  return make_float2(e >= 897u ? hi : 0.f, e >= 949u ? lo : 0.f);
+}
 
 // ---------------------------------------------------------------------------
 // Exact displacement arithmetic.  The support decision d^2 < r^2 is an
@@ -235,9 +263,12 @@ struct StageArgs {
 };
 struct OrbLayout {
   int n, n3, bo, n_blk, n_orb, n_orb_pad, prec, half_order, n_atoms;
-  int stage_variant;   // complex64 stage kernel (EMD_OPT_STAGE_VARIANT)
+  int stage_variant;   // Horner-stage kernel (EMD_OPT_STAGE_VARIANT)
   double h;
   double w[EMD_MAX_HALF_ORDER + 1];   // w_0 = -3 c_0 / (2 h^2), w_k = -c_k/(2 h^2)
+  // the same stencil as integers over a common denominator: c_k = num_k / den
+  // (the double-float FP64 stage accumulates with these, exact in FP32)
+  double num[EMD_MAX_HALF_ORDER + 1], den;
 };
 void emd_launch_stage(const OrbLayout &o, const StageArgs &a, cudaStream_t st);
 void emd_launch_project(const OrbLayout &o, const TableSet &t, int n_atoms,

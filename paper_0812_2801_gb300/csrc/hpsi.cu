@@ -1241,6 +1241,306 @@ k_abs2_sum(const double2 *c, int n, double *out) {
   if (threadIdx.x == 0) *out = acc[0];
 }
 
+// ---------------------------------------------------------------------------
+// FP64 Horner stage in double-float arithmetic (complex128 orbitals, bo = 2).
+// GB300 issues one FP64 warp instruction per 16 SM cycles, and the plain FP64
+// stage spends ~59 FP64 instructions per update.  Here every value of a
+// staged plane is split once into two floats, x = hi + lo (hi: the top 24
+// significand bits, lo: the rest rounded to 24 bits; 48 bits in all), by
+// integer operations on its bits, and the stencil runs on the FP32 pipes:
+// products by the integer FD numerators num_k (exact in FP32) through
+// TwoProduct with an FMA, sums through Knuth's TwoSum, the rounding errors
+// gathered in the low word.  The accumulated K = dv u + sum_k num_k S_k,
+// dv = 3 num_0 - 2 h^2 den v_eff, gives H u = -K / (2 h^2 den) + V_nl u; only
+// the conversion of H u back to double and the Taylor update use FP64
+// instructions (four per update).  The tile marches through z like the
+// complex64 column kernels; each thread owns one orbital of one point, the
+// z-direction accumulates in a (2M+1)-slot shift register, and planes are
+// staged through registers (load, split, store) one plane ahead.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 df_split(double x) { return emd_df_split(x); }
+
+// exact widening of a float (normal or zero; float subnormals, below 2^-126,
+// become 0) by integer operations
+__device__ __forceinline__ double df_widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  const unsigned hw = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  const double d = __hiloint2double((int)hw, (int)(u << 29));
+  return ex == 0u ? 0.0 : d;
+}
+
+// Double-float pairs for a complex value, packed so that both components go
+// through one FP32x2 instruction: hi = (re_hi, im_hi), lo = (re_lo, im_lo);
+// the packed operations round each lane as the scalar ones would.
+__device__ __forceinline__ float2 f2neg_sub(float2 a, float2 b) {   // a - b
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+// Knuth's TwoSum, per lane: s + e = a + b exactly
+__device__ __forceinline__ void dfp_two_sum(float2 a, float2 b, float2 &s, float2 &e) {
+  s = __fadd2_rn(a, b);
+  const float2 bb = f2neg_sub(s, a);
+  e = __fadd2_rn(f2neg_sub(a, f2neg_sub(s, bb)), f2neg_sub(b, bb));
+}
+// (hi, lo) += (p, q), p the leading part
+__device__ __forceinline__ void dfp_add(float2 &hi, float2 &lo, float2 p, float2 q) {
+  float2 s, e;
+  dfp_two_sum(hi, p, s, e);
+  hi = s;
+  lo = __fadd2_rn(lo, __fadd2_rn(e, q));
+}
+// TwoProduct of a scalar pair (w, w) and x, per lane: p + pe = w x exactly
+__device__ __forceinline__ void dfp_two_prod(float2 w, float2 x, float2 &p, float2 &pe) {
+  p = __fmul2_rn(w, x);
+  pe = __ffma2_rn(w, x, __fmul2_rn(make_float2(-w.x, -w.y), x));
+}
+// (hi, lo) += (wh + wl)(xh + xl) for a real double-float w, dropping wl xl
+__device__ __forceinline__ void dfp_add_prod(float2 &hi, float2 &lo, float wh, float wl,
+                                             float2 xh, float2 xl) {
+  const float2 w2 = make_float2(wh, wh);
+  float2 p, pe;
+  dfp_two_prod(w2, xh, p, pe);
+  dfp_add(hi, lo, p, __ffma2_rn(w2, xl, __ffma2_rn(make_float2(wl, wl), xh, pe)));
+}
+
+// a complex double-float: (re_hi, im_hi, re_lo, im_lo)
+__device__ __forceinline__ float4 df_split2(double2 v) {
+  const float2 r = df_split(v.x), i = df_split(v.y);
+  return make_float4(r.x, i.x, r.y, i.y);
+}
+__device__ __forceinline__ float2 f4hi(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 f4lo(float4 v) { return make_float2(v.z, v.w); }
+
+struct DFWeights {
+  float num[EMD_MAX_HALF_ORDER + 1];   // FD numerators, exact in FP32
+  float sk_hi, sk_lo;                  // -1 / (2 h^2 den) as double-float
+  double dvs, dv0;                     // dv = dv0 + dvs v_eff
+};
+
+template <int M> struct DFTile {
+  static constexpr int BO = 2;
+  static constexpr int NC = 64;                 // orbital columns = threads in x
+  static constexpr int TX = NC / BO;            // points per tile row
+  static constexpr int NT = 512;
+  static constexpr int TY = NT / NC;            // rows, one per thread row
+  static constexpr int SW = TX + 2 * M, SH = TY + 2 * M;
+  static constexpr int NCH = SH * SW * BO;      // complex values per staged plane
+  static constexpr int CPT = (NCH + NT - 1) / NT;
+  static constexpr int NV = TX * TY;            // tile points
+  static constexpr int NS = 2 * M + 1;          // shift-register slots
+  // raw slot (3, cp.async, two planes ahead): plane as complex128 | v_eff of
+  // the tile points | records and psi0 of the output plane completed by it
+  static constexpr int RU = NCH * 16, RV = NV * 8, RQ = NV * 48, RP = NV * BO * 16;
+  static constexpr int RSLOT = RU + RV + RQ + RP;
+  // split slot (2): plane as double-float complex | dv of the tile points
+  static constexpr int DU = NCH * 16, DD = NV * 8;
+  static constexpr int DSLOT = DU + DD;
+  static constexpr size_t SMEM_FIXED = 3 * (size_t)RSLOT + 2 * (size_t)DSLOT;
+};
+
+template <int M, bool HCS>
+__global__ void __launch_bounds__(512, 1)
+k_stage_df(const double2 *__restrict__ u_in, const double2 *__restrict__ psi0,
+           double2 *__restrict__ u_out, const double *__restrict__ v_eff,
+           const int4 *__restrict__ pt4d, const int *__restrict__ pt_J,
+           const double *__restrict__ pt_p, const double2 *__restrict__ hc, int n,
+           int ntx, int zc, int n_orb_pad, int n_atoms, double a, int apply_only,
+           DFWeights W) {
+  typedef DFTile<M> Z;
+  constexpr int BO = Z::BO, NS = Z::NS, SW = Z::SW, NT = Z::NT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  unsigned char *dfbase = smraw + 3 * Z::RSLOT;
+  float4 *hcs = reinterpret_cast<float4 *>(smraw + Z::SMEM_FIXED);
+  const int tid = threadIdx.x;
+  const int col = tid % Z::NC, tyr = tid / Z::NC;
+  const int xl = col / BO, j = col % BO;
+  const int tx0 = (blockIdx.x % ntx) * Z::TX, ty0 = (blockIdx.x / ntx) * Z::TY;
+  const int z0 = blockIdx.y * zc;
+  const int zcount = min(zc, n - z0);
+  const int total = zcount + 2 * M;
+  const int n2 = n * n;
+  const size_t n3 = (size_t)n2 * n;
+  const size_t boff = (size_t)blockIdx.z * n3 * BO;
+  const double2 *ub = u_in + boff;
+  const double2 *pb = psi0 + boff;
+  double2 *ob = u_out + boff;
+  const int x = tx0 + xl, y = ty0 + tyr;
+  const bool valid = x < n && y < n;
+  const size_t pxy = (size_t)min(y, n - 1) * n + min(x, n - 1);
+
+  // staging map of the plane values: source index within a plane, -1 = none
+  int src[Z::CPT];
+#pragma unroll
+  for (int i = 0; i < Z::CPT; ++i) {
+    const int q = tid + i * NT;
+    src[i] = -1;
+    if (q < Z::NCH) {
+      const int jj = q % BO, pnt = q / BO;
+      const int c = pnt % SW, rr = pnt / SW;
+      const int xx = (tx0 - M + c + 2 * n) % n;
+      const int yy = (ty0 - M + rr + 2 * n) % n;
+      src[i] = (yy * n + xx) * BO + jj;
+    }
+  }
+  // tile point of this thread in the per-point stagings (v_eff, records)
+  const int vp = tid < Z::NV ? min(ty0 + tid / Z::TX, n - 1) * n + min(tx0 + tid % Z::TX, n - 1)
+                             : -1;
+  if (HCS) {
+    for (int i = tid; i < n_atoms * BO; i += NT)
+      hcs[i] = df_split2(hc[(size_t)(i / BO) * n_orb_pad + (size_t)blockIdx.z * BO + i % BO]);
+  }
+  const unsigned sm0 = (unsigned)__cvta_generic_to_shared(smraw);
+
+  auto issue = [&](int zi) {
+    const unsigned base = sm0 + (zi % 3) * Z::RSLOT;
+    int zz = z0 - M + zi;
+    zz += zz < 0 ? n : 0;
+    zz -= zz >= n ? n : 0;
+    const size_t poff = (size_t)zz * n2;
+#pragma unroll
+    for (int i = 0; i < Z::CPT; ++i)
+      if (src[i] >= 0)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + (tid + i * NT) * 16),
+                     "l"(ub + poff * BO + src[i]) : "memory");
+    if (vp >= 0)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(base + Z::RU + tid * 8),
+                   "l"(v_eff + poff + vp) : "memory");
+    if (zi >= 2 * M && vp >= 0) {
+      const size_t po = (size_t)(z0 + zi - 2 * M) * n2 + vp;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                         base + Z::RU + Z::RV + (tid * 3 + k) * 16),
+                     "l"(pt4d + po * 3 + k) : "memory");
+      if (!apply_only) {
+#pragma unroll
+        for (int jj = 0; jj < BO; ++jj)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                           base + Z::RU + Z::RV + Z::RQ + (tid * BO + jj) * 16),
+                       "l"(pb + po * BO + jj) : "memory");
+      }
+    }
+    cp_async_commit();
+  };
+  // split the raw plane zi into double-float slot zi & 1
+  auto convert = [&](int zi) {
+    const unsigned char *raw = smraw + (zi % 3) * Z::RSLOT;
+    unsigned char *dst = dfbase + (zi & 1) * Z::DSLOT;
+    const double2 *R = reinterpret_cast<const double2 *>(raw);
+    float4 *D = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+    for (int i = 0; i < Z::CPT; ++i)
+      if (src[i] >= 0) D[tid + i * NT] = df_split2(R[tid + i * NT]);
+    if (vp >= 0)
+      reinterpret_cast<float2 *>(dst + Z::DU)[tid] =
+          df_split(__fma_rn(W.dvs, reinterpret_cast<const double *>(raw + Z::RU)[tid], W.dv0));
+  };
+
+  // ah, al [s]: output plane zi - M + s, K as hi = (re, im), lo = (re, im)
+  float2 ah[NS], al[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) ah[s] = al[s] = make_float2(0.f, 0.f);
+  const int ci = ((tyr + M) * SW + xl + M) * BO + j;       // centre, float4 index
+  const int pt = tyr * Z::TX + xl;                         // tile point index
+  const char *hcj = reinterpret_cast<const char *>(hcs + j);
+  const double2 *hcg = hc + (size_t)blockIdx.z * BO + j;
+
+  issue(0);
+  if (total > 1) issue(1);
+  if (total > 1) cp_async_wait<1>();
+  else cp_async_wait<0>();
+  __syncthreads();
+  convert(0);
+  for (int zi = 0; zi < total; ++zi) {
+    // raw plane zi + 1 (issued one iteration ago) is the only group in flight
+    cp_async_wait<0>();
+    // one barrier: raw zi + 1 visible; split zi (converted last iteration)
+    // visible; every thread has finished iteration zi - 1, so split slot
+    // (zi + 1) & 1 and raw slot (zi + 2) % 3 are free
+    __syncthreads();
+    if (zi + 2 < total) issue(zi + 2);
+    if (zi + 1 < total) convert(zi + 1);
+    const unsigned char *base = dfbase + (zi & 1) * Z::DSLOT;
+    const float4 *P = reinterpret_cast<const float4 *>(base) + ci;
+    const float2 d = reinterpret_cast<const float2 *>(base + Z::DU)[pt];
+    const float4 c = P[0];
+    const float2 ch = f4hi(c), cl = f4lo(c);
+    // own plane: dv u + the x/y shells
+    dfp_add_prod(ah[M], al[M], d.x, d.y, ch, cl);
+#pragma unroll
+    for (int k = 1; k <= M; ++k) {
+      const float4 v1 = P[k * BO], v2 = P[-k * BO], v3 = P[k * SW * BO], v4 = P[-k * SW * BO];
+      float2 sh = f4hi(v1), sl = f4lo(v1);
+      dfp_add(sh, sl, f4hi(v2), f4lo(v2));
+      dfp_add(sh, sl, f4hi(v3), f4lo(v3));
+      dfp_add(sh, sl, f4hi(v4), f4lo(v4));
+      const float2 w2 = make_float2(W.num[k], W.num[k]);
+      float2 p, pe;
+      dfp_two_prod(w2, sh, p, pe);
+      dfp_add(ah[M], al[M], p, __ffma2_rn(w2, sl, pe));
+    }
+    // z-direction: this plane is neighbour k of output planes zi +- k
+#pragma unroll
+    for (int k = 1; k <= M; ++k) {
+      const float2 w2 = make_float2(W.num[k], W.num[k]);
+      float2 p, pe;
+      dfp_two_prod(w2, ch, p, pe);
+      const float2 q = __ffma2_rn(w2, cl, pe);
+      dfp_add(ah[M + k], al[M + k], p, q);
+      if (zi >= k) dfp_add(ah[M - k], al[M - k], p, q);
+    }
+    if (zi >= 2 * M && valid) {   // output plane z0 + zi - 2M is complete in slot 0
+      const unsigned char *raw = smraw + (zi % 3) * Z::RSLOT;
+      const int4 *Q = reinterpret_cast<const int4 *>(raw + Z::RU + Z::RV) + pt * 3;
+      const int4 q0 = Q[0], q1 = Q[1], q2 = Q[2];
+      float2 hh = make_float2(0.f, 0.f), hl = make_float2(0.f, 0.f);
+      dfp_add_prod(hh, hl, W.sk_hi, W.sk_lo, ah[0], al[0]);
+      // four entries (unused ones have p = 0 and add exactly zero)
+      const int Je[4] = {q0.x & 0xffff, q0.y, q0.z, q0.w};
+      const float ph[4] = {__int_as_float(q1.x), __int_as_float(q1.z), __int_as_float(q2.x),
+                           __int_as_float(q2.z)};
+      const float pl[4] = {__int_as_float(q1.y), __int_as_float(q1.w), __int_as_float(q2.y),
+                           __int_as_float(q2.w)};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float4 h4 = HCS ? *reinterpret_cast<const float4 *>(hcj + Je[e] * (BO * 16))
+                              : df_split2(hcg[(size_t)Je[e] * n_orb_pad]);
+        dfp_add_prod(hh, hl, ph[e], pl[e], f4hi(h4), f4lo(h4));
+      }
+      const int cnt = q0.x >> 16;
+      if (cnt > 4) {
+        const size_t p = (size_t)(z0 + zi - 2 * M) * n2 + pxy;
+        for (int e = 4; e < cnt; ++e) {
+          const int J = pt_J[(size_t)e * n3 + p];
+          const float2 pv = df_split(pt_p[(size_t)e * n3 + p]);
+          const float4 h4 = HCS ? *reinterpret_cast<const float4 *>(hcj + J * (BO * 16))
+                                : df_split2(hcg[(size_t)J * n_orb_pad]);
+          dfp_add_prod(hh, hl, pv.x, pv.y, f4hi(h4), f4lo(h4));
+        }
+      }
+      const double Hr = __dadd_rn(df_widen(hh.x), df_widen(hl.x));
+      const double Hi = __dadd_rn(df_widen(hh.y), df_widen(hl.y));
+      double2 out;
+      if (apply_only) {
+        out = make_double2(Hr, Hi);
+      } else {
+        const double2 sv =
+            reinterpret_cast<const double2 *>(raw + Z::RU + Z::RV + Z::RQ)[pt * BO + j];
+        out.x = __fma_rn(a, Hi, sv.x);
+        out.y = __fma_rn(-a, Hr, sv.y);
+      }
+      ob[((size_t)(z0 + zi - 2 * M) * n2 + pxy) * BO + j] = out;
+    }
+    // shift the register line: output plane zi - M + 1 moves to slot 0
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) {
+      ah[s] = ah[s + 1];
+      al[s] = al[s + 1];
+    }
+    ah[NS - 1] = al[NS - 1] = make_float2(0.f, 0.f);
+  }
+}
+
 // ---- dispatch -------------------------------------------------------------
 
 template <typename T, int BO, int M>
@@ -1364,6 +1664,52 @@ void stage_z_m(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
   }
 }
 
+template <int M, bool HCS>
+void stage_df_tt(const OrbLayout &o, const StageArgs &a, size_t smem, cudaStream_t st) {
+  typedef DFTile<M> Z;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_stage_df<M, HCS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(Z::SMEM_FIXED + 32768));
+    attr_done = true;
+  }
+  const int ntx = (o.n + Z::TX - 1) / Z::TX, nty = (o.n + Z::TY - 1) / Z::TY;
+  const int cols = ntx * nty * o.n_blk;
+  const int nz = std::max(1, std::min((2 * 152 + cols - 1) / cols, o.n / 16));
+  const int zc = (o.n + nz - 1) / nz;
+  DFWeights W;
+  for (int k = 0; k <= EMD_MAX_HALF_ORDER; ++k) W.num[k] = (float)o.num[k];
+  const double sk = -1.0 / (2.0 * o.h * o.h * o.den);
+  W.sk_hi = (float)sk;
+  W.sk_lo = (float)(sk - (double)W.sk_hi);
+  W.dvs = -2.0 * o.h * o.h * o.den;
+  W.dv0 = 3.0 * o.num[0];
+  dim3 grid(ntx * nty, (o.n + zc - 1) / zc, o.n_blk);
+  k_stage_df<M, HCS><<<grid, Z::NT, smem, st>>>(
+      (const double2 *)a.u_in, (const double2 *)a.psi0, (double2 *)a.u_out,
+      (const double *)a.v_eff, a.tab->pt4d, a.tab->pt_J, a.tab->pt_p,
+      (const double2 *)a.hc, o.n, ntx, zc, o.n_orb_pad, o.n_atoms, a.a, a.apply_only, W);
+}
+
+template <int M>
+void stage_df_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
+  typedef DFTile<M> Z;
+  const int hc_bytes = o.n_atoms * Z::BO * (int)sizeof(float4);
+  if (hc_bytes <= 32768)
+    stage_df_tt<M, true>(o, a, Z::SMEM_FIXED + hc_bytes, st);
+  else
+    stage_df_tt<M, false>(o, a, Z::SMEM_FIXED, st);
+}
+
+inline void stage_df_m(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
+  switch (o.half_order) {
+    case 1: stage_df_t<1>(o, a, st); break;
+    case 2: stage_df_t<2>(o, a, st); break;
+    case 3: stage_df_t<3>(o, a, st); break;
+    case 4: stage_df_t<4>(o, a, st); break;
+  }
+}
+
 template <typename T, int BO>
 void stage_m(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
   switch (o.half_order) {
@@ -1466,7 +1812,10 @@ void emd_launch_stage(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
   if (o.prec == EMD_FP64) {
     switch (o.bo) {
       case 1: stage_m<double, 1>(o, a, st); break;
-      case 2: stage_m<double, 2>(o, a, st); break;
+      case 2:
+        if (o.stage_variant == 1 || !a.tab->pt4d) stage_m<double, 2>(o, a, st);
+        else stage_df_m(o, a, st);
+        break;
       case 4: stage_m<double, 4>(o, a, st); break;
     }
   } else {

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(512)
 k_point_table(int n, int n3, double h, double L, const double *Rw,
               SpeciesDev sp, float margin, const int *tile_cnt, const int *tile_ent,
               const double *gtab, const int *glo,
-              int *pt_cnt, int *pt_J, double *pt_p, float *pt_pf, int2 *pt4,
+              int *pt_cnt, int *pt_J, double *pt_p, float *pt_pf, int2 *pt4, int4 *pt4d,
               double *g_ion, int *te_off, uint2 *te_pp, float4 *te_q, int *err) {
   __shared__ int cand[EMD_TILE_CAND_MAX];
   __shared__ float cfs[EMD_TILE_CAND_MAX][3];
@@ -318,6 +318,20 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
     if (e < cnt) q = make_int2(pt_J[e * n3 + p], __float_as_int(pt_pf[e * n3 + p]));
     if (e == 0) q.x |= cnt << 16;
     pt4[(size_t)p * 4 + e] = q;
+  }
+  if (pt4d) {
+    int J[4];
+    float2 pv[4];
+    for (int e = 0; e < 4; ++e) {
+      J[e] = e < cnt ? pt_J[e * n3 + p] : 0;
+      pv[e] = e < cnt ? emd_df_split(pt_p[e * n3 + p]) : make_float2(0.f, 0.f);
+    }
+    int4 *r = pt4d + (size_t)p * 3;
+    r[0] = make_int4(J[0] | (cnt << 16), J[1], J[2], J[3]);
+    r[1] = make_int4(__float_as_int(pv[0].x), __float_as_int(pv[0].y), __float_as_int(pv[1].x),
+                     __float_as_int(pv[1].y));
+    r[2] = make_int4(__float_as_int(pv[2].x), __float_as_int(pv[2].y), __float_as_int(pv[3].x),
+                     __float_as_int(pv[3].y));
   }
 }
 
@@ -767,13 +781,13 @@ void emd_launch_tables(const GridInfo &g, const SpeciesDev &sp, int n_atoms,
   if (t.te_off)
     k_point_table<true><<<ntiles, 512, 0, st>>>(g.n, g.n3, g.h, g.L, t.Rw, sp, margin_pt,
                                                 t.tile_cnt, t.tile_ent, t.gtab, t.glo,
-                                                t.pt_cnt, t.pt_J, t.pt_p, t.pt_pf, t.pt4,
+                                                t.pt_cnt, t.pt_J, t.pt_p, t.pt_pf, t.pt4, t.pt4d,
                                                 t.g_ion, t.te_off, t.te_pp, t.te_q,
                                                 err);
   else
     k_point_table<false><<<ntiles, 512, 0, st>>>(g.n, g.n3, g.h, g.L, t.Rw, sp, margin_pt,
                                                  t.tile_cnt, t.tile_ent, t.gtab, t.glo,
-                                                 t.pt_cnt, t.pt_J, t.pt_p, t.pt_pf, t.pt4,
+                                                 t.pt_cnt, t.pt_J, t.pt_p, t.pt_pf, t.pt4, t.pt4d,
                                                  t.g_ion, t.te_off, t.te_pp, t.te_q,
                                                  err);
   if (n_atoms > 0 && !t.te_off) {
