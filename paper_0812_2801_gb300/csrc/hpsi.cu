@@ -1541,6 +1541,107 @@ k_stage_df(const double2 *__restrict__ u_in, const double2 *__restrict__ psi0,
   }
 }
 
+// complex128 projections and nonlocal-force moments (bo = 2) in double-float
+// arithmetic on the FP32 pipes: the FP64 forms spend 2 (projection) and 8
+// (moments) FP64 instructions per table entry and orbital, which bounds them
+// by GB300's FP64 rate.  Each thread accumulates its entries as (hi, lo)
+// pairs (TwoProduct and TwoSum, real and imaginary parts packed), widens the
+// sums to FP64 once and joins the fixed-tree FP64 block sum of the FP64
+// kernels.
+__global__ void __launch_bounds__(256)
+k_project_df(const double2 *__restrict__ u, size_t n3, const int *__restrict__ at_cnt,
+             const int *__restrict__ at_pt, const double *__restrict__ at_p, int cap, double h3,
+             double h_kb, int n_orb_pad, double2 *c, double2 *hc) {
+  constexpr int BO = 2;
+  __shared__ double red[8 * 2 * BO];
+  const int J = blockIdx.x, blk = blockIdx.y;
+  const int cnt = at_cnt[J];
+  const double2 *ub = u + (size_t)blk * n3 * BO;
+  float2 ah[BO], al[BO];
+#pragma unroll
+  for (int j = 0; j < BO; ++j) ah[j] = al[j] = make_float2(0.f, 0.f);
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const size_t idx = (size_t)J * cap + e;
+    const int pt = at_pt[idx];
+    const float2 pv = df_split(at_p[idx]);
+#pragma unroll
+    for (int j = 0; j < BO; ++j) {
+      const float4 v = df_split2(ub[(size_t)pt * BO + j]);
+      dfp_add_prod(ah[j], al[j], pv.x, pv.y, f4hi(v), f4lo(v));
+    }
+  }
+  double acc[2 * BO];
+#pragma unroll
+  for (int j = 0; j < BO; ++j) {
+    acc[2 * j] = __dadd_rn(df_widen(ah[j].x), df_widen(al[j].x));
+    acc[2 * j + 1] = __dadd_rn(df_widen(ah[j].y), df_widen(al[j].y));
+  }
+  emd_block_sum<2 * BO>(acc, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < BO; ++j) {
+      const size_t o = (size_t)J * n_orb_pad + (size_t)blk * BO + j;
+      const double re = h3 * acc[2 * j], im = h3 * acc[2 * j + 1];
+      c[o] = make_double2(re, im);
+      hc[o] = make_double2(h_kb * re, h_kb * im);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_nl_force_df(const double2 *__restrict__ u, size_t n3, int n_blk,
+              const int *__restrict__ at_cnt, const int *__restrict__ at_pt,
+              const double *__restrict__ at_p, const double *__restrict__ at_d, int cap,
+              const double2 *__restrict__ c, int n_orb_pad, int n_orb, double h3, double coef,
+              double inv_rc2, double *part) {
+  constexpr int BO = 2;
+  __shared__ double red[8 * 6 * BO];
+  const int J = blockIdx.x, blk = blockIdx.y;
+  const int cnt = at_cnt[J];
+  const double2 *ub = u + (size_t)blk * n3 * BO;
+  float2 ah[3 * BO], al[3 * BO];      // [orbital][axis] complex moments
+#pragma unroll
+  for (int k = 0; k < 3 * BO; ++k) ah[k] = al[k] = make_float2(0.f, 0.f);
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const size_t idx = (size_t)J * cap + e;
+    const int pt = at_pt[idx];
+    const double pw = at_p[idx] * inv_rc2;
+    float2 dd[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dd[a] = df_split(pw * at_d[3 * idx + a]);
+#pragma unroll
+    for (int j = 0; j < BO; ++j) {
+      const float4 v = df_split2(ub[(size_t)pt * BO + j]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        dfp_add_prod(ah[3 * j + a], al[3 * j + a], dd[a].x, dd[a].y, f4hi(v), f4lo(v));
+    }
+  }
+  double acc[6 * BO];
+#pragma unroll
+  for (int j = 0; j < BO; ++j)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      acc[6 * j + 2 * a] = __dadd_rn(df_widen(ah[3 * j + a].x), df_widen(al[3 * j + a].x));
+      acc[6 * j + 2 * a + 1] = __dadd_rn(df_widen(ah[3 * j + a].y), df_widen(al[3 * j + a].y));
+    }
+  emd_block_sum<6 * BO>(acc, red);
+  if (threadIdx.x == 0) {
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < BO; ++j) {
+      const int A = blk * BO + j;
+      if (A >= n_orb) continue;
+      const double2 cj = c[(size_t)J * n_orb_pad + A];
+      for (int a = 0; a < 3; ++a) {
+        const double dr = h3 * acc[6 * j + 2 * a], di = h3 * acc[6 * j + 2 * a + 1];
+        f[a] += cj.x * dr + cj.y * di;   // Re(conj(c) dc)
+      }
+    }
+    for (int a = 0; a < 3; ++a)
+      part[((size_t)J * n_blk + blk) * 3 + a] = coef * f[a];
+  }
+}
+
 // ---- dispatch -------------------------------------------------------------
 
 template <typename T, int BO, int M>
@@ -1733,6 +1834,10 @@ void project_t(const OrbLayout &o, const TableSet &t, int n_atoms,
                cudaStream_t st) {
   typedef typename cplx<T>::type V;
   dim3 grid(n_atoms, o.n_blk);
+  if (sizeof(T) == 8 && BO == 2)
+    k_project_df<<<grid, 256, 0, st>>>((const double2 *)u, (size_t)o.n3, t.at_cnt, t.at_pt,
+                                       t.at_p, t.cap, h3, h_kb, o.n_orb_pad, c, (double2 *)hc);
+  else
     k_project<T, BO><<<grid, 256, 0, st>>>((const V *)u, (size_t)o.n3, t.at_cnt,
                                            t.at_pt, t.at_p, t.cap, h3, h_kb,
                                            o.n_orb_pad, c, (V *)hc);
@@ -1775,6 +1880,11 @@ void nlf_t(const OrbLayout &o, const TableSet &t, int n_atoms, const void *u,
            double *part, cudaStream_t st) {
   typedef typename cplx<T>::type V;
   dim3 grid(n_atoms, o.n_blk);
+  if (sizeof(T) == 8 && BO == 2)
+    k_nl_force_df<<<grid, 256, 0, st>>>((const double2 *)u, (size_t)o.n3, o.n_blk, t.at_cnt,
+                                        t.at_pt, t.at_p, t.at_d, t.cap, c, o.n_orb_pad,
+                                        o.n_orb, h3, coef, inv_rc2, part);
+  else
     k_nl_force<T, BO><<<grid, 256, 0, st>>>((const V *)u, (size_t)o.n3, o.n_blk,
                                             t.at_cnt, t.at_pt, t.at_p, t.at_d,
                                             t.cap, c, o.n_orb_pad, o.n_orb, h3,
