@@ -543,16 +543,18 @@ def main():
     bytes_launch = BYTES_PER_UPDATE["f32"] * s.n_orb * n3
     achieved = bytes_launch / stage_avg_s / 1e9
     stage64_s = r64["stage_ms"] * 1e-3 / max(1, r64["stage_launches"])
-    # FP64 stage: FP64 instructions per update of the stencil kernel at
-    # order p = 2M: 2 (w_0 u) + 12 M (5 + 5 adds and 2 FMAs per neighbour
-    # shell) + 2 (v_eff u) + 2 kappa (projector terms) + 2 (Taylor update),
-    # kappa = mean projectors per point = n_atoms (4/3) pi r_proj^3 / L^3
-    # (continuum estimate; 2.424 here, 2.4246 counted on the grid)
+    # FP64 form's stage: double-float arithmetic on the FP32 pipes, real and
+    # imaginary parts in one FP32x2 instruction.  Packed operations per
+    # update (one orbital at one point): dv u 13, each x/y shell 36 (three
+    # double-float adds of the four neighbours, the weight's TwoProduct and
+    # one add), each z shell 20 (TwoProduct, two adds into the delay line),
+    # the epilogue 65 (the scale and four projector entries): 78 + 56 M,
+    # i.e. 2 (78 + 56 M) FP32 lane operations.  Peak: 128 FP32 lanes x 152
+    # SMs x 2.07 GHz (an FMA counts once).
     M = s.fd_order // 2
-    kappa = s.n_atoms * 4.0 / 3.0 * math.pi * s.species.r_proj ** 3 / s.L ** 3
-    f64_ops = 6 + 12 * M + 2 * kappa
-    f64_peak = 152 * 2 * 2.07e9 / 1e9           # G FP64 instructions/s (nominal)
-    f64_achieved = f64_ops * s.n_orb * n3 / stage64_s / 1e9
+    df_ops = 2.0 * (78 + 56 * M)
+    f32_peak = 128 * 152 * 2.07e9 / 1e12          # T FP32 lane operations/s
+    df_achieved = df_ops * s.n_orb * n3 / stage64_s / 1e12
     f64_hbm = BYTES_PER_UPDATE["f64"] * s.n_orb * n3 / stage64_s / 1e9
 
     line = {
@@ -576,12 +578,14 @@ def main():
         "fp64": {"value": v64, "unit": UNIT, "ms_per_step": r64["ms"] / args.fp64_steps,
                  "horner_stage_avg_ms": stage64_s * 1e3,
                  "speedup_fp32_over_fp64": value / ws / v64,
-                 "roofline": {"bound": "alu", "unit": "G FP64 instructions/s",
-                              "achieved": f64_achieved, "peak": f64_peak,
-                              "frac": f64_achieved / f64_peak, "peak_kind": "nominal",
-                              "ops_per_update": f64_ops,
-                              "peak_note": "1.25 TFLOP/s nominal FP64 = 2 FP64 lanes x "
-                                           "152 SMs x 2.07 GHz (an FMA counts once)",
+                 "roofline": {"bound": "alu", "unit": "T FP32 lane operations/s",
+                              "achieved": df_achieved, "peak": f32_peak,
+                              "frac": df_achieved / f32_peak, "peak_kind": "nominal",
+                              "ops_per_update": df_ops,
+                              "kernel": "horner_stage (FP64 form, double-float on FP32 pipes)",
+                              "peak_note": "128 FP32 lanes x 152 SMs x 2.07 GHz; the plain "
+                                           "FP64 stage (EMD_OPT_STAGE_VARIANT 1) is bound by "
+                                           "2 FP64 lanes per SM",
                               "hbm_achieved_GBps": f64_hbm, "hbm_frac": f64_hbm / peak}},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo, "steps": args.e2e_steps,
