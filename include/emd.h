@@ -62,13 +62,16 @@ extern "C" {
                                    (one event pair each; emd_propagate then
                                    steps without graph replay)              */
 #define EMD_OPT_CHECK_STABLE 3  /* value == 0: skip the stability refusal    */
-#define EMD_OPT_STAGE_VARIANT 4 /* complex64 Horner-stage kernel: 0 one
+#define EMD_OPT_STAGE_VARIANT 4 /* Horner-stage kernel.  complex64: 0 one
                                    thread per (orbital column, 2 rows) with
                                    compile-time ring slots (default); 1 the
                                    same tiling, earlier form; bo = 2 only:
                                    2 one thread per point, 3 one thread per
                                    (point column, 2 rows).  bo = 4 uses 0
-                                   unless 1 is asked for                  */
+                                   unless 1 is asked for.  complex128 with
+                                   bo = 2: 0 double-float arithmetic on the
+                                   FP32 pipes (48-bit (hi, lo) float pairs,
+                                   default), 1 plain FP64 arithmetic     */
 #define EMD_OPT_PROJECTION   5  /* complex128 projections <p_J|u>: 1
                                    atom-major (each atom gathers its sphere,
                                    default), 0 point-major (each 8^3 tile
