@@ -323,40 +323,71 @@ def time_e2e(emd, torch, sysin, precision, steps):
 def time_batched(emd, torch, steps, n_replicas=32):
     """32 ragged replicas (8-64 atoms, 48^3-80^3, 16-128 orbitals, order 8,
     complex64, mu = 10): one batch whose 6-step chunks replay a captured CUDA
-    graph, against the same replicas propagated one after another."""
+    graph, against the same replicas propagated one after another; each
+    replica runs the stage configuration (block width, tile variant,
+    z-chunk) the autotuner measured fastest for its shape.  16 small 48^3
+    replicas are also timed as a batch of their own, where launch overhead
+    and an underfilled GPU are the larger share of a step."""
     from paper_0812_2801_gb300 import autotune, inputs
     specs = inputs.replica_specs(n_replicas, seed=5)
-    systems, upd = [], 0.0
-    tuned = {}
+    sysins, cfgs = [], []
+    tune_t0 = time.perf_counter()
     for i, spec in enumerate(specs):
         sysin = inputs.replica(spec, i)
-        bo = autotune.best_block_orbitals(sysin, emd.EMD_FP32_ORBITALS)
-        tuned[f"n{sysin.n}-orb{sysin.n_orb}"] = bo
-        systems.append(emd.System(sysin, emd.EMD_FP32_ORBITALS, block_orbitals=bo))
-        upd += 8.0 * sysin.n_orb * sysin.n ** 3
-        sysin.psi = None
-    dt, mu = systems[0].sysin.dt, systems[0].sysin.mu
-    b = emd.emd_batch_create([g.handle for g in systems])
-    emd.emd_batch_propagate(b, 8, dt, mu)          # warm-up + graph capture
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    emd.emd_batch_propagate(b, steps, dt, mu)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
-    emd.emd_batch_destroy(b)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for g in systems:
-        g.propagate(steps, dt, mu)
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
-    for g in systems:
-        g.close()
+        cfgs.append(autotune.best_config(sysin, emd.EMD_FP32_ORBITALS))
+        sysins.append(sysin)
+    tune_s = time.perf_counter() - tune_t0
+
+    def run(idx):
+        systems, upd = [], 0.0
+        for i in idx:
+            g = emd.System(sysins[i], emd.EMD_FP32_ORBITALS, block_orbitals=cfgs[i]["bo"])
+            autotune.configure(g, cfgs[i])
+            systems.append(g)
+            upd += 8.0 * sysins[i].n_orb * sysins[i].n ** 3
+        dt, mu = sysins[idx[0]].dt, sysins[idx[0]].mu
+        b = emd.emd_batch_create([g.handle for g in systems])
+        emd.emd_batch_propagate(b, 8, dt, mu)          # warm-up + graph capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        emd.emd_batch_propagate(b, steps, dt, mu)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        emd.emd_batch_destroy(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for g in systems:
+            g.propagate(steps, dt, mu)
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+        for g in systems:
+            g.close()
+        return upd, t_batch, t_seq
+
+    upd, t_batch, t_seq = run(list(range(len(sysins))))
+    # 16 small replicas (8 atoms, 48^3, 16 orbitals) of another seed
+    base = len(sysins)
+    for spec in inputs.small_replica_specs(16, seed=6):
+        sysin = inputs.replica(spec, len(sysins))
+        cfgs.append(autotune.best_config(sysin, emd.EMD_FP32_ORBITALS))
+        sysins.append(sysin)
+    small = list(range(base, len(sysins)))
+    s_upd, s_batch, s_seq = run(small) if small else (0.0, 1.0, 1.0)
+    rep = autotune.report()
+    chosen = {k: autotune.cfg_name(v["best"]) for k, v in rep.items()}
+    timings = {k: {c: round(t["step_ms"], 3) for c, t in v["timings"].items()}
+               for k, v in rep.items()}
     return {"value": upd * steps / t_batch, "unit": UNIT, "replicas": n_replicas,
             "steps": steps, "ms_per_step": 1e3 * t_batch / steps,
             "sequential_value": upd * steps / t_seq,
             "speedup_vs_sequential": t_seq / t_batch,
-            "updates_per_step": upd, "block_orbitals": tuned,
+            "updates_per_step": upd,
+            "small_48": {"replicas": len(small),
+                         "workload": "8 Si-like atoms, 48^3, 16 orbitals each (seed 6)",
+                         "value": s_upd * steps / s_batch,
+                         "ms_per_step": 1e3 * s_batch / steps,
+                         "speedup_vs_sequential": s_seq / s_batch},
+            "configs": chosen, "tuning_step_ms": timings, "tuning_s": tune_s,
             "workload": "32 ragged replicas: 8-64 Si-like atoms, 48^3/64^3/80^3, "
                         "2 orbitals per atom, order 8, complex64, mu 10, dt 0.158"}
 

@@ -80,6 +80,13 @@ extern "C" {
                                    use per-tile entry lists grouped by atom
                                    (each tile read once, one warp per atom) */
 
+#define EMD_OPT_ZCHUNK       6  /* planes per z-chunk of the z-marching
+                                   stage kernels (each CTA marches through
+                                   one chunk and restages 2 * order / 2 halo
+                                   planes): 0 automatic (whole columns unless
+                                   that leaves SMs idle), else an integer
+                                   1 .. 1024 (clamped to the grid)          */
+
 /* kernels that can be timed with EMD_OPT_PROFILE */
 #define EMD_KERNEL_HORNER    0  /* one Taylor/Horner stage u' = psi0 + a H u */
 #define EMD_KERNEL_ALL       1  /* every kernel the library launched (count

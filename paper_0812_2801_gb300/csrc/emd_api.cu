@@ -382,6 +382,7 @@ double kinetic_fp32(emd_system *s, int *np) {
                                                      (float)(3.0 * fd_num(order, 0)));
   OrbLayout o = s->o;
   o.stage_variant = 0;
+  o.zchunk = 0;
   o.w[0] = 3.0 * fd_num(order, 0);
   for (int k = 1; k <= o.half_order; ++k) o.w[k] = fd_num(order, k);
   StageArgs a;
@@ -488,6 +489,7 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
   o.half_order = c.fd_order / 2;
   o.n_atoms = c.n_atoms;
   o.stage_variant = 0;
+  o.zchunk = 0;
   for (int k = 0; k <= EMD_MAX_HALF_ORDER; ++k) o.w[k] = o.num[k] = 0.0;
   o.w[0] = -1.5 * fd_weight(c.fd_order, 0) / (c.h * c.h);
   for (int k = 1; k <= o.half_order; ++k)
@@ -779,6 +781,11 @@ int emd_set_option(emd_system *s, int option, double value) {
         return fail(EMD_EINVAL, "stage variant must be 0, 1, 2 or 3");
       s->o.stage_variant = (int)value;
       return EMD_OK;
+    case EMD_OPT_ZCHUNK:
+      if (!(value >= 0.0 && value <= 1024.0) || value != (double)(int)value)
+        return fail(EMD_EINVAL, "z-chunk must be an integer in 0 .. 1024");
+      s->o.zchunk = (int)value;
+      return EMD_OK;
   }
   return fail(EMD_EINVAL, "unknown option %d", option);
 }
@@ -874,7 +881,7 @@ struct emd_batch {
   // host-side state baked into the captured graph: the position-set parity,
   // the v_Hxc history slots (rotated by pointer, period 3) and the options
   // that select kernels
-  std::vector<int> key_cur, key_variant, key_proj;
+  std::vector<int> key_cur, key_variant, key_proj, key_zchunk;
   std::vector<const double *> key_hist;
   long long graph_launches = 0;
 };
@@ -926,11 +933,13 @@ int batch_capture(emd_batch *b, double dt, double mu) {
   const size_t m = b->sys.size();
   b->key_cur.resize(m);
   b->key_variant.resize(m);
+  b->key_zchunk.resize(m);
   b->key_proj.resize(m);
   b->key_hist.resize(m);
   for (size_t i = 0; i < m; ++i) {
     b->key_cur[i] = b->sys[i]->cur;
     b->key_variant[i] = b->sys[i]->o.stage_variant;
+    b->key_zchunk[i] = b->sys[i]->o.zchunk;
     b->key_proj[i] = b->sys[i]->proj_atom_major;
     b->key_hist[i] = b->sys[i]->hist[0];
   }
@@ -942,6 +951,7 @@ bool batch_graph_valid(const emd_batch *b, double dt, double mu) {
   for (size_t i = 0; i < b->sys.size(); ++i)
     if (b->key_cur[i] != b->sys[i]->cur || b->key_hist[i] != b->sys[i]->hist[0] ||
         b->key_variant[i] != b->sys[i]->o.stage_variant ||
+        b->key_zchunk[i] != b->sys[i]->o.zchunk ||
         b->key_proj[i] != b->sys[i]->proj_atom_major)
       return false;
   return true;

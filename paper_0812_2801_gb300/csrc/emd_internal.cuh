@@ -264,6 +264,7 @@ struct StageArgs {
 struct OrbLayout {
   int n, n3, bo, n_blk, n_orb, n_orb_pad, prec, half_order, n_atoms;
   int stage_variant;   // Horner-stage kernel (EMD_OPT_STAGE_VARIANT)
+  int zchunk;          // planes per z-chunk of the marching stage kernels, 0 = automatic
   double h;
   double w[EMD_MAX_HALF_ORDER + 1];   // w_0 = -3 c_0 / (2 h^2), w_k = -c_k/(2 h^2)
   // the same stencil as integers over a common denominator: c_k = num_k / den

@@ -1644,6 +1644,15 @@ k_nl_force_df(const double2 *__restrict__ u, size_t n3, int n_blk,
 
 // ---- dispatch -------------------------------------------------------------
 
+// planes per z-chunk of a marching stage launch: the caller's choice, else
+// whole columns unless the columns alone would leave SMs idle (each chunk
+// restages and re-stencils 2M halo planes)
+inline int stage_zchunk(const OrbLayout &o, int cols, int min_ctas) {
+  if (o.zchunk > 0) return std::min(o.zchunk, o.n);
+  const int nz = std::max(1, std::min((min_ctas + cols - 1) / cols, o.n / 16));
+  return (o.n + nz - 1) / nz;
+}
+
 template <typename T, int BO, int M>
 void stage_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
   typedef typename cplx<T>::type V;
@@ -1669,7 +1678,8 @@ void stage_z_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
     attr_done = true;
   }
   const int ntx = (o.n + Z::TX - 1) / Z::TX, nty = (o.n + Z::TY - 1) / Z::TY;
-  const int zc = o.n <= 64 ? o.n : (o.n + 1) / 2 <= 64 ? (o.n + 1) / 2 : 48;
+  const int zc = o.zchunk > 0 ? std::min(o.zchunk, o.n)
+                             : (o.n <= 64 ? o.n : (o.n + 1) / 2 <= 64 ? (o.n + 1) / 2 : 48);
   dim3 grid(ntx * nty, (o.n + zc - 1) / zc, o.n_blk);
   k_stage_z<BO, M><<<grid, Z::NT, smem, st>>>(
       (const float2 *)a.u_in, (const float2 *)a.psi0, (float2 *)a.u_out,
@@ -1691,9 +1701,7 @@ void stage_c_tt(const OrbLayout &o, const StageArgs &a, size_t smem, cudaStream_
   const int ntx = (o.n + Z::TX - 1) / Z::TX, nty = (o.n + Z::TY - 1) / Z::TY;
   // one z-chunk per column unless the columns alone would leave SMs idle:
   // each chunk restages and re-stencils 2M halo planes
-  const int cols = ntx * nty * o.n_blk;
-  const int nz = std::max(1, std::min((2 * 152 + cols - 1) / cols, o.n / 16));
-  const int zc = (o.n + nz - 1) / nz;
+  const int zc = stage_zchunk(o, ntx * nty * o.n_blk, 2 * 152);
   dim3 grid(ntx * nty, (o.n + zc - 1) / zc, o.n_blk);
   k_stage_c<BO, M, HCS><<<grid, Z::NT, smem, st>>>(
       (const float2 *)a.u_in, (const float2 *)a.psi0, (float2 *)a.u_out,
@@ -1736,7 +1744,8 @@ void stage_zp_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
     attr_done = true;
   }
   const int ntx = (o.n + Z::TX - 1) / Z::TX, nty = (o.n + Z::TY - 1) / Z::TY;
-  const int zc = o.n <= 64 ? o.n : (o.n + 1) / 2 <= 64 ? (o.n + 1) / 2 : 48;
+  const int zc = o.zchunk > 0 ? std::min(o.zchunk, o.n)
+                             : (o.n <= 64 ? o.n : (o.n + 1) / 2 <= 64 ? (o.n + 1) / 2 : 48);
   dim3 grid(ntx * nty, (o.n + zc - 1) / zc, o.n_blk);
   k_stage_zp<BO, M, RY><<<grid, Z::NT, smem, st>>>(
       (const float2 *)a.u_in, (const float2 *)a.psi0, (float2 *)a.u_out,
@@ -1775,9 +1784,7 @@ void stage_df_tt(const OrbLayout &o, const StageArgs &a, size_t smem, cudaStream
     attr_done = true;
   }
   const int ntx = (o.n + Z::TX - 1) / Z::TX, nty = (o.n + Z::TY - 1) / Z::TY;
-  const int cols = ntx * nty * o.n_blk;
-  const int nz = std::max(1, std::min((2 * 152 + cols - 1) / cols, o.n / 16));
-  const int zc = (o.n + nz - 1) / nz;
+  const int zc = stage_zchunk(o, ntx * nty * o.n_blk, 2 * 152);
   DFWeights W;
   for (int k = 0; k <= EMD_MAX_HALF_ORDER; ++k) W.num[k] = (float)o.num[k];
   const double sk = -1.0 / (2.0 * o.h * o.h * o.den);

@@ -20,6 +20,7 @@ EMD_ENOTCONV = 7
 EMD_FP64, EMD_FP32_ORBITALS = 0, 1
 EMD_OPT_FROZEN_IONS, EMD_OPT_PROFILE, EMD_OPT_CHECK_STABLE, EMD_OPT_STAGE_VARIANT = 1, 2, 3, 4
 EMD_OPT_PROJECTION = 5
+EMD_OPT_ZCHUNK = 6
 EMD_KERNEL_HORNER, EMD_KERNEL_ALL = 0, 1
 EMD_OBS_ENERGY, EMD_OBS_DIPOLE_Z = 0, 1
 

@@ -308,6 +308,16 @@ def replica_specs(n_replicas: int = 32, seed: int = 5):
     return specs
 
 
+def small_replica_specs(n_replicas: int = 16, seed: int = 6):
+    """Replicas of the smallest shape of the ragged set: 8 atoms on the 2^3
+    lattice at 6.0 bohr, each coordinate jittered by U[-0.2, 0.2], 48^3 at
+    0.25 bohr (16 orbitals)."""
+    rng = np.random.default_rng(seed)
+    sites = lattice_sites("sc", 2, 6.0)
+    return [dict(n=48, h=0.25, R=sites + rng.uniform(-0.2, 0.2, size=sites.shape),
+                 vel_seed=300 + r, phase_seed=400 + r) for r in range(n_replicas)]
+
+
 def replica(spec: dict, idx: int) -> SystemInput:
     return build_system(f"replica-{idx}", spec["n"], spec["h"], 8, spec["R"],
                         spec["vel_seed"], spec["phase_seed"], mu=10.0,

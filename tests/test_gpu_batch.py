@@ -89,3 +89,74 @@ def test_batch_fp64_matches_oracle():
         st = O.run(s, 8, dt=0.04, mu=1.0)
         assert np.max(np.abs(psi - st.psi)) <= 1e-10
         assert np.max(np.abs(F - st.F)) <= 1e-9 * np.max(np.abs(st.F))
+
+
+def c3_replicas():
+    """One replica of each grid of the ragged-replica workload (48^3, 64^3,
+    80^3; Si-like, order 8, 2 orbitals per atom)."""
+    specs = inputs.replica_specs(32, seed=5)
+    out, seen = [], set()
+    for i, sp in enumerate(specs):
+        if sp["n"] not in seen:
+            seen.add(sp["n"])
+            out.append(inputs.replica(sp, i))
+    return out
+
+
+CONFIGS = [dict(bo=4, variant=0, zchunk=0), dict(bo=2, variant=2, zchunk=16),
+           dict(bo=2, variant=3, zchunk=0), dict(bo=1, variant=0, zchunk=0)]
+
+
+def test_c3_shapes_every_tuned_configuration_against_oracle_points():
+    """H psi of 4 orbitals at sampled points of each replica shape, in every
+    configuration the autotuner searches (block width, tile variant,
+    z-chunk), against the oracle evaluated point by point."""
+    from paper_0812_2801_gb300 import autotune
+    for s in c3_replicas():
+        tables = O.atom_tables(s.R, s.species, s.n, s.h)
+        rng = np.random.default_rng(s.n)
+        pts = [tuple(int(v) for v in rng.integers(0, s.n, size=3)) for _ in range(16)]
+        pts += [(0, 0, 0), (s.n - 1, s.n - 1, s.n - 1), (0, s.n - 1, s.n // 2)]
+        u = s.psi[:4]
+        c = O.projections(u, tables, s.species, s.h)
+        for cfg in CONFIGS:
+            g = emd.System(s, emd.EMD_FP32_ORBITALS, block_orbitals=cfg["bo"])
+            autotune.configure(g, cfg)
+            pot = emd.emd_get_potentials(g.handle, s.n)
+            hu = emd.emd_apply_hamiltonian(g.handle, u)
+            g.close()
+            v_eff = pot["v_loc"] + pot["v_h"] + pot["v_xc"]
+            ref = O.hamiltonian_at_points(u, v_eff, c, s.R, s.species, s.h, s.fd_order, pts,
+                                          list(range(4)))
+            got = np.array([[hu[a, z, y, x] for (z, y, x) in pts] for a in range(4)])
+            assert np.max(np.abs(got - ref)) < 2e-5 * np.max(np.abs(ref)), (s.n, cfg)
+
+
+def test_c3_shapes_batch_with_mixed_configurations_equals_solo_runs():
+    """The three replica shapes, each in a different configuration, stepped as
+    one batch (eager warm-up, then graph chunks) equal the same systems
+    stepped alone, bit for bit."""
+    from paper_0812_2801_gb300 import autotune
+    sysins = c3_replicas()
+    cfgs = CONFIGS[:len(sysins)]
+    dt, mu = sysins[0].dt, sysins[0].mu
+    solo = []
+    for s, cfg in zip(sysins, cfgs):
+        g = emd.System(s, emd.EMD_FP32_ORBITALS, block_orbitals=cfg["bo"])
+        autotune.configure(g, cfg)
+        g.propagate(8, dt=dt, mu=mu)
+        solo.append(g.state()[2])
+        g.close()
+    gs = []
+    for s, cfg in zip(sysins, cfgs):
+        g = emd.System(s, emd.EMD_FP32_ORBITALS, block_orbitals=cfg["bo"])
+        autotune.configure(g, cfg)
+        gs.append(g)
+    b = emd.emd_batch_create([g.handle for g in gs])
+    emd.emd_batch_propagate(b, 8, dt, mu)
+    got = [g.state()[2] for g in gs]
+    emd.emd_batch_destroy(b)
+    for g in gs:
+        g.close()
+    for p1, p2 in zip(solo, got):
+        assert np.array_equal(p1, p2)
