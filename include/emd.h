@@ -50,6 +50,10 @@ extern "C" {
                              orbitals and ions are set)                   */
 #define EMD_ETABLE    6   /* a per-point or per-tile atom list overflowed */
 #define EMD_ENOTCONV  7   /* emd_ground_state: tolerance not reached        */
+#define EMD_ETIMEOUT  8   /* a bounded wait inside a kernel gave up (its
+                             tensor copies did not complete in ~1 s); the
+                             results of the calls since the last check are
+                             invalid; reported by the next emd_get_* call */
 
 /* orbital storage precision */
 #define EMD_FP64           0  /* complex128 orbitals, FP64 stencil          */
@@ -67,8 +71,12 @@ extern "C" {
                                    compile-time ring slots (default); 1 the
                                    same tiling, earlier form; bo = 2 only:
                                    2 one thread per point, 3 one thread per
-                                   (point column, 2 rows).  bo = 4 uses 0
-                                   unless 1 is asked for.  complex128 with
+                                   (point column, 2 rows).  bo = 4: 0 with
+                                   the per-plane diagonal, projector records
+                                   and psi0 fetched by tensor copies (TMA),
+                                   2 the same kernel with per-thread
+                                   cp.async copies, 1 the earlier form.
+                                   complex128 with
                                    bo = 2: 0 double-float arithmetic on the
                                    FP32 pipes (48-bit (hi, lo) float pairs,
                                    default), 1 plain FP64 arithmetic     */

@@ -196,6 +196,11 @@ int read_err_flag(emd_system *s) {
   int h = 0;
   CK(cudaMemcpyAsync(&h, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->st));
   CK(cudaStreamSynchronize(s->st));
+  if (h & EMD_ERRBIT_WAIT) {
+    CK(cudaMemsetAsync(s->err, 0, sizeof(int), s->st));
+    return fail(EMD_ETIMEOUT, "a bounded wait in a stage kernel gave up (tensor copies "
+                              "not completed within ~1 s); results of that call are invalid");
+  }
   if (h)
     return fail(EMD_ETABLE,
                 "atom list overflow (bits %d: 1 point list > %d atoms, 2 tile "
@@ -244,6 +249,7 @@ void stage(emd_system *s, const void *u_in, const void *psi0, void *u_out,
     a_.v_diag = which_veff == 1 ? (const void *)s->veff1d : (const void *)s->veff2d;
   }
   a_.tab = &s->ts[set];
+  a_.err = s->err;
   a_.hc = s->hc;
   a_.a = a;
   a_.apply_only = 0;
@@ -392,6 +398,7 @@ double kinetic_fp32(emd_system *s, int *np) {
   a.v_eff = s->veff1f;
   a.v_diag = s->veff1d;
   a.tab = &s->ts[s->cur];
+  a.err = s->err;
   a.hc = s->hc_zero;
   a.a = 0.0;
   a.apply_only = 1;
@@ -1361,6 +1368,7 @@ int adjoint_moving(emd_system *s, int n_steps, double dt, double mu,
     a_.u_out = A->acc;
     a_.v_eff = s->veff1;
     a_.tab = &s->ts[s->cur];
+    a_.err = s->err;
     a_.hc = s->hc;
     a_.a = 0.0;
     a_.apply_only = 1;
@@ -1624,6 +1632,7 @@ int emd_propagate_adjoint(emd_system *s, int n_steps, double dt, double mu,
     a_.u_out = A->acc;
     a_.v_eff = s->veff1;
     a_.tab = &s->ts[s->cur];
+    a_.err = s->err;
     a_.hc = s->hc;
     a_.a = 0.0;
     a_.apply_only = 1;
@@ -1907,6 +1916,7 @@ int emd_apply_hamiltonian(emd_system *s, int n_vec, const double *psi,
   a.v_eff = s->o.prec == EMD_FP64 ? (const void *)s->veff1 : (const void *)s->veff1f;
   if (s->o.prec != EMD_FP64) a.v_diag = s->veff1d;
   a.tab = &s->ts[s->cur];
+  a.err = s->err;
   a.hc = s->hc;
   a.a = 0.0;
   a.apply_only = 1;
@@ -2027,6 +2037,7 @@ void gs_apply(emd_system *s, const void *u_in, void *u_out) {
   a.v_eff = s->o.prec == EMD_FP64 ? (const void *)s->veff1 : (const void *)s->veff1f;
   if (s->o.prec != EMD_FP64) a.v_diag = s->veff1d;
   a.tab = &s->ts[s->cur];
+  a.err = s->err;
   a.hc = g->hc;
   a.a = 0.0;
   a.apply_only = 1;

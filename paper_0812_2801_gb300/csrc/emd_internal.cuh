@@ -33,6 +33,7 @@ constexpr double C = -gam * (0.5 * b1 + b2) / (q1 * q1) - A - D;    // slope
 #define EMD_ERRBIT_PT   1       // per-point list overflow
 #define EMD_ERRBIT_TILE 2       // per-tile candidate overflow
 #define EMD_ERRBIT_AT   4       // per-atom table overflow
+#define EMD_ERRBIT_WAIT 8       // a bounded device wait gave up
 
 template <typename T> struct cplx;
 template <> struct cplx<double> { typedef double2 type; };
@@ -260,6 +261,7 @@ struct StageArgs {
   const void *hc;          // [n_atoms][n_orb_pad] h_kb*c in orbital precision
   double a;                // tau / k ; u_out = psi0 + (-i a) H u_in
   int apply_only;          // 1: u_out = H u_in (psi0 unused)
+  int *err = nullptr;      // device error bits (EMD_ERRBIT_*), may be NULL
 };
 struct OrbLayout {
   int n, n3, bo, n_blk, n_orb, n_orb_pad, prec, half_order, n_atoms;

@@ -13,6 +13,11 @@
 // per grid point, so one thread updates bo orbitals at one point and shares
 // the potential, the projector list and the index arithmetic between them.
 #include <algorithm>
+#include <cstring>
+#include <cuda.h>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "emd_internal.cuh"
 
@@ -412,6 +417,41 @@ inline WPairs<float> wpairs_of(const OrbLayout &o) {
   return r;
 }
 
+// ---- tensor copies (TMA) completing on an mbarrier -------------------------
+__device__ __forceinline__ void mbar_init(unsigned addr, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(addr), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned addr, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(addr), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned addr, unsigned parity) {
+  unsigned ok;
+  asm volatile("{\n\t.reg .pred p;\n\t"
+               "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.u32 %0, 1, 0, p;\n\t}\n"
+               : "=r"(ok)
+               : "r"(addr), "r"(parity)
+               : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of the barrier; gives up after 2^31 SM cycles
+// (about a second at 2 GHz) and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned addr, unsigned parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(addr, parity))
+    if (clock64() - t0 > (1ll << 31)) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *tm, int c0, int c1,
+                                            int c2, unsigned mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+      : "memory");
+}
+
 template <int M> struct LeanGroup {
   // planes unrolled per group: a multiple of both the ring depth 3 and 2M+1
   static constexpr int NS = 2 * M + 1;
@@ -427,19 +467,30 @@ template <int BO, int M> struct ZCTile : ZTile<BO, M> {
   static constexpr size_t SMEM_FIXED = (size_t)B::NB * SLOT;
 };
 
-template <int BO, int M, bool HCS>
+// TMA (bo = 4): the diagonal, the projector records and psi0 of a plane,
+// which never wrap around the grid, arrive as three tensor copies issued by
+// one thread and completing on the ring slot's mbarrier; the orbital plane
+// with its periodic halo keeps the per-thread cp.async chunks.
+template <int BO, int M, bool HCS, bool TMA>
 __global__ void __launch_bounds__(512, 1)
 k_stage_c(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
           float2 *__restrict__ u_out, const float4 *__restrict__ diag,
           const int2 *__restrict__ pt4, const int *__restrict__ pt_J,
           const float *__restrict__ pt_pf, const float2 *__restrict__ hc,
           int n, int ntx, int zc, int n_orb_pad, int n_atoms, float a,
-          int apply_only, WPairs<float> W) {
+          int apply_only, WPairs<float> W, const __grid_constant__ CUtensorMap tm_diag,
+          const __grid_constant__ CUtensorMap tm_pt4, const __grid_constant__ CUtensorMap tm_psi,
+          int *err) {
+  static_assert(!TMA || BO == 4, "tensor copies are laid out for bo = 4");
   typedef ZCTile<BO, M> Z;
   constexpr int RY = Z::RY;
   constexpr int NS = Z::NS;
   constexpr int G = LeanGroup<M>::G;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smdyn[];
+  // tensor copies land on 128-byte boundaries: align the ring (the launch
+  // reserves 128 bytes of slack)
+  unsigned char *smraw =
+      smdyn + ((128u - ((unsigned)__cvta_generic_to_shared(smdyn) & 127u)) & 127u);
   float2 *hcs = reinterpret_cast<float2 *>(smraw + Z::NB * Z::SLOT);
   const int tid = threadIdx.x;
   const int col = tid % Z::NC, tyr = tid / Z::NC;
@@ -504,6 +555,16 @@ k_stage_c(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
       hcs[i] = hc[(size_t)(i / BO) * n_orb_pad + (size_t)blockIdx.z * BO + i % BO];
   }
   const unsigned sm0 = (unsigned)__cvta_generic_to_shared(smraw);
+  // one mbarrier per ring slot (after the h_kb c copy, 8-byte aligned)
+  const unsigned mb0 = (sm0 + Z::NB * Z::SLOT + (HCS ? n_atoms * BO * 8 : 0) + 7u) & ~7u;
+  bool timed_out = false;
+  if (TMA) {
+    if (tid == 0) {
+      for (int k = 0; k < Z::NB; ++k) mbar_init(mb0 + 8 * k, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+  }
 
   auto issue = [&](int zi, int slot) {
     const unsigned base = sm0 + slot * Z::SLOT;
@@ -517,6 +578,26 @@ k_stage_c(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
       if (src_off[i] >= 0)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + dst_b[i]),
                      "l"(src + src_off[i]) : "memory");
+    if (TMA) {
+      if (tid == 0) {
+        const bool out = zi >= 2 * M;
+        const unsigned bytes = Z::NV * 16 + (out ? Z::NV * 32 + (apply_only ? 0 : Z::NV * 32) : 0);
+        const unsigned mb = mb0 + 8 * slot;
+        // the slot's previous contents were read through the generic proxy
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_expect_tx(mb, bytes);
+        tma_load_3d(base + Z::UB, &tm_diag, 0, tx0, zz * n + ty0, mb);
+        if (out) {
+          const int zo = z0 + zi - 2 * M;
+          tma_load_3d(base + Z::UB + Z::VB, &tm_pt4, 0, tx0, zo * n + ty0, mb);
+          if (!apply_only)
+            tma_load_3d(base + Z::UB + Z::VB + Z::QB, &tm_psi, 0, tx0,
+                        ((int)blockIdx.z * n + zo) * n + ty0, mb);
+        }
+      }
+      cp_async_commit();
+      return;
+    }
     if (v_src >= 0)
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + Z::UB + tid * 16),
                    "l"(diag + poff + v_src) : "memory");
@@ -566,6 +647,7 @@ k_stage_c(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
       // finished plane zi - 1, whose ring slot the prefetch of zi + 2 reuses
       if (zi + 1 < total) cp_async_wait<1>();
       else cp_async_wait<0>();
+      if (TMA && !mbar_wait_bounded(mb0 + 8 * sb, (unsigned)(zi / 3) & 1u)) timed_out = true;
       __syncthreads();
       if (zi + 2 < total) issue(zi + 2, (ph + 2) % 3);
       const unsigned char *base = smraw + sb * Z::SLOT;
@@ -642,6 +724,16 @@ k_stage_c(const float2 *__restrict__ u_in, const float2 *__restrict__ psi0,
         for (int r = 0; r < RY; ++r) acc[r][slot] = make_float2(0.f, 0.f);
       }
     }
+  }
+  if (TMA && timed_out) {
+    if (err) atomicOr(err, EMD_ERRBIT_WAIT);
+    // copies of a slot that never completed may still be in flight: give
+    // them one more bounded wait before the shared memory is released
+    if (tid == 0)
+      for (int k = 0; k < Z::NB && k < total; ++k) {
+        const int last = k + 3 * ((total - 1 - k) / 3);   // last plane staged in slot k
+        mbar_wait_bounded(mb0 + 8 * k, (unsigned)(last / 3) & 1u);
+      }
   }
 }
 
@@ -1688,14 +1780,65 @@ void stage_z_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
       (float)a.a, a.apply_only, weights_of<float>(o));
 }
 
-template <int BO, int M, bool HCS>
-void stage_c_tt(const OrbLayout &o, const StageArgs &a, size_t smem, cudaStream_t st) {
+// ---- tensor maps of the complex64 stage (encoded once per array) ---------
+typedef CUresult (*TmEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                               const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                               const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                               CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+TmEncodeFn tm_encode_fn() {
+  static TmEncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<TmEncodeFn>(p);
+  });
+  return fn;
+}
+
+// A 3-D view (inner elements, x, rows) of an array of n x-points per row
+// with `inner` 4-byte elements per point, and a box of (inner, bx, by).
+bool tm_get(CUtensorMap *out, const void *base, bool is_int, int inner, int n, size_t rows,
+            int bx, int by) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void *, int, int, size_t, int, int>, CUtensorMap> cache;
+  const auto key = std::make_tuple(base, inner * (is_int ? -1 : 1), n, rows, bx, by);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *out = it->second;
+    return true;
+  }
+  TmEncodeFn f = tm_encode_fn();
+  if (!f) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)n, (cuuint64_t)rows};
+  const cuuint64_t strides[2] = {(cuuint64_t)inner * 4, (cuuint64_t)inner * 4 * n};
+  const cuuint32_t box[3] = {(cuuint32_t)inner, (cuuint32_t)bx, (cuuint32_t)by};
+  const cuuint32_t es[3] = {1, 1, 1};
+  CUtensorMap tm;
+  if (f(&tm, is_int ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+        const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  cache[key] = tm;
+  *out = tm;
+  return true;
+}
+
+template <int BO, int M, bool HCS, bool TMA>
+void stage_c_tt(const OrbLayout &o, const StageArgs &a, size_t smem, cudaStream_t st,
+                const CUtensorMap *tm) {
   typedef ZCTile<BO, M> Z;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(k_stage_c<BO, M, HCS>,
+    cudaFuncSetAttribute(k_stage_c<BO, M, HCS, TMA>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(Z::SMEM_FIXED + 16384));
+                         (int)(Z::SMEM_FIXED + 16384 + 256));
     attr_done = true;
   }
   const int ntx = (o.n + Z::TX - 1) / Z::TX, nty = (o.n + Z::TY - 1) / Z::TY;
@@ -1703,21 +1846,39 @@ void stage_c_tt(const OrbLayout &o, const StageArgs &a, size_t smem, cudaStream_
   // each chunk restages and re-stencils 2M halo planes
   const int zc = stage_zchunk(o, ntx * nty * o.n_blk, 2 * 152);
   dim3 grid(ntx * nty, (o.n + zc - 1) / zc, o.n_blk);
-  k_stage_c<BO, M, HCS><<<grid, Z::NT, smem, st>>>(
+  k_stage_c<BO, M, HCS, TMA><<<grid, Z::NT, smem + 256, st>>>(
       (const float2 *)a.u_in, (const float2 *)a.psi0, (float2 *)a.u_out,
       (const float4 *)a.v_diag, a.tab->pt4, a.tab->pt_J, a.tab->pt_pf,
       (const float2 *)a.hc, o.n, ntx, zc, o.n_orb_pad, o.n_atoms, (float)a.a,
-      a.apply_only, wpairs_of(o));
+      a.apply_only, wpairs_of(o), tm[0], tm[1], tm[2], a.err);
 }
 
 template <int BO, int M>
 void stage_c_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
   typedef ZCTile<BO, M> Z;
   const int hc_bytes = o.n_atoms * BO * (int)sizeof(float2);
-  if (hc_bytes <= 16384)
-    stage_c_tt<BO, M, true>(o, a, Z::SMEM_FIXED + hc_bytes, st);
-  else
-    stage_c_tt<BO, M, false>(o, a, Z::SMEM_FIXED, st);
+  // tensor copies for bo = 4 unless the cp.async form is asked for
+  // (variant 2) or a map cannot be encoded
+  CUtensorMap tm[3];
+  memset(tm, 0, sizeof(tm));
+  bool tma = false;
+  if (BO == 4 && o.stage_variant != 2) {
+    const size_t n2 = (size_t)o.n * o.n;
+    tma = tm_get(&tm[0], a.v_diag, false, 4, o.n, n2, Z::TX, Z::TY) &&
+          tm_get(&tm[1], a.tab->pt4, true, 8, o.n, n2, Z::TX, Z::TY) &&
+          (a.apply_only || tm_get(&tm[2], a.psi0, false, 8, o.n, n2 * o.n * o.n_blk, Z::TX, Z::TY));
+  }
+  if (tma) {
+    if (hc_bytes <= 16384)
+      stage_c_tt<BO, M, true, BO == 4>(o, a, Z::SMEM_FIXED + hc_bytes, st, tm);
+    else
+      stage_c_tt<BO, M, false, BO == 4>(o, a, Z::SMEM_FIXED, st, tm);
+  } else {
+    if (hc_bytes <= 16384)
+      stage_c_tt<BO, M, true, false>(o, a, Z::SMEM_FIXED + hc_bytes, st, tm);
+    else
+      stage_c_tt<BO, M, false, false>(o, a, Z::SMEM_FIXED, st, tm);
+  }
 }
 
 template <int BO>

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libemd.so")
 
 EMD_OK, EMD_EINVAL, EMD_ENOMEM, EMD_ECUDA, EMD_EUNSTABLE, EMD_ESTATE, EMD_ETABLE = range(7)
 EMD_ENOTCONV = 7
+EMD_ETIMEOUT = 8
 EMD_FP64, EMD_FP32_ORBITALS = 0, 1
 EMD_OPT_FROZEN_IONS, EMD_OPT_PROFILE, EMD_OPT_CHECK_STABLE, EMD_OPT_STAGE_VARIANT = 1, 2, 3, 4
 EMD_OPT_PROJECTION = 5

@@ -68,7 +68,8 @@ def test_binding_constants_match_the_header():
         if hasattr(emd, name):
             assert getattr(emd, name) == int(value), name
     for name in ("EMD_OK", "EMD_EINVAL", "EMD_ESTATE", "EMD_EUNSTABLE", "EMD_ENOTCONV",
-                 "EMD_FP64", "EMD_FP32_ORBITALS", "EMD_OPT_PROFILE", "EMD_OBS_DIPOLE_Z"):
+                 "EMD_ETIMEOUT", "EMD_FP64", "EMD_FP32_ORBITALS", "EMD_OPT_PROFILE",
+                 "EMD_OPT_ZCHUNK", "EMD_OBS_DIPOLE_Z"):
         assert hasattr(emd, name) and name in defs, name
 
 

@@ -251,7 +251,7 @@ def test_point_major_projections_equal_atom_major(prec, tol):
     assert np.max(np.abs(out[0] - out[1])) <= tol * np.max(np.abs(out[1]))
 
 
-@pytest.mark.parametrize("bo,variant", [(2, 0), (2, 1), (2, 2), (2, 3), (4, 0), (4, 1)])
+@pytest.mark.parametrize("bo,variant", [(2, 0), (2, 1), (2, 2), (2, 3), (4, 0), (4, 1), (4, 2)])
 @pytest.mark.parametrize("order", [4, 8])
 def test_fp32_stage_variants(bo, variant, order):
     """Every complex64 Horner-stage kernel: H psi against the FP64 oracle with
@@ -339,7 +339,7 @@ def test_fp32_stage_small_grid_wrapped_rows(bo, order):
     u = rng.normal(size=(5, s.n, s.n, s.n)) + 1j * rng.normal(size=(5, s.n, s.n, s.n))
     H = O.Hamiltonian(st.v_loc + st.v_h + st.v_xc, st.tables, s.species, s.h, s.fd_order)
     ref = H.apply(u)
-    for variant in (0, 1):
+    for variant in (0, 1, 2):
         g = emd.System(s, emd.EMD_FP32_ORBITALS, block_orbitals=bo)
         emd.emd_set_option(g.handle, emd.EMD_OPT_STAGE_VARIANT, variant)
         got = emd.emd_apply_hamiltonian(g.handle, u)
