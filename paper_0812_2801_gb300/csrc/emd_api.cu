@@ -557,6 +557,12 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
     TRY(A((void **)&t.at_pt, (size_t)na * cap * 4));
     TRY(A((void **)&t.at_p, (size_t)na * cap * 8));
     TRY(A((void **)&t.at_d, (size_t)na * cap * 24));
+    t.at_rec = nullptr;
+    t.at_w = nullptr;
+    if (c.precision == EMD_FP64 && o.bo == 2 && c.n_atoms > 0) {
+      TRY(A((void **)&t.at_rec, (size_t)na * cap * sizeof(uint4)));
+      TRY(A((void **)&t.at_w, (size_t)na * cap * 2 * sizeof(float4)));
+    }
     t.te_off = nullptr;
     t.te_pp = nullptr;
     t.te_q = nullptr;

@@ -70,6 +70,11 @@ struct TableSet {
   int *at_pt;       // [n_atoms][cap] flat grid index
   double *at_p;     // [n_atoms][cap] p value of that (point, image)
   double *at_d;     // [n_atoms][cap][3] displacement r - R_image
+  // complex128 with bo = 2 (double-float projections and moments): the same
+  // entries pre-split, (point, p hi, p lo, 0) and (w_x hi, w_x lo, w_y hi,
+  // w_y lo), (w_z hi, w_z lo, 0, 0) with w = p d / r_c^2; NULL otherwise
+  uint4 *at_rec;    // [n_atoms][cap]
+  float4 *at_w;     // [n_atoms][cap][2]
   // complex64 path: per 8^3 tile, the (point, atom) pairs of the projectors
   // grouped by the tile's atoms (slots, in tile_atoms order): te_off[t][s]
   // is the first entry of slot s (te_off[t][S] the end), an entry holds the
@@ -96,27 +101,82 @@ struct TableSet {
 };
 
 // ---------------------------------------------------------------------------
-// Double-float split of a double by integer operations on its bits:
-// x = hi + lo, hi = x truncated to 24 significant bits, lo = x - hi rounded to
-// 24 bits (|x - hi - lo| <= 2^-47 |x|).  |x| < 2^-126 gives (0, 0), and lo is
-// dropped below |x| < 2^-74 (an absolute error under 1e-29).  Branch-free:
-// the out-of-range cases are selected away.
+// Double-float split of a double from its bits: x = hi + lo, hi = x truncated
+// to 24 significant bits (sign, exponent rebased from 1023 to 127 and the
+// top 23 stored mantissa bits, moved into place by one funnel shift), lo =
+// the remaining 29 mantissa bits converted to float with rounding to nearest
+// and scaled by 2^(e - 1075), so |x - hi - lo| <= 2^-48 |x|.  |x| < 2^-126
+// gives hi = 0, and lo is dropped below |x| < 2^-74 (an absolute error under
+// 1e-29).  No FP64 instruction; the one conversion runs on the conversion
+// unit.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 emd_df_split(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned h = (unsigned)(b >> 32), l = (unsigned)b;
   const unsigned e = (h >> 20) & 0x7ffu;
   const unsigned s = h & 0x80000000u;
-  const float hi = __uint_as_float(s | ((e - 896u) << 23) | ((h & 0xfffffu) << 3) | (l >> 29));
-  // the remaining 29 bits r = r1 2^23 + r0 carry weight 2^(e - 1075); r1 and
-  // r0 become exact floats through the 2^23 exponent trick
-  const float f1 = __fsub_rn(__uint_as_float(0x4b000000u | ((l >> 23) & 0x3fu)), 8388608.f);
-  const float f0 = __fsub_rn(__uint_as_float(0x4b000000u | (l & 0x7fffffu)), 8388608.f);
-  const float s1 = __uint_as_float(s | ((e - 925u) << 23));
-  const float s0 = __uint_as_float(s | ((e - 948u) << 23));
-  const float lo = __fmaf_rn(f1, s1, __fmul_rn(f0, s0));
-  return make_float2(e >= 897u ? hi : 0.f, e >= 949u ? lo : 0.f);
+  // (h - 896 << 20) << 3 | l >> 29: the rebased exponent fits 8 bits, so the
+  // sign position receives a zero and is set from s
+  const unsigned hb = s | __funnelshift_l(l, (h & 0x7fffffffu) - (896u << 20), 3);
+  const float r = __uint2float_rn(l & 0x1fffffffu);
+  const float sc = __uint_as_float(s | ((max(e, 948u) - 948u) << 23));   // 2^(e-1075) or 0
+  return make_float2(e >= 897u ? __uint_as_float(hb) : 0.f, __fmul_rn(r, sc));
 }
+
+// Double-float arithmetic on the FP32 pipes (the complex128 stage,
+// projections and nonlocal-force moments).
+__device__ __forceinline__ float2 df_split(double x) { return emd_df_split(x); }
+
+// exact widening of a float (normal or zero; float subnormals, below 2^-126,
+// become 0) by integer operations
+__device__ __forceinline__ double df_widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  const unsigned hw = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  const double d = __hiloint2double((int)hw, (int)(u << 29));
+  return ex == 0u ? 0.0 : d;
+}
+
+// Double-float pairs for a complex value, packed so that both components go
+// through one FP32x2 instruction: hi = (re_hi, im_hi), lo = (re_lo, im_lo);
+// the packed operations round each lane as the scalar ones would.
+__device__ __forceinline__ float2 f2neg_sub(float2 a, float2 b) {   // a - b
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+// Knuth's TwoSum, per lane: s + e = a + b exactly
+__device__ __forceinline__ void dfp_two_sum(float2 a, float2 b, float2 &s, float2 &e) {
+  s = __fadd2_rn(a, b);
+  const float2 bb = f2neg_sub(s, a);
+  e = __fadd2_rn(f2neg_sub(a, f2neg_sub(s, bb)), f2neg_sub(b, bb));
+}
+// (hi, lo) += (p, q), p the leading part
+__device__ __forceinline__ void dfp_add(float2 &hi, float2 &lo, float2 p, float2 q) {
+  float2 s, e;
+  dfp_two_sum(hi, p, s, e);
+  hi = s;
+  lo = __fadd2_rn(lo, __fadd2_rn(e, q));
+}
+// TwoProduct of a scalar pair (w, w) and x, per lane: p + pe = w x exactly
+__device__ __forceinline__ void dfp_two_prod(float2 w, float2 x, float2 &p, float2 &pe) {
+  p = __fmul2_rn(w, x);
+  pe = __ffma2_rn(w, x, __fmul2_rn(make_float2(-w.x, -w.y), x));
+}
+// (hi, lo) += (wh + wl)(xh + xl) for a real double-float w, dropping wl xl
+__device__ __forceinline__ void dfp_add_prod(float2 &hi, float2 &lo, float wh, float wl,
+                                             float2 xh, float2 xl) {
+  const float2 w2 = make_float2(wh, wh);
+  float2 p, pe;
+  dfp_two_prod(w2, xh, p, pe);
+  dfp_add(hi, lo, p, __ffma2_rn(w2, xl, __ffma2_rn(make_float2(wl, wl), xh, pe)));
+}
+
+// a complex double-float: (re_hi, im_hi, re_lo, im_lo)
+__device__ __forceinline__ float4 df_split2(double2 v) {
+  const float2 r = df_split(v.x), i = df_split(v.y);
+  return make_float4(r.x, i.x, r.y, i.y);
+}
+__device__ __forceinline__ float2 f4hi(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 f4lo(float4 v) { return make_float2(v.z, v.w); }
 
 // ---------------------------------------------------------------------------
 // Exact displacement arithmetic.  The support decision d^2 < r^2 is an

@@ -1350,59 +1350,6 @@ k_abs2_sum(const double2 *c, int n, double *out) {
 // z-direction accumulates in a (2M+1)-slot shift register, and planes are
 // staged through registers (load, split, store) one plane ahead.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 df_split(double x) { return emd_df_split(x); }
-
-// exact widening of a float (normal or zero; float subnormals, below 2^-126,
-// become 0) by integer operations
-__device__ __forceinline__ double df_widen(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned ex = (u >> 23) & 0xffu;
-  const unsigned hw = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
-  const double d = __hiloint2double((int)hw, (int)(u << 29));
-  return ex == 0u ? 0.0 : d;
-}
-
-// Double-float pairs for a complex value, packed so that both components go
-// through one FP32x2 instruction: hi = (re_hi, im_hi), lo = (re_lo, im_lo);
-// the packed operations round each lane as the scalar ones would.
-__device__ __forceinline__ float2 f2neg_sub(float2 a, float2 b) {   // a - b
-  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
-}
-// Knuth's TwoSum, per lane: s + e = a + b exactly
-__device__ __forceinline__ void dfp_two_sum(float2 a, float2 b, float2 &s, float2 &e) {
-  s = __fadd2_rn(a, b);
-  const float2 bb = f2neg_sub(s, a);
-  e = __fadd2_rn(f2neg_sub(a, f2neg_sub(s, bb)), f2neg_sub(b, bb));
-}
-// (hi, lo) += (p, q), p the leading part
-__device__ __forceinline__ void dfp_add(float2 &hi, float2 &lo, float2 p, float2 q) {
-  float2 s, e;
-  dfp_two_sum(hi, p, s, e);
-  hi = s;
-  lo = __fadd2_rn(lo, __fadd2_rn(e, q));
-}
-// TwoProduct of a scalar pair (w, w) and x, per lane: p + pe = w x exactly
-__device__ __forceinline__ void dfp_two_prod(float2 w, float2 x, float2 &p, float2 &pe) {
-  p = __fmul2_rn(w, x);
-  pe = __ffma2_rn(w, x, __fmul2_rn(make_float2(-w.x, -w.y), x));
-}
-// (hi, lo) += (wh + wl)(xh + xl) for a real double-float w, dropping wl xl
-__device__ __forceinline__ void dfp_add_prod(float2 &hi, float2 &lo, float wh, float wl,
-                                             float2 xh, float2 xl) {
-  const float2 w2 = make_float2(wh, wh);
-  float2 p, pe;
-  dfp_two_prod(w2, xh, p, pe);
-  dfp_add(hi, lo, p, __ffma2_rn(w2, xl, __ffma2_rn(make_float2(wl, wl), xh, pe)));
-}
-
-// a complex double-float: (re_hi, im_hi, re_lo, im_lo)
-__device__ __forceinline__ float4 df_split2(double2 v) {
-  const float2 r = df_split(v.x), i = df_split(v.y);
-  return make_float4(r.x, i.x, r.y, i.y);
-}
-__device__ __forceinline__ float2 f4hi(float4 v) { return make_float2(v.x, v.y); }
-__device__ __forceinline__ float2 f4lo(float4 v) { return make_float2(v.z, v.w); }
-
 struct DFWeights {
   float num[EMD_MAX_HALF_ORDER + 1];   // FD numerators, exact in FP32
   float sk_hi, sk_lo;                  // -1 / (2 h^2 den) as double-float
@@ -1636,31 +1583,46 @@ k_stage_df(const double2 *__restrict__ u_in, const double2 *__restrict__ psi0,
 // complex128 projections and nonlocal-force moments (bo = 2) in double-float
 // arithmetic on the FP32 pipes: the FP64 forms spend 2 (projection) and 8
 // (moments) FP64 instructions per table entry and orbital, which bounds them
-// by GB300's FP64 rate.  Each thread accumulates its entries as (hi, lo)
-// pairs (TwoProduct and TwoSum, real and imaginary parts packed), widens the
-// sums to FP64 once and joins the fixed-tree FP64 block sum of the FP64
-// kernels.
+// by GB300's FP64 rate.  Each thread takes the atom's entries tid, tid + 256,
+// ... from the pre-split records (point, p as (hi, lo), and for the moments
+// p d / r_c^2 as (hi, lo) per axis), DF_EU of them in flight at a time (the
+// loads of an entry's orbital values wait on its record), splits the
+// orbital values and accumulates (hi, lo) pairs with TwoProduct and TwoSum,
+// real and imaginary parts packed; the sums are widened to FP64 once and
+// join the fixed-tree FP64 block sum.
+#define DF_EU 4
+
 __global__ void __launch_bounds__(256)
 k_project_df(const double2 *__restrict__ u, size_t n3, const int *__restrict__ at_cnt,
-             const int *__restrict__ at_pt, const double *__restrict__ at_p, int cap, double h3,
-             double h_kb, int n_orb_pad, double2 *c, double2 *hc) {
+             const uint4 *__restrict__ at_rec, int cap, double h3, double h_kb, int n_orb_pad,
+             double2 *c, double2 *hc) {
   constexpr int BO = 2;
   __shared__ double red[8 * 2 * BO];
   const int J = blockIdx.x, blk = blockIdx.y;
   const int cnt = at_cnt[J];
   const double2 *ub = u + (size_t)blk * n3 * BO;
+  const uint4 *rec = at_rec + (size_t)J * cap;
   float2 ah[BO], al[BO];
 #pragma unroll
   for (int j = 0; j < BO; ++j) ah[j] = al[j] = make_float2(0.f, 0.f);
-  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-    const size_t idx = (size_t)J * cap + e;
-    const int pt = at_pt[idx];
-    const float2 pv = df_split(at_p[idx]);
+  for (int e0 = threadIdx.x; e0 < cnt; e0 += DF_EU * 256) {
+    uint4 r[DF_EU];
 #pragma unroll
-    for (int j = 0; j < BO; ++j) {
-      const float4 v = df_split2(ub[(size_t)pt * BO + j]);
-      dfp_add_prod(ah[j], al[j], pv.x, pv.y, f4hi(v), f4lo(v));
-    }
+    for (int v = 0; v < DF_EU; ++v)       // past the end: point 0, p = 0 (adds zero)
+      r[v] = e0 + 256 * v < cnt ? __ldg(rec + e0 + 256 * v) : make_uint4(0u, 0u, 0u, 0u);
+    double2 x[DF_EU][BO];
+#pragma unroll
+    for (int v = 0; v < DF_EU; ++v)
+#pragma unroll
+      for (int j = 0; j < BO; ++j) x[v][j] = ub[(size_t)r[v].x * BO + j];
+#pragma unroll
+    for (int v = 0; v < DF_EU; ++v)
+#pragma unroll
+      for (int j = 0; j < BO; ++j) {
+        const float4 xs = df_split2(x[v][j]);
+        dfp_add_prod(ah[j], al[j], __uint_as_float(r[v].y), __uint_as_float(r[v].z), f4hi(xs),
+                     f4lo(xs));
+      }
   }
   double acc[2 * BO];
 #pragma unroll
@@ -1682,32 +1644,44 @@ k_project_df(const double2 *__restrict__ u, size_t n3, const int *__restrict__ a
 
 __global__ void __launch_bounds__(256)
 k_nl_force_df(const double2 *__restrict__ u, size_t n3, int n_blk,
-              const int *__restrict__ at_cnt, const int *__restrict__ at_pt,
-              const double *__restrict__ at_p, const double *__restrict__ at_d, int cap,
-              const double2 *__restrict__ c, int n_orb_pad, int n_orb, double h3, double coef,
-              double inv_rc2, double *part) {
-  constexpr int BO = 2;
+              const int *__restrict__ at_cnt, const uint4 *__restrict__ at_rec,
+              const float4 *__restrict__ at_w, int cap, const double2 *__restrict__ c,
+              int n_orb_pad, int n_orb, double h3, double coef, double *part) {
+  constexpr int BO = 2, EU = DF_EU / 2;
   __shared__ double red[8 * 6 * BO];
   const int J = blockIdx.x, blk = blockIdx.y;
   const int cnt = at_cnt[J];
   const double2 *ub = u + (size_t)blk * n3 * BO;
+  const uint4 *rec = at_rec + (size_t)J * cap;
+  const float4 *wr = at_w + (size_t)J * cap * 2;
   float2 ah[3 * BO], al[3 * BO];      // [orbital][axis] complex moments
 #pragma unroll
   for (int k = 0; k < 3 * BO; ++k) ah[k] = al[k] = make_float2(0.f, 0.f);
-  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-    const size_t idx = (size_t)J * cap + e;
-    const int pt = at_pt[idx];
-    const double pw = at_p[idx] * inv_rc2;
-    float2 dd[3];
+  for (int e0 = threadIdx.x; e0 < cnt; e0 += EU * 256) {
+    int pt[EU];
+    float4 w0[EU], w1[EU];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) dd[a] = df_split(pw * at_d[3 * idx + a]);
-#pragma unroll
-    for (int j = 0; j < BO; ++j) {
-      const float4 v = df_split2(ub[(size_t)pt * BO + j]);
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        dfp_add_prod(ah[3 * j + a], al[3 * j + a], dd[a].x, dd[a].y, f4hi(v), f4lo(v));
+    for (int v = 0; v < EU; ++v) {        // past the end: point 0, w = 0 (adds zero)
+      const int e = e0 + 256 * v;
+      const bool ok = e < cnt;
+      pt[v] = ok ? (int)__ldg(&rec[e].x) : 0;
+      w0[v] = ok ? __ldg(wr + 2 * e) : make_float4(0.f, 0.f, 0.f, 0.f);
+      w1[v] = ok ? __ldg(wr + 2 * e + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    double2 x[EU][BO];
+#pragma unroll
+    for (int v = 0; v < EU; ++v)
+#pragma unroll
+      for (int j = 0; j < BO; ++j) x[v][j] = ub[(size_t)pt[v] * BO + j];
+#pragma unroll
+    for (int v = 0; v < EU; ++v)
+#pragma unroll
+      for (int j = 0; j < BO; ++j) {
+        const float4 xs = df_split2(x[v][j]);
+        dfp_add_prod(ah[3 * j + 0], al[3 * j + 0], w0[v].x, w0[v].y, f4hi(xs), f4lo(xs));
+        dfp_add_prod(ah[3 * j + 1], al[3 * j + 1], w0[v].z, w0[v].w, f4hi(xs), f4lo(xs));
+        dfp_add_prod(ah[3 * j + 2], al[3 * j + 2], w1[v].x, w1[v].y, f4hi(xs), f4lo(xs));
+      }
   }
   double acc[6 * BO];
 #pragma unroll
@@ -2002,9 +1976,9 @@ void project_t(const OrbLayout &o, const TableSet &t, int n_atoms,
                cudaStream_t st) {
   typedef typename cplx<T>::type V;
   dim3 grid(n_atoms, o.n_blk);
-  if (sizeof(T) == 8 && BO == 2)
-    k_project_df<<<grid, 256, 0, st>>>((const double2 *)u, (size_t)o.n3, t.at_cnt, t.at_pt,
-                                       t.at_p, t.cap, h3, h_kb, o.n_orb_pad, c, (double2 *)hc);
+  if (sizeof(T) == 8 && BO == 2 && t.at_rec)
+    k_project_df<<<grid, 256, 0, st>>>((const double2 *)u, (size_t)o.n3, t.at_cnt, t.at_rec,
+                                       t.cap, h3, h_kb, o.n_orb_pad, c, (double2 *)hc);
   else
     k_project<T, BO><<<grid, 256, 0, st>>>((const V *)u, (size_t)o.n3, t.at_cnt,
                                            t.at_pt, t.at_p, t.cap, h3, h_kb,
@@ -2048,10 +2022,10 @@ void nlf_t(const OrbLayout &o, const TableSet &t, int n_atoms, const void *u,
            double *part, cudaStream_t st) {
   typedef typename cplx<T>::type V;
   dim3 grid(n_atoms, o.n_blk);
-  if (sizeof(T) == 8 && BO == 2)
+  if (sizeof(T) == 8 && BO == 2 && t.at_rec)
     k_nl_force_df<<<grid, 256, 0, st>>>((const double2 *)u, (size_t)o.n3, o.n_blk, t.at_cnt,
-                                        t.at_pt, t.at_p, t.at_d, t.cap, c, o.n_orb_pad,
-                                        o.n_orb, h3, coef, inv_rc2, part);
+                                        t.at_rec, t.at_w, t.cap, c, o.n_orb_pad, o.n_orb, h3,
+                                        coef, part);
   else
     k_nl_force<T, BO><<<grid, 256, 0, st>>>((const V *)u, (size_t)o.n3, o.n_blk,
                                             t.at_cnt, t.at_pt, t.at_p, t.at_d,

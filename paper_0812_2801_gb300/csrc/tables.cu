@@ -386,7 +386,8 @@ __device__ void image_boxes(const double *c, double L, double h, double r,
 __global__ void __launch_bounds__(256)
 k_atom_table(int pass, int n, double h, double L, const double *Rw,
              SpeciesDev sp, int cap, float margin, int *split_cnt, int *at_cnt,
-             int *at_pt, double *at_p, double *at_d, int *err) {
+             int *at_pt, double *at_p, double *at_d, uint4 *at_rec, float4 *at_w,
+             int *err) {
   __shared__ ImageBoxes B;
   __shared__ float cf[27][3];
   __shared__ int warp_tot[8];
@@ -451,16 +452,27 @@ k_atom_table(int pass, int n, double h, double L, const double *Rw,
       const int e = off + __popc(m & ((1u << lane) - 1u));
       if (e < cap) {
         const size_t q = (size_t)J * cap + e;
-        at_pt[q] = (iz * n + iy) * n + ix;
+        const int pidx = (iz * n + iy) * n + ix;
+        at_pt[q] = pidx;
         const int ni[3] = {img % 3 - 1, (img / 3) % 3 - 1, img / 9 - 1};
         const double dx = emd_disp(ix, h, c[0], ni[0], L);
         const double dy = emd_disp(iy, h, c[1], ni[1], L);
         const double dz = emd_disp(iz, h, c[2], ni[2], L);
-        at_p[q] = sp.c_p * exp(-emd_norm2(dx, dy, dz) * sp.inv_2rc2);
+        const double pv = sp.c_p * exp(-emd_norm2(dx, dy, dz) * sp.inv_2rc2);
+        at_p[q] = pv;
         double *dd = at_d + 3 * q;
         dd[0] = dx;
         dd[1] = dy;
         dd[2] = dz;
+        if (at_rec) {
+          const float2 ps = emd_df_split(pv);
+          const double pw = pv * sp.inv_rc2;
+          const float2 wx = emd_df_split(pw * dx), wy = emd_df_split(pw * dy),
+                       wz = emd_df_split(pw * dz);
+          at_rec[q] = make_uint4((unsigned)pidx, __float_as_uint(ps.x), __float_as_uint(ps.y), 0u);
+          at_w[2 * q] = make_float4(wx.x, wx.y, wy.x, wy.y);
+          at_w[2 * q + 1] = make_float4(wz.x, wz.y, 0.f, 0.f);
+        }
       } else {
         atomicOr(err, EMD_ERRBIT_AT);
       }
@@ -796,7 +808,7 @@ void emd_launch_tables(const GridInfo &g, const SpeciesDev &sp, int n_atoms,
     for (int pass = 0; pass < 2; ++pass)
       k_atom_table<<<grid, 256, 0, st>>>(pass, g.n, g.h, g.L, t.Rw, sp, t.cap, margin,
                                          t.split_cnt, t.at_cnt, t.at_pt, t.at_p, t.at_d,
-                                         err);
+                                         t.at_rec, t.at_w, err);
   }
 }
 
