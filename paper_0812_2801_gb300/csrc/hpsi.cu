@@ -1176,6 +1176,36 @@ __global__ void k_density_c64(const float2 *__restrict__ u, size_t n3, int n_blk
   rho[p] = occ * ((double)hi + (double)lo);
 }
 
+// complex128 orbitals: sum |u|^2 in double-float arithmetic on the FP32
+// pipes (an FP64 multiply-add per component would bound the kernel by
+// GB300's FP64 rate).  Each component splits into hi + lo (48 bits); its
+// square is hi^2 (TwoProduct: p + e exactly) + 2 hi lo, the lo^2 term lying
+// below 2^-47 of the square; the real and imaginary squares accumulate as
+// packed (hi, lo) pairs with TwoSum and are widened and added once per point
+// (relative error ~1e-14).
+template <int BO>
+__global__ void k_density_df(const double2 *__restrict__ u, size_t n3, int n_blk, double occ,
+                             double *rho) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n3) return;
+  float2 ah = make_float2(0.f, 0.f), al = ah;
+#pragma unroll 4
+  for (int b = 0; b < n_blk; ++b) {
+    const double2 *ub = u + ((size_t)b * n3 + p) * BO;
+#pragma unroll
+    for (int j = 0; j < BO; ++j) {
+      const float4 v = df_split2(ub[j]);
+      const float2 h = f4hi(v), l = f4lo(v);
+      float2 sq, e;
+      dfp_two_prod(h, h, sq, e);
+      dfp_add(ah, al, sq, __ffma2_rn(__fadd2_rn(h, h), l, e));
+    }
+  }
+  const double re = __dadd_rn(df_widen(ah.x), df_widen(al.x));
+  const double im = __dadd_rn(df_widen(ah.y), df_widen(al.y));
+  rho[p] = occ * (re + im);
+}
+
 // partial[b] = sum over the points of block b and all orbitals of
 // Re(conj(u) (-1/2 nabla^2_FD u)), FP64.
 template <typename T, int BO, int M>
@@ -1992,6 +2022,9 @@ void density_t(const OrbLayout &o, const void *u, double occ, double *rho,
   if (sizeof(T) == 4)
     k_density_c64<BO><<<(o.n3 + 255) / 256, 256, 0, st>>>(
         (const float2 *)u, (size_t)o.n3, o.n_blk, occ, rho);
+  else if (BO == 2)
+    k_density_df<BO><<<(o.n3 + 255) / 256, 256, 0, st>>>(
+        (const double2 *)u, (size_t)o.n3, o.n_blk, occ, rho);
   else
     k_density<T, BO><<<(o.n3 + 255) / 256, 256, 0, st>>>((const V *)u,
                                                          (size_t)o.n3, o.n_blk,

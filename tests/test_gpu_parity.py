@@ -224,15 +224,17 @@ def test_fp32_hamiltonian_all_orders_and_blocks(order, bo):
     assert rel(got, H.apply(u)) < 3e-6
 
 
-def test_fp32_density_is_fp64_accurate():
-    """complex64 orbitals: the density (compensated FP32 sums) equals the FP64
-    density of the same complex64 values to ~1e-13."""
+@pytest.mark.parametrize("prec,tol", [(emd.EMD_FP32_ORBITALS, 1e-12), (emd.EMD_FP64, 1e-13)])
+def test_density_is_fp64_accurate(prec, tol):
+    """The density (double-float sums of exact FP32 squares for complex64
+    orbitals; of 48-bit double-float squares for complex128) equals the FP64
+    density of the same orbital values to ~1e-13."""
     s = inputs.small_system(n=24, h=0.3, fd_order=4, n_atoms=4, seed=17)
-    g = emd.System(s, emd.EMD_FP32_ORBITALS)
+    g = emd.System(s, prec)
     _, _, psi, rho = g.state()
     g.close()
     ref = s.occ * np.sum(psi.real.astype(np.float64) ** 2 + psi.imag.astype(np.float64) ** 2, axis=0)
-    assert np.max(np.abs(rho - ref)) <= 1e-12 * np.max(ref)
+    assert np.max(np.abs(rho - ref)) <= tol * np.max(ref)
 
 
 @pytest.mark.parametrize("prec,forms,tol", [(emd.EMD_FP64, (0, 1), 1e-12),
