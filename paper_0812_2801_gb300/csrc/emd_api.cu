@@ -124,6 +124,11 @@ struct emd_system {
   // k filled (1 + k), half k free again (3 + k)
   cudaStream_t cst = nullptr;
   cudaEvent_t cev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // an MD step builds the next position set's tables, v_loc and v_eff on
+  // their own stream (created on first use) while exponential 1 runs on st
+  // with the current set: fork (0) and join (1) events
+  cudaStream_t tst = nullptr;
+  cudaEvent_t tev[2] = {nullptr, nullptr};
   double *veff1 = nullptr, *veff2 = nullptr;
   float *veff1f = nullptr, *veff2f = nullptr;
   float4 *veff1d = nullptr, *veff2d = nullptr;   // complex64: (w_0 + v_eff) x4
@@ -209,15 +214,27 @@ int read_err_flag(emd_system *s) {
   return EMD_OK;
 }
 
-// Build every table of set k from ts[k].R.
-int build_set(emd_system *s, int k) {
+// Build every table of set k from ts[k].R, on stream st (uses the FFT
+// scratch fft_a / fft_b).
+int build_set(emd_system *s, int k, cudaStream_t st) {
   TableSet &t = s->ts[k];
-  emd_launch_wrap(t.R, t.Rw, s->n_atoms, s->g.L, s->st);
-  emd_launch_tables(s->g, s->sp, s->n_atoms, t, s->err, s->st);
-  emd_launch_tile_atoms(s->g, s->n_atoms, t, s->err, s->st);
+  emd_launch_wrap(t.R, t.Rw, s->n_atoms, s->g.L, st);
+  emd_launch_tables(s->g, s->sp, s->n_atoms, t, s->err, st);
+  emd_launch_tile_atoms(s->g, s->n_atoms, t, s->err, st);
   // v_loc = Poisson(-g): solve for g, negate in the final pass
-  emd_launch_poisson(s->g, t.g_ion, t.v_loc, s->fft_a, s->fft_b, s->st);
+  emd_launch_poisson(s->g, t.g_ion, t.v_loc, s->fft_a, s->fft_b, st);
   return launch_check("build_set");
+}
+int build_set(emd_system *s, int k) { return build_set(s, k, s->st); }
+
+int table_pipe(emd_system *s) {
+  if (s->tst) return EMD_OK;
+  if (cudaStreamCreateWithFlags(&s->tst, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(EMD_ECUDA, "table stream creation failed");
+  for (cudaEvent_t &e : s->tev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return fail(EMD_ECUDA, "event creation failed");
+  return EMD_OK;
 }
 
 void negate_grid(double *v, int n3, cudaStream_t st);
@@ -840,17 +857,28 @@ int step_once(emd_system *s, double dt, double mu, double e) {
   if (!s->frozen_ions) {
     emd_launch_vv_positions(s->n_atoms, s->ts[cur].R, s->V, s->F, dt,
                             s->sp.mass, s->ts[nw].R, s->st);
-    int r = build_set(s, nw);
+    // set nw and veff2 on the table stream; exponential 1 reads neither, and
+    // the FFT scratch they use is free until electrons() after the join
+    int r = table_pipe(s);
     if (r) return r;
-    negate_grid(s->ts[nw].v_loc, s->g.n3, s->st);
+    CK(cudaEventRecord(s->tev[0], s->st));
+    CK(cudaStreamWaitEvent(s->tst, s->tev[0], 0));
+    r = build_set(s, nw, s->tst);
+    if (r) return r;
+    negate_grid(s->ts[nw].v_loc, s->g.n3, s->tst);
+    emd_launch_veff(s->g, s->ts[nw].v_loc, s->hist, s->hist_len, e, s->veff2,
+                    s->veff2f, s->tst, s->veff2d, s->o.w[0]);
+    CK(cudaEventRecord(s->tev[1], s->tst));
+  } else {
+    emd_launch_veff(s->g, s->ts[nw].v_loc, s->hist, s->hist_len, e, s->veff2,
+                    s->veff2f, s->st, s->veff2d, s->o.w[0]);
   }
   emd_launch_veff(s->g, s->ts[cur].v_loc, s->hist, 1, e, s->veff1, s->veff1f,
                   s->st, s->veff1d, s->o.w[0]);
-  emd_launch_veff(s->g, s->ts[nw].v_loc, s->hist, s->hist_len, e, s->veff2,
-                  s->veff2f, s->st, s->veff2d, s->o.w[0]);
   if (!s->c_valid) project(s, s->psi, cur);
   // exponential 1: psi -> ub with H(t)
   exponential(s, s->psi, s->ua, s->ub, cur, 1, tau);
+  if (!s->frozen_ions) CK(cudaStreamWaitEvent(s->st, s->tev[1], 0));
   project(s, s->ub, nw);
   // exponential 2: ub -> psi with H(t+dt)
   exponential(s, s->ub, s->ua, s->psi, nw, 2, tau);
@@ -2397,6 +2425,12 @@ void emd_destroy(emd_system *s) {
     cudaStreamDestroy(s->cst);
   }
   for (cudaEvent_t e : s->cev)
+    if (e) cudaEventDestroy(e);
+  if (s->tst) {
+    cudaStreamSynchronize(s->tst);
+    cudaStreamDestroy(s->tst);
+  }
+  for (cudaEvent_t e : s->tev)
     if (e) cudaEventDestroy(e);
   for (void *p : s->allocs) cudaFree(p);
   if (s->adj) {
