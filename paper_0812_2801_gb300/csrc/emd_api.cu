@@ -239,19 +239,20 @@ int table_pipe(emd_system *s) {
 
 void negate_grid(double *v, int n3, cudaStream_t st);
 
-void project(emd_system *s, const void *u, int set) {
+void project(emd_system *s, const void *u, int set, cudaStream_t st) {
   if (s->o.prec == EMD_FP32_ORBITALS)
     emd_launch_project_tile(s->o, s->ts[set], s->n_atoms, u,
                             s->g.h * s->g.h * s->g.h, s->sp.h_kb, s->c, s->hc,
-                            s->proj_part, s->st);
+                            s->proj_part, st);
   else if (s->proj_atom_major)
     emd_launch_project(s->o, s->ts[set], s->n_atoms, u, s->g.h * s->g.h * s->g.h,
-                       s->sp.h_kb, s->c, s->hc, s->st);
+                       s->sp.h_kb, s->c, s->hc, st);
   else
     emd_launch_project_pm(s->o, s->ts[set], s->n_atoms, u,
                           s->g.h * s->g.h * s->g.h, s->sp.h_kb, s->c, s->hc,
-                          s->proj_part, s->st);
+                          s->proj_part, st);
 }
+void project(emd_system *s, const void *u, int set) { project(s, u, set, s->st); }
 
 void stage(emd_system *s, const void *u_in, const void *psi0, void *u_out,
            int set, int which_veff, double a) {
@@ -309,25 +310,39 @@ void electrons(emd_system *s, int slot) {
                  s->st);
 }
 
-// Forces at set k (projections of psi at k must be in c).
-void forces(emd_system *s, int k, double field, double dt, int update_v) {
-  emd_launch_local_force(s->g, s->sp, s->n_atoms, s->ts[k], s->v_h,
-                         s->ts[k].v_loc, s->lf_part, s->F_loc, s->st);
+// The force terms that read neither rho nor the potentials: nonlocal (from
+// psi and its projections c at set k) and ion short range.
+void forces_nl_sr(emd_system *s, int k, cudaStream_t st) {
   if (s->o.prec == EMD_FP32_ORBITALS)
     emd_launch_nl_force_tile(s->o, s->ts[k], s->n_atoms, s->psi, s->c,
                              s->g.h * s->g.h * s->g.h,
-                             -2.0 * s->sp.h_kb * s->cfg.occ, s->proj_part, s->F_nl,
-                             s->st);
+                             -2.0 * s->sp.h_kb * s->cfg.occ, s->proj_part, s->F_nl, st);
   else
     emd_launch_nl_force(s->o, s->ts[k], s->n_atoms, s->psi, s->c,
                         s->g.h * s->g.h * s->g.h,
                         -2.0 * s->sp.h_kb * s->cfg.occ, s->sp.inv_rc2,
-                        s->nl_part, s->F_nl, s->st);
+                        s->nl_part, s->F_nl, st);
   emd_launch_short_range(s->sp, s->n_atoms, s->ts[k].Rw, s->g.L, s->F_sr,
-                         s->e_sr, s->sr_part, s->st);
+                         s->e_sr, s->sr_part, st);
+}
+
+void local_force(emd_system *s, int k) {
+  emd_launch_local_force(s->g, s->sp, s->n_atoms, s->ts[k], s->v_h,
+                         s->ts[k].v_loc, s->lf_part, s->F_loc, s->st);
+}
+
+// F = the three terms (+ the field's force); V += F dt / (2 M) if update_v
+void total_force(emd_system *s, double field, double dt, int update_v) {
   emd_launch_vv_velocities(s->n_atoms, s->F_loc, s->F_nl, s->F_sr, field,
                            s->sp.z, s->F, s->V, dt, s->sp.mass, update_v,
                            s->st);
+}
+
+// Forces at set k (projections of psi at k must be in c).
+void forces(emd_system *s, int k, double field, double dt, int update_v) {
+  local_force(s, k);
+  forces_nl_sr(s, k, s->st);
+  total_force(s, field, dt, update_v);
 }
 
 int reduce_max_veff(emd_system *s, double *out);
@@ -882,6 +897,16 @@ int step_once(emd_system *s, double dt, double mu, double e) {
   project(s, s->ub, nw);
   // exponential 2: ub -> psi with H(t+dt)
   exponential(s, s->ub, s->ua, s->psi, nw, 2, tau);
+  if (!s->frozen_ions) {
+    // psi's projections at set nw and the nonlocal and short-range forces
+    // on the table stream, beside the density and potentials (which they
+    // neither read nor write)
+    CK(cudaEventRecord(s->tev[0], s->st));
+    CK(cudaStreamWaitEvent(s->tst, s->tev[0], 0));
+    project(s, s->psi, nw, s->tst);
+    forces_nl_sr(s, nw, s->tst);
+    CK(cudaEventRecord(s->tev[1], s->tst));
+  }
   // new density and potentials; history slot of the oldest entry
   double *oldest = s->hist[2];
   s->hist[2] = s->hist[1];
@@ -890,8 +915,9 @@ int step_once(emd_system *s, double dt, double mu, double e) {
   electrons(s, 0);
   s->hist_len = std::min(3, s->hist_len + 1);
   if (!s->frozen_ions) {
-    project(s, s->psi, nw);
-    forces(s, nw, e, dt, 1);
+    local_force(s, nw);
+    CK(cudaStreamWaitEvent(s->st, s->tev[1], 0));
+    total_force(s, e, dt, 1);
     s->cur = nw;
     s->c_valid = 1;
   } else {
