@@ -45,6 +45,8 @@ class TorchStep:
     def __init__(self, sysin):
         self.s = sysin
         self.n, self.h, self.sp = sysin.n, sysin.h, sysin.species
+        if int(getattr(self.sp, "lmax", 0)) > 0:
+            raise NotImplementedError("the adjoint reference covers the s-projector only")
         self.L = self.n * self.h
         self.order = sysin.fd_order
         self.c = torch.as_tensor(O.fd_coefficients(self.order))

@@ -147,24 +147,31 @@ class AtomTables:
     """Per-atom supports at one set of positions.
 
     loc, proj: [(idx, dx, dy, dz)] per atom, every (point, image) pair;
-    pmerged:   [(idx, p)] per atom with p_J(r) summed over images, idx unique.
+    pmerged:   [(idx, p)] per projector P = J n_ch + k (channel k of
+               channels(sp); P = J for an s-projector only) with p_P(r)
+               summed over images, idx unique;
+    hP:        strength of projector P (h_kb for l = 0, h_l otherwise).
     """
     loc: list
     proj: list
     pmerged: list
+    hP: Optional[np.ndarray] = None
 
 
 def atom_tables(R: np.ndarray, sp, n: int, h: float) -> AtomTables:
     Rw = wrap(R, n * h)
     loc = [sphere_entries(Rw[j], sp.r_loc, n, h) for j in range(R.shape[0])]
     proj = [sphere_entries(Rw[j], sp.r_proj, n, h) for j in range(R.shape[0])]
-    pmerged = []
+    ch = channels(sp)
+    pmerged, hP = [], []
     for (idx, dx, dy, dz) in proj:
         uidx, inv = np.unique(idx, return_inverse=True)
-        p = np.bincount(inv, weights=projector_values(sp, dx, dy, dz),
-                        minlength=uidx.size)
-        pmerged.append((uidx, p))
-    return AtomTables(loc=loc, proj=proj, pmerged=pmerged)
+        for (l, m) in ch:
+            p = np.bincount(inv, weights=projector_lm_values(sp, l, m, dx, dy, dz),
+                            minlength=uidx.size)
+            pmerged.append((uidx, p))
+            hP.append(channel_strength(sp, l))
+    return AtomTables(loc=loc, proj=proj, pmerged=pmerged, hP=np.array(hP))
 
 
 def gaussian_charge_values(sp, dx, dy, dz) -> np.ndarray:
@@ -180,6 +187,70 @@ def projector_values(sp, dx, dy, dz) -> np.ndarray:
     d2 = dx * dx + dy * dy + dz * dz
     rc = sp.r_c
     return math.pi ** -0.75 * rc ** -1.5 * np.exp(-d2 / (2.0 * rc * rc))
+
+
+# Several projectors per atom.  The paper's norm-conserving pseudopotentials
+# (Sec. 5) carry one separable term per angular momentum l; here each l <=
+# lmax has 2l + 1 Gaussian-type projectors p_lm(d) = N_l S_lm(d) exp(-d^2 /
+# (2 r_c^2)) with the real solid harmonics S_lm normalised so that their
+# square integrates over directions to 4 pi r^(2l) / (2l + 1), and one
+# strength h_l shared by the m of an l (rotational invariance).
+
+def channels(sp) -> list:
+    """(l, m) of the projectors of one atom, in their order within the atom."""
+    lmax = int(getattr(sp, "lmax", 0))
+    return [(l, m) for l in range(lmax + 1) for m in range(2 * l + 1)]
+
+
+def channel_strength(sp, l: int) -> float:
+    return sp.h_kb if l == 0 else float(sp.h_l[l - 1])
+
+
+def solid_harmonic(l: int, m: int, dx, dy, dz):
+    """S_lm(d) and its gradient (three arrays)."""
+    z0 = np.zeros_like(dx)
+    one = np.ones_like(dx)
+    s3 = math.sqrt(3.0)
+    if l == 0:
+        return one, (z0, z0, z0)
+    if l == 1:
+        d = (dx, dy, dz)[m]
+        g = [z0, z0, z0]
+        g[m] = one
+        return d, tuple(g)
+    if m == 0:
+        return s3 * dx * dy, (s3 * dy, s3 * dx, z0)
+    if m == 1:
+        return s3 * dy * dz, (z0, s3 * dz, s3 * dy)
+    if m == 2:
+        return s3 * dz * dx, (s3 * dz, z0, s3 * dx)
+    if m == 3:
+        return 0.5 * s3 * (dx * dx - dy * dy), (s3 * dx, -s3 * dy, z0)
+    return 0.5 * (2.0 * dz * dz - dx * dx - dy * dy), (-dx, -dy, 2.0 * dz)
+
+
+def projector_norm(l: int, rc: float) -> float:
+    """N_l with int p_lm^2 d^3r = 1: N_l^-2 = (4 pi/(2l+1)) int_0^inf
+    r^(2l+2) exp(-r^2/r_c^2) dr = (2 pi/(2l+1)) Gamma(l + 3/2) r_c^(2l+3)."""
+    return (2.0 * math.pi / (2 * l + 1) * math.gamma(l + 1.5) * rc ** (2 * l + 3)) ** -0.5
+
+
+def projector_lm_values(sp, l: int, m: int, dx, dy, dz) -> np.ndarray:
+    if l == 0:
+        return projector_values(sp, dx, dy, dz)
+    S, _ = solid_harmonic(l, m, dx, dy, dz)
+    d2 = dx * dx + dy * dy + dz * dz
+    rc = sp.r_c
+    return projector_norm(l, rc) * S * np.exp(-d2 / (2.0 * rc * rc))
+
+
+def projector_lm_gradient(sp, l: int, m: int, dx, dy, dz):
+    """grad_d p_lm = N_l exp(-d^2/(2 r_c^2)) (grad S_lm - S_lm d / r_c^2)."""
+    S, gS = solid_harmonic(l, m, dx, dy, dz)
+    d2 = dx * dx + dy * dy + dz * dz
+    rc = sp.r_c
+    e = projector_norm(l, rc) * np.exp(-d2 / (2.0 * rc * rc))
+    return tuple(e * (gS[a] - S * d / (rc * rc)) for a, d in enumerate((dx, dy, dz)))
 
 
 def ion_charge(tables: AtomTables, sp, n: int) -> np.ndarray:
@@ -312,7 +383,8 @@ def dipole(rho: np.ndarray, R: np.ndarray, z_ion: float, h: float) -> np.ndarray
 
 
 def projections(u: np.ndarray, tables: AtomTables, sp, h: float) -> np.ndarray:
-    """c[J, A] = <p_J|u_A> = h^3 sum_r p_J(r) u_A(r) (p real)."""
+    """c[P, A] = <p_P|u_A> = h^3 sum_r p_P(r) u_A(r) (p real; P = J with an
+    s-projector only, J n_ch + k with several)."""
     n_orb = u.shape[0]
     flat = u.reshape(n_orb, -1)
     c = np.zeros((len(tables.pmerged), n_orb), dtype=np.complex128)
@@ -322,11 +394,11 @@ def projections(u: np.ndarray, tables: AtomTables, sp, h: float) -> np.ndarray:
 
 
 def nonlocal_apply(c: np.ndarray, tables: AtomTables, sp, shape) -> np.ndarray:
-    """sum_J h_J |p_J><p_J|u> = sum_J h_J c_J p_J(r)."""
+    """sum_P h_P |p_P><p_P|u> = sum_P h_P c_P p_P(r)."""
     n_orb = c.shape[1]
     outT = np.zeros((int(np.prod(shape[1:])), n_orb), dtype=np.complex128)
     for j, (idx, p) in enumerate(tables.pmerged):
-        outT[idx] += np.outer(p, sp.h_kb * c[j])       # idx unique per atom
+        outT[idx] += np.outer(p, tables.hP[j] * c[j])  # idx unique per projector
     return outT.T.reshape(shape)
 
 
@@ -442,13 +514,16 @@ def forces(st: State) -> np.ndarray:
         F[j] += h ** 3 * np.array([w @ dx, w @ dy, w @ dz])
     c = projections(st.psi, st.tables, sp, h)
     flat = st.psi.reshape(st.psi.shape[0], -1)
-    rc2 = sp.r_c ** 2
+    ch = channels(sp)
     for j, (idx, dx, dy, dz) in enumerate(st.tables.proj):
-        p = projector_values(sp, dx, dy, dz)
         u = flat[:, idx]
-        for ax, d in enumerate((dx, dy, dz)):
-            dc = (u @ (p * d / rc2)) * h ** 3           # d c_JA / d R_J,ax
-            F[j, ax] += -2.0 * sp.h_kb * st.occ * np.sum((np.conj(c[j]) * dc).real)
+        for k, (l, m) in enumerate(ch):
+            P = j * len(ch) + k
+            # p_P depends on r - R_J: d p / d R_J = -grad_d p
+            g = projector_lm_gradient(sp, l, m, dx, dy, dz)
+            for ax in range(3):
+                dc = (u @ (-g[ax])) * h ** 3            # d c_PA / d R_J,ax
+                F[j, ax] += -2.0 * st.tables.hP[P] * st.occ * np.sum((np.conj(c[P]) * dc).real)
     _, Fsr = short_range_ion(st.R, sp, st.n * h)
     return F + Fsr
 
@@ -460,7 +535,7 @@ def energies(st: State, V: Optional[np.ndarray] = None) -> dict:
     dv = h ** 3
     e_kin = st.occ * dv * float(np.sum((np.conj(psi) * kinetic(psi, h, st.order)).real))
     c = projections(psi, st.tables, sp, h)
-    e_nl = st.occ * sp.h_kb * float(np.sum(np.abs(c) ** 2))
+    e_nl = st.occ * float(np.sum(st.tables.hP[:, None] * np.abs(c) ** 2))
     n_tot = st.rho - st.g_ion
     v_es = st.v_h + st.v_loc
     e_sr, _ = short_range_ion(st.R, sp, st.n * h)
@@ -562,17 +637,18 @@ def hamiltonian_at_points(u: np.ndarray, v_eff: np.ndarray, c: np.ndarray,
                           points, orbitals) -> np.ndarray:
     """(H u)_A(r) at the listed points (z, y, x) and orbitals, one by one.
 
-    u is [n_orb, N, N, N]; c are the projections <p_J|u_A> [n_atoms, n_orb].
+    u is [n_orb, N, N, N]; c are the projections <p_P|u_A> [n_proj, n_orb].
     """
     n = u.shape[1]
     L = n * h
     cf = fd_coefficients(order)
     Rw = wrap(R, L)
+    ch = channels(sp)
+    hP = np.array([channel_strength(sp, l) for _ in range(R.shape[0]) for (l, m) in ch])
     out = np.zeros((len(orbitals), len(points)), dtype=np.complex128)
     for pi_, (z, y, x) in enumerate(points):
-        pv = np.zeros(R.shape[0])
+        pv = np.zeros(R.shape[0] * len(ch))
         for j in range(R.shape[0]):
-            tot = 0.0
             for nz in (-1, 0, 1):
                 for ny in (-1, 0, 1):
                     for nx in (-1, 0, 1):
@@ -581,8 +657,9 @@ def hamiltonian_at_points(u: np.ndarray, v_eff: np.ndarray, c: np.ndarray,
                         dz = (z * h - Rw[j, 2]) - nz * L
                         d2 = dx * dx + dy * dy + dz * dz
                         if d2 < sp.r_proj * sp.r_proj:
-                            tot += projector_values(sp, np.array(dx), np.array(dy), np.array(dz))
-            pv[j] = tot
+                            for k, (l, m) in enumerate(ch):
+                                pv[j * len(ch) + k] += projector_lm_values(
+                                    sp, l, m, np.array(dx), np.array(dy), np.array(dz))
         for oi, a in enumerate(orbitals):
             lap = 3.0 * cf[0] * u[a, z, y, x]
             for k in range(1, len(cf)):
@@ -590,6 +667,6 @@ def hamiltonian_at_points(u: np.ndarray, v_eff: np.ndarray, c: np.ndarray,
                                 + u[a, z, (y + k) % n, x] + u[a, z, (y - k) % n, x]
                                 + u[a, (z + k) % n, y, x] + u[a, (z - k) % n, y, x])
             val = -0.5 * lap / (h * h) + v_eff[z, y, x] * u[a, z, y, x]
-            val += np.sum(sp.h_kb * c[:, a] * pv)
+            val += np.sum(hP * c[:, a] * pv)
             out[oi, pi_] = val
     return out

@@ -45,9 +45,12 @@ class Species:
     mass    ionic mass M_J (electron masses)
     a_loc   width of the Gaussian ion charge, v_loc = -Z erf(r/a_loc)/r
     r_loc   support radius of that Gaussian charge on the grid
-    r_c     width of the Gaussian s-projector
-    h_kb    strength of the separable (Kleinman-Bylander) term
-    r_proj  support radius of the projector on the grid
+    r_c     width of the Gaussian projectors
+    h_kb    strength of the separable (Kleinman-Bylander) term, l = 0
+    r_proj  support radius of the projectors on the grid
+    lmax    highest angular momentum of the separable term (0, 1 or 2):
+            projectors p_lm = N_l S_lm(d) exp(-d^2/(2 r_c^2)) for l <= lmax
+    h_l     strengths of the l = 1 and l = 2 terms
     """
     z: float = 4.0
     mass: float = 28.0 * AMU_IN_ME
@@ -56,6 +59,8 @@ class Species:
     r_c: float = 1.0
     h_kb: float = 1.0
     r_proj: float = 5.0
+    lmax: int = 0
+    h_l: tuple = (0.0, 0.0)
 
 
 SI_LIKE = Species()

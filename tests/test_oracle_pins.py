@@ -710,3 +710,126 @@ def test_field_forces_are_minus_gradient_of_energy_with_dipole_term():
             Rm = st.R.copy(); Rm[j, ax] -= dR
             fd = -(energy(Rp) - energy(Rm)) / (2 * dR)
             assert abs(fd - st.F[j, ax]) < 2e-6 * scale + 1e-8, (j, ax, fd, st.F[j, ax])
+
+
+# --------------------------------------------------------------------------
+# Several projectors per atom (l <= 2): the Gaussian-type separable terms
+# against closed forms of Gaussian moments, and E / F / H consistency
+# --------------------------------------------------------------------------
+
+LM_SP = I.Species(r_c=0.7, r_proj=4.9, lmax=2, h_l=(0.7, -0.4))
+LM_NAMES = ["s", "x", "y", "z", "xy", "yz", "zx", "x2-y2", "3z2-r2"]
+
+
+def _lm_grid_projectors(R, n, h):
+    """Every projector of the atoms at R on the full grid, [n_atoms * 9, n^3]."""
+    t = O.atom_tables(R, LM_SP, n, h)
+    P = np.zeros((len(t.pmerged), n ** 3))
+    for k, (idx, p) in enumerate(t.pmerged):
+        P[k, idx] = p
+    return P
+
+
+def test_lm_projectors_orthonormal_and_overlaps_closed_forms():
+    """Written from the definitions, not from the oracle's formulas.  The 9
+    projectors of one atom are orthonormal in the continuum (unit norm by
+    the choice of N_l; the real solid harmonics are orthogonal on the
+    sphere).  For two atoms a vector D apart, with s the position relative
+    to their midpoint, the product of two Gaussians of width r_c is
+    exp(-D^2/(4 r_c^2)) exp(-s^2/r_c^2), whose moments are <s_a^2> = r_c^2/2
+    and <s_a^2 s_b^2> = r_c^4/4 (a != b): the s-s overlap is E =
+    exp(-D^2/(4 r_c^2)); p_a-p_b is E (delta_ab - D_a D_b / (2 r_c^2)); s on
+    J with p_a on K (K at J + D) is -E D_a / (sqrt(2) r_c); xy-xy is E (1 -
+    D_x^2/(2 r_c^2)) (1 - D_y^2/(2 r_c^2)).  The grid sums differ by
+    aliasing (~exp(-pi^2 r_c^2/h^2) = e^-121 here) and the cut-off at r_proj
+    = 7 r_c (relative tails below 1e-16 for l <= 2)."""
+    n, h = 56, 0.2
+    L = n * h
+    rc = LM_SP.r_c
+    c0 = np.array([0.5 * L + 0.013, 0.5 * L - 0.021, 0.5 * L + 0.007])
+    G = h ** 3 * (lambda P: P @ P.T)(_lm_grid_projectors(c0[None, :], n, h))
+    assert np.max(np.abs(G - np.eye(9))) < 1e-10, np.round(G, 6)
+    for d in (0.45, 1.1):
+        D = d * np.array([1.0, 2.0, 2.0]) / 3.0
+        P = _lm_grid_projectors(np.stack([c0 - 0.5 * D, c0 + 0.5 * D]), n, h)
+        ov = h ** 3 * (P[:9] @ P[9:].T)          # [channel on J, channel on K]
+        E = math.exp(-d * d / (4 * rc * rc))
+        assert abs(ov[0, 0] - E) < 1e-10
+        for a in range(3):
+            assert abs(ov[0, 1 + a] - (-E * D[a] / (math.sqrt(2.0) * rc))) < 1e-10
+            for b in range(3):
+                exact = E * ((a == b) - D[a] * D[b] / (2 * rc * rc))
+                assert abs(ov[1 + a, 1 + b] - exact) < 1e-10, (a, b)
+        exact = E * (1 - D[0] ** 2 / (2 * rc * rc)) * (1 - D[1] ** 2 / (2 * rc * rc))
+        assert abs(ov[4, 4] - exact) < 1e-10
+
+
+def _lm_system(seed):
+    sp = I.Species(r_c=0.6, lmax=2, h_l=(0.7, -0.4))
+    return I.small_system(n=16, h=0.35, fd_order=4, n_atoms=2, seed=seed, species=sp, n_orb=3)
+
+
+def test_lm_forces_are_minus_energy_gradient():
+    """F = -dE_KS/dR at fixed orbitals with s, p and d projectors, by central
+    differences (narrow projectors as in the s-only test, so that no grid
+    point crosses the cut-off sphere during the displacement)."""
+    s = _lm_system(37)
+    st = O.init_state(s)
+    F = st.F
+    dR = 1e-4
+
+    def eks(R):
+        t = O.atom_tables(R, s.species, s.n, s.h)
+        g = O.ion_charge(t, s.species, s.n)
+        st2 = O.State(**{**st.__dict__, "R": R, "tables": t, "g_ion": g,
+                          "v_loc": O.poisson(-g, s.h)})
+        return O.energies(st2)["ks"]
+
+    for j in range(2):
+        for ax in range(3):
+            Rp = st.R.copy(); Rp[j, ax] += dR
+            Rm = st.R.copy(); Rm[j, ax] -= dR
+            fd = -(eks(Rp) - eks(Rm)) / (2 * dR)
+            assert abs(fd - F[j, ax]) < 2e-6 * np.max(np.abs(F)) + 1e-8
+
+
+def test_lm_hamiltonian_is_functional_derivative_of_energy():
+    """H phi = dE_KS/d phi^* / f with s, p and d projectors (eq. new_EoM_a)."""
+    s = _lm_system(71)
+    st = O.init_state(s)
+    rng = np.random.default_rng(3)
+    chi = 0.05 * (rng.normal(size=st.psi.shape[1:]) + 1j * rng.normal(size=st.psi.shape[1:]))
+    A = 1
+    H = O.Hamiltonian(st.v_loc + st.v_h + st.v_xc, st.tables, s.species, s.h, s.fd_order)
+    ana = 2 * s.occ * s.h ** 3 * float(np.sum((np.conj(chi) * H.apply(st.psi)[A]).real))
+
+    def eks(eps):
+        psi = st.psi.copy()
+        psi[A] = psi[A] + eps * chi
+        rho, vh, ex, vx = O.electron_potentials(psi, s.occ, s.h)
+        st2 = O.State(**{**st.__dict__, "psi": psi, "rho": rho, "v_h": vh,
+                          "eps_xc": ex, "v_xc": vx})
+        return O.energies(st2)["ks"]
+
+    e = 1e-5
+    num = (eks(e) - eks(-e)) / (2 * e)
+    assert abs(num - ana) < 1e-6 * abs(ana)
+
+
+def test_lm_nonlocal_term_is_rotation_invariant():
+    """Rotating the whole configuration (atoms and orbitals) by a cube
+    symmetry of the grid (x -> y -> z -> x) leaves the nonlocal energy
+    unchanged: the strength is shared by the m of an l, and the solid
+    harmonics of one l span a rotation-invariant space.  A wrong
+    normalisation of one m (e.g. without the sqrt(3) of xy) breaks it."""
+    s = _lm_system(53)
+    st = O.init_state(s)
+    c = O.projections(st.psi, st.tables, s.species, s.h)
+    e1 = float(np.sum(st.tables.hP[:, None] * np.abs(c) ** 2))
+    # (x, y, z) -> (y, z, x): array axes are [z, y, x]
+    psi_r = np.transpose(st.psi, (0, 2, 3, 1))
+    R_r = st.R[:, [2, 0, 1]]
+    t = O.atom_tables(R_r, s.species, s.n, s.h)
+    c_r = O.projections(psi_r, t, s.species, s.h)
+    e2 = float(np.sum(t.hP[:, None] * np.abs(c_r) ** 2))
+    assert abs(e1 - e2) < 1e-12 * abs(e1)
