@@ -112,10 +112,23 @@ extern "C" {
  *   r_c     projector p(d) = pi^-3/4 r_c^-3/2 exp(-d^2/(2 r_c^2))
  *   h_kb    strength of the term h_kb |p><p|
  *   r_proj  support radius of p on the grid (d < r_proj)
- * Both radii must not exceed the box length N h.
+ *   lmax    angular momenta of the separable term, 0, 1 or 2 (the paper's
+ *           norm-conserving pseudopotentials carry one term per l): each
+ *           l <= lmax adds 2l + 1 projectors p_lm(d) = N_l S_lm(d)
+ *           exp(-d^2/(2 r_c^2)), S_lm the real solid harmonics (x, y, z;
+ *           sqrt3 xy, sqrt3 yz, sqrt3 zx, sqrt3/2 (x^2 - y^2),
+ *           (3z^2 - d^2)/2), N_l^-2 = 2 pi Gamma(l + 3/2) r_c^(2l+3) /
+ *           (2l + 1) (unit norm); lmax > 0 needs EMD_FP64 with block
+ *           width 2 and is refused by the adjoint and the ground state
+ *   h_l     strengths of the l = 1 and l = 2 terms (h_kb is l = 0)
+ * Both radii must not exceed the box length N h.  Projector P of atom J is
+ * row J (lmax + 1)^2 + k of the projections, k in the order above (s, then
+ * x y z, then the five l = 2 functions).
  */
 typedef struct {
   double z, mass, a_loc, r_loc, r_c, h_kb, r_proj;
+  int lmax;
+  double h_l[2];
 } emd_species;
 
 typedef struct {
@@ -219,8 +232,9 @@ int emd_get_state(emd_system *s, double *R, double *V, double *psi, double *rho)
 int emd_get_potentials(emd_system *s, double *v_loc, double *v_h, double *v_xc,
                        double *g_ion);
 
-/* Projections c[n_atoms][n_orb] complex128 (re, im) of the current orbitals:
- * c_JA = h^3 sum_r p_J(r) phi_A(r) (the separable term of H). */
+/* Projections c[n_atoms (lmax + 1)^2][n_orb] complex128 (re, im) of the
+ * current orbitals: c_PA = h^3 sum_r p_P(r) phi_A(r) (the separable term of
+ * H), row P = J (lmax + 1)^2 + k for channel k of atom J. */
 int emd_get_projections(emd_system *s, double *c);
 
 /* hpsi = H psi for n_vec orbitals (complex128 canonical [n_vec][N][N][N],

@@ -208,9 +208,9 @@ int read_err_flag(emd_system *s) {
   }
   if (h)
     return fail(EMD_ETABLE,
-                "atom list overflow (bits %d: 1 point list > %d atoms, 2 tile "
+                "atom list overflow (bits %d: 1 point list > %d projectors, 2 tile "
                 "candidates > %d, 4 atom table)",
-                h, EMD_PT_KMAX, EMD_TILE_CAND_MAX);
+                h, s->ts[0].kmax, EMD_TILE_CAND_MAX);
   return EMD_OK;
 }
 
@@ -244,7 +244,7 @@ void project(emd_system *s, const void *u, int set, cudaStream_t st) {
     emd_launch_project_tile(s->o, s->ts[set], s->n_atoms, u,
                             s->g.h * s->g.h * s->g.h, s->sp.h_kb, s->c, s->hc,
                             s->proj_part, st);
-  else if (s->proj_atom_major)
+  else if (s->proj_atom_major || s->sp.nch > 1)
     emd_launch_project(s->o, s->ts[set], s->n_atoms, u, s->g.h * s->g.h * s->g.h,
                        s->sp.h_kb, s->c, s->hc, st);
   else
@@ -320,7 +320,7 @@ void forces_nl_sr(emd_system *s, int k, cudaStream_t st) {
   else
     emd_launch_nl_force(s->o, s->ts[k], s->n_atoms, s->psi, s->c,
                         s->g.h * s->g.h * s->g.h,
-                        -2.0 * s->sp.h_kb * s->cfg.occ, s->sp.inv_rc2,
+                        -2.0 * s->sp.h_kb * s->cfg.occ, -2.0 * s->cfg.occ, s->sp.inv_rc2,
                         s->nl_part, s->F_nl, st);
   emd_launch_short_range(s->sp, s->n_atoms, s->ts[k].Rw, s->g.L, s->F_sr,
                          s->e_sr, s->sr_part, st);
@@ -483,6 +483,10 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
       return fail(EMD_EINVAL, "support radii (%g, %g) exceed the box length %g",
                   p.r_loc, p.r_proj, L);
   }
+  if (p.lmax < 0 || p.lmax > 2) return fail(EMD_EINVAL, "species lmax must be 0, 1 or 2");
+  if (p.lmax > 0 && !(c.precision == EMD_FP64 && (c.block_orbitals == 0 || c.block_orbitals == 2)))
+    return fail(EMD_EINVAL, "several projectors per atom (lmax > 0) need EMD_FP64 with block "
+                            "width 2 (the double-float projection kernels)");
   int ok = 0;
   emd_fft_plan_check(c.n, &ok);
   if (!ok) return fail(EMD_EINVAL, "n = %d has a prime factor above 13", c.n);
@@ -513,6 +517,17 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
   s->sp.inv_a2 = c.n_atoms ? 1.0 / (p.a_loc * p.a_loc) : 0.0;
   s->sp.inv_2rc2 = c.n_atoms ? 1.0 / (2.0 * p.r_c * p.r_c) : 0.0;
   s->sp.inv_rc2 = c.n_atoms ? 1.0 / (p.r_c * p.r_c) : 0.0;
+  s->sp.lmax = p.lmax;
+  s->sp.nch = (p.lmax + 1) * (p.lmax + 1);
+  s->sp.hl[0] = p.h_kb;
+  s->sp.hl[1] = p.lmax >= 1 ? p.h_l[0] : 0.0;
+  s->sp.hl[2] = p.lmax >= 2 ? p.h_l[1] : 0.0;
+  // N_l^-2 = 2 pi Gamma(l + 3/2) r_c^(2l+3) / (2l + 1): unit norm in the continuum
+  for (int l = 0; l < 3; ++l)
+    s->sp.nl[l] = c.n_atoms ? 1.0 / std::sqrt(2.0 * M_PI * std::tgamma(l + 1.5) *
+                                              std::pow(p.r_c, 2 * l + 3) / (2 * l + 1))
+                            : 0.0;
+  s->sp.nl[0] = s->sp.c_p;
 
   OrbLayout &o = s->o;
   o.n = c.n;
@@ -529,6 +544,9 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
   o.n_atoms = c.n_atoms;
   o.stage_variant = 0;
   o.zchunk = 0;
+  o.nch = s->sp.nch;
+  o.n_proj = c.n_atoms * o.nch;
+  for (int l = 0; l < 3; ++l) o.hl[l] = s->sp.hl[l];
   for (int k = 0; k <= EMD_MAX_HALF_ORDER; ++k) o.w[k] = o.num[k] = 0.0;
   o.w[0] = -1.5 * fd_weight(c.fd_order, 0) / (c.h * c.h);
   for (int k = 1; k <= o.half_order; ++k)
@@ -572,17 +590,19 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
                                   : std::min<long>(8L * (long)n3, 27L * cube);
   // the complex64 path reads the per-tile entries instead of the atom table
   if (c.n_atoms == 0 || c.precision == EMD_FP32_ORBITALS) cap = 1;
+  const int nproj = na * s->sp.nch;      // projector rows of c and hc
   for (int k = 0; k < 2; ++k) {
     TableSet &t = s->ts[k];
     t.cap = (int)cap;
+    t.kmax = EMD_PT_KMAX * s->sp.nch;
     TRY(A((void **)&t.R, na * 3 * 8));
     TRY(A((void **)&t.Rw, na * 3 * 8));
     TRY(A((void **)&t.tile_cnt, ntiles * 4));
     TRY(A((void **)&t.tile_ent, (size_t)ntiles * EMD_TILE_CAND_MAX * 4));
     TRY(A((void **)&t.pt_cnt, n3 * 4));
-    TRY(A((void **)&t.pt_J, n3 * EMD_PT_KMAX * 4));
-    TRY(A((void **)&t.pt_p, n3 * EMD_PT_KMAX * 8));
-    TRY(A((void **)&t.pt_pf, n3 * EMD_PT_KMAX * 4));
+    TRY(A((void **)&t.pt_J, n3 * t.kmax * 4));
+    TRY(A((void **)&t.pt_p, n3 * t.kmax * 8));
+    TRY(A((void **)&t.pt_pf, n3 * t.kmax * 4));
     TRY(A((void **)&t.pt4, n3 * 4 * sizeof(int2)));
     TRY(A((void **)&t.at_cnt, na * 4));
     TRY(A((void **)&t.split_cnt, na * EMD_SPLIT * 4));
@@ -592,8 +612,8 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
     t.at_rec = nullptr;
     t.at_w = nullptr;
     if (c.precision == EMD_FP64 && o.bo == 2 && c.n_atoms > 0) {
-      TRY(A((void **)&t.at_rec, (size_t)na * cap * sizeof(uint4)));
-      TRY(A((void **)&t.at_w, (size_t)na * cap * 2 * sizeof(float4)));
+      TRY(A((void **)&t.at_rec, (size_t)nproj * cap * sizeof(uint4)));
+      TRY(A((void **)&t.at_w, (size_t)nproj * cap * 2 * sizeof(float4)));
     }
     t.te_off = nullptr;
     t.te_pp = nullptr;
@@ -632,8 +652,8 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
             ? EMD_OK
             : fail(EMD_ECUDA, "cudaMemset failed"));
   }
-  TRY(A((void **)&s->c, (size_t)na * o.n_orb_pad * sizeof(double2)));
-  TRY(A(&s->hc, (size_t)na * o.n_orb_pad * esz));
+  TRY(A((void **)&s->c, (size_t)nproj * o.n_orb_pad * sizeof(double2)));
+  TRY(A(&s->hc, (size_t)nproj * o.n_orb_pad * esz));
   TRY(A((void **)&s->V, na * 3 * 8));
   TRY(A((void **)&s->F, na * 3 * 8));
   TRY(A((void **)&s->F_loc, na * 3 * 8));
@@ -641,7 +661,7 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
   TRY(A((void **)&s->F_sr, na * 3 * 8));
   TRY(A((void **)&s->e_sr, na * 8));
   TRY(A((void **)&s->sr_part, (size_t)na * EMD_SR_SPLIT * 4 * 8));
-  TRY(A((void **)&s->nl_part, (size_t)na * o.n_blk * 3 * 8));
+  TRY(A((void **)&s->nl_part, (size_t)nproj * o.n_blk * 3 * 8));
   TRY(A((void **)&s->lf_part, (size_t)na * EMD_SPLIT * 3 * 8));
   s->n_partials = std::max(1024, (int)((n3 + 255) / 256));
   TRY(A((void **)&s->partials, (size_t)s->n_partials * 8));
@@ -651,8 +671,8 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
   cudaError_t e = cudaMemsetAsync(s->err, 0, sizeof(int), s->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->V, 0, na * 3 * 8, s->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->F, 0, na * 3 * 8, s->st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->c, 0, (size_t)na * o.n_orb_pad * 16, s->st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->hc, 0, (size_t)na * o.n_orb_pad * esz, s->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->c, 0, (size_t)nproj * o.n_orb_pad * 16, s->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->hc, 0, (size_t)nproj * o.n_orb_pad * esz, s->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
   if (e != cudaSuccess) {
     emd_destroy(s);
@@ -852,7 +872,8 @@ int check_propagate(emd_system *s, double dt, double mu) {
   const double tau = 0.5 * (dt / mu);
   if (s->check_stable) {
     const double lam = 1.5 * kinetic_lambda_max(s->cfg.fd_order) / (s->g.h * s->g.h) +
-                       std::max(0.0, s->v_max) + std::max(0.0, s->sp.h_kb);
+                       std::max(0.0, s->v_max) +
+                       std::max({0.0, s->sp.hl[0], s->sp.hl[1], s->sp.hl[2]});
     const double x = tau * lam;
     if (x > 2.0 * std::sqrt(2.0))
       return fail(EMD_EUNSTABLE,
@@ -1614,6 +1635,8 @@ int emd_propagate_adjoint(emd_system *s, int n_steps, double dt, double mu,
                           const double *field, int ckpt_every, int observable,
                           double *L_out, double *dL_dR, double *dL_dfield) {
   g_err.clear();
+  if (s && s->sp.nch > 1)
+    return fail(EMD_EINVAL, "the adjoint covers the s-projector only (species lmax = 0)");
   int r = check_propagate(s, dt, mu);
   if (r) return r;
   if (s->o.prec != EMD_FP64)
@@ -1845,7 +1868,12 @@ int emd_get_energy(emd_system *s, emd_energy *out) {
     project(s, s->psi, cur);
     s->c_valid = 1;
   }
-  emd_launch_abs2_sum(s->c, s->n_atoms * s->o.n_orb_pad, s->scal + 1, s->st);
+  {
+    // nl = occ sum_P h_P |c_P|^2: weights 1 with one projector (times h_kb below)
+    const double w1[3] = {1.0, 1.0, 1.0};
+    emd_launch_abs2_sum(s->c, s->o.n_proj * s->o.n_orb_pad, s->o.n_orb_pad, s->sp.nch,
+                        s->sp.nch > 1 ? s->sp.hl : w1, s->scal + 1, s->st);
+  }
   const int nb = std::min(s->n_partials, 1024);
   emd_launch_dot_partials(s->g.n3, s->rho, s->v_h, s->ts[cur].g_ion,
                           s->ts[cur].v_loc, s->partials, nb, s->st);
@@ -1872,7 +1900,7 @@ int emd_get_energy(emd_system *s, emd_energy *out) {
   if (r) return r;
   const double occ = s->cfg.occ;
   out->kin_e = occ * h3 * kin_scale * hs[0];
-  out->nl = occ * s->sp.h_kb * hs[1];
+  out->nl = s->sp.nch > 1 ? occ * hs[1] : occ * s->sp.h_kb * hs[1];
   out->sr = s->n_atoms ? hs[3] : 0.0;
   const double self = s->n_atoms * s->sp.z * s->sp.z /
                       (std::sqrt(2.0 * M_PI) * (s->n_atoms ? s->sp.a_loc : 1.0));
@@ -1938,8 +1966,8 @@ int emd_get_projections(emd_system *s, double *c) {
     project(s, s->psi, s->cur);
     s->c_valid = 1;
   }
-  for (int J = 0; J < s->n_atoms; ++J)
-    CK(cudaMemcpyAsync(c + 2 * (size_t)J * s->o.n_orb, s->c + (size_t)J * s->o.n_orb_pad,
+  for (int P = 0; P < s->o.n_proj; ++P)
+    CK(cudaMemcpyAsync(c + 2 * (size_t)P * s->o.n_orb, s->c + (size_t)P * s->o.n_orb_pad,
                        (size_t)s->o.n_orb * 16, cudaMemcpyDeviceToHost, s->st));
   CK(cudaStreamSynchronize(s->st));
   return read_err_flag(s);
@@ -2280,6 +2308,8 @@ extern "C" {
 int emd_ground_state(emd_system *s, int max_scf, double tol, int degree, double mix,
                      double *eigenvalues, emd_gs_info *info) {
   g_err.clear();
+  if (s && s->sp.nch > 1)
+    return fail(EMD_EINVAL, "the ground-state solver covers the s-projector only (species lmax = 0)");
   if (!s) return fail(EMD_EINVAL, "NULL system");
   if (!s->ions_set || !s->orbs_set) return fail(EMD_ESTATE, "set ions and orbitals first");
   if (max_scf < 1 || !(tol > 0.0) || degree < 1 || degree > 64 || !(mix > 0.0) || mix > 1.0)

@@ -46,7 +46,43 @@ struct SpeciesDev {
   double inv_a2;   // 1 / a^2
   double inv_2rc2; // 1 / (2 r_c^2)
   double inv_rc2;  // 1 / r_c^2
+  // several projectors per atom: channels k = 0 .. nch - 1 = (lmax + 1)^2 - 1
+  // (s; x, y, z; sqrt3 xy, sqrt3 yz, sqrt3 zx, sqrt3/2 (x^2 - y^2),
+  // (3z^2 - d^2)/2), strengths hl[l] (hl[0] = h_kb) and norms nl[l] (nl[0] = c_p)
+  int lmax, nch;
+  double hl[3], nl[3];
 };
+
+// angular momentum of channel k
+__host__ __device__ __forceinline__ int emd_channel_l(int k) { return k == 0 ? 0 : k < 4 ? 1 : 2; }
+
+// The projector values of channels 1 .. nch - 1 at displacement d (channel 0,
+// the s-projector, is computed by the callers as before), and optionally
+// their derivatives with respect to the atom position, -grad_d p =
+// N_l e (S d / r_c^2 - grad S), e = exp(-d^2 / (2 r_c^2)).
+__device__ __forceinline__ void emd_channel_values(const SpeciesDev &sp, double dx, double dy,
+                                                   double dz, double e, double *pk,
+                                                   double (*gk)[3]) {
+  const double s3 = 1.7320508075688772;
+  double S[9], G[9][3];
+  S[1] = dx; G[1][0] = 1.0; G[1][1] = 0.0; G[1][2] = 0.0;
+  S[2] = dy; G[2][0] = 0.0; G[2][1] = 1.0; G[2][2] = 0.0;
+  S[3] = dz; G[3][0] = 0.0; G[3][1] = 0.0; G[3][2] = 1.0;
+  S[4] = s3 * dx * dy; G[4][0] = s3 * dy; G[4][1] = s3 * dx; G[4][2] = 0.0;
+  S[5] = s3 * dy * dz; G[5][0] = 0.0; G[5][1] = s3 * dz; G[5][2] = s3 * dy;
+  S[6] = s3 * dz * dx; G[6][0] = s3 * dz; G[6][1] = 0.0; G[6][2] = s3 * dx;
+  S[7] = 0.5 * s3 * (dx * dx - dy * dy); G[7][0] = s3 * dx; G[7][1] = -s3 * dy; G[7][2] = 0.0;
+  S[8] = 0.5 * (2.0 * dz * dz - dx * dx - dy * dy); G[8][0] = -dx; G[8][1] = -dy; G[8][2] = 2.0 * dz;
+  for (int k = 1; k < sp.nch; ++k) {
+    const double ne = sp.nl[emd_channel_l(k)] * e;
+    pk[k] = ne * S[k];
+    if (gk) {
+      gk[k][0] = ne * (S[k] * dx * sp.inv_rc2 - G[k][0]);
+      gk[k][1] = ne * (S[k] * dy * sp.inv_rc2 - G[k][1]);
+      gk[k][2] = ne * (S[k] * dz * sp.inv_rc2 - G[k][2]);
+    }
+  }
+}
 
 // One set of ion positions and every table derived from it.
 struct TableSet {
@@ -55,7 +91,8 @@ struct TableSet {
   int *tile_cnt;    // [n_tiles]
   int *tile_ent;    // [n_tiles][EMD_TILE_CAND_MAX], J*27 + image
   int *pt_cnt;      // [n3]
-  int *pt_J;        // [EMD_PT_KMAX][n3]
+  int kmax;         // entries per point: EMD_PT_KMAX x projectors per atom
+  int *pt_J;        // [kmax][n3] projector P = J n_ch + k (atom J if n_ch = 1)
   double *pt_p;     // [EMD_PT_KMAX][n3] p_J(r) summed over images
   float *pt_pf;     // [EMD_PT_KMAX][n3] the same in FP32 (complex64 path)
   int2 *pt4;        // [n3][4] first four (atom, FP32 p bits) per point, unused
@@ -65,7 +102,7 @@ struct TableSet {
   // p_2 lo, p_3 hi, p_3 lo) with p in double-float (unused entries 0);
   // NULL for other layouts
   int4 *pt4d;
-  int *at_cnt;      // [n_atoms]
+  int *at_cnt;      // [n_atoms] (projector P's list: at_cnt[P / n_ch])
   int *split_cnt;   // [n_atoms][EMD_SPLIT] hits per range (table building)
   int *at_pt;       // [n_atoms][cap] flat grid index
   double *at_p;     // [n_atoms][cap] p value of that (point, image)
@@ -73,8 +110,11 @@ struct TableSet {
   // complex128 with bo = 2 (double-float projections and moments): the same
   // entries pre-split, (point, p hi, p lo, 0) and (w_x hi, w_x lo, w_y hi,
   // w_y lo), (w_z hi, w_z lo, 0, 0) with w = p d / r_c^2; NULL otherwise
-  uint4 *at_rec;    // [n_atoms][cap]
-  float4 *at_w;     // [n_atoms][cap][2]
+  // (with several projectors per atom, lists per projector P, [n_proj][cap],
+  // the entries of P at the positions of atom P / n_ch's entries; w = the
+  // derivative of p_P with respect to the atom position)
+  uint4 *at_rec;    // [n_proj][cap]
+  float4 *at_w;     // [n_proj][cap][2]
   // complex64 path: per 8^3 tile, the (point, atom) pairs of the projectors
   // grouped by the tile's atoms (slots, in tile_atoms order): te_off[t][s]
   // is the first entry of slot s (te_off[t][S] the end), an entry holds the
@@ -325,6 +365,10 @@ struct StageArgs {
 };
 struct OrbLayout {
   int n, n3, bo, n_blk, n_orb, n_orb_pad, prec, half_order, n_atoms;
+  // projectors: nch per atom, n_proj = n_atoms nch rows of c and hc; hl[l]
+  // the strength of channel l (hl[0] = h_kb)
+  int nch = 1, n_proj = 0;
+  double hl[3] = {0.0, 0.0, 0.0};
   int stage_variant;   // Horner-stage kernel (EMD_OPT_STAGE_VARIANT)
   int zchunk;          // planes per z-chunk of the marching stage kernels, 0 = automatic
   double h;
@@ -342,9 +386,11 @@ void emd_launch_density(const OrbLayout &o, const void *u, double occ,
 void emd_launch_kinetic_partials(const OrbLayout &o, const void *u,
                                  double *partials, int *nparts,
                                  cudaStream_t st);
+// coef = -2 h_kb occ; coef_unit = -2 occ (times each channel's strength when
+// the atoms carry several projectors)
 void emd_launch_nl_force(const OrbLayout &o, const TableSet &t, int n_atoms,
                          const void *u, const double2 *c, double h3,
-                         double coef, double inv_rc2, double *part,
+                         double coef, double coef_unit, double inv_rc2, double *part,
                          double *F_nl, cudaStream_t st);
 void emd_launch_pack(const OrbLayout &o, const double2 *canon, void *u,
                      int n_vec, cudaStream_t st);
@@ -355,7 +401,9 @@ void emd_launch_pack_c64(const OrbLayout &o, const float2 *canon, void *u, int n
                          cudaStream_t st);
 void emd_launch_unpack_c64(const OrbLayout &o, const void *u, float2 *canon, int n_vec,
                            cudaStream_t st);
-void emd_launch_abs2_sum(const double2 *c, int n, double *out,
+// sum |c|^2 over n entries; rows of `row` entries, row r weighted by w[l] of
+// its channel l = emd_channel_l(r % nch) (w = {1, ...} with nch = 1)
+void emd_launch_abs2_sum(const double2 *c, int n, int row, int nch, const double *w, double *out,
                          cudaStream_t st);
 
 // project_pm.cu

@@ -1354,11 +1354,18 @@ __global__ void k_unpack(const typename cplx<T>::type *__restrict__ u,
 }
 
 __global__ void __launch_bounds__(256)
-k_abs2_sum(const double2 *c, int n, double *out) {
+k_abs2_sum(const double2 *c, int n, int row, int nch, double3 w, double *out) {
   __shared__ double red[8];
   double acc[1] = {0.0};
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-    acc[0] += c[i].x * c[i].x + c[i].y * c[i].y;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double a2 = c[i].x * c[i].x + c[i].y * c[i].y;
+    if (nch == 1) {
+      acc[0] += a2;
+    } else {
+      const int l = emd_channel_l((i / row) % nch);
+      acc[0] += (l == 0 ? w.x : l == 1 ? w.y : w.z) * a2;
+    }
+  }
   emd_block_sum<1>(acc, red);
   if (threadIdx.x == 0) *out = acc[0];
 }
@@ -1624,14 +1631,17 @@ k_stage_df(const double2 *__restrict__ u_in, const double2 *__restrict__ psi0,
 
 __global__ void __launch_bounds__(256)
 k_project_df(const double2 *__restrict__ u, size_t n3, const int *__restrict__ at_cnt,
-             const uint4 *__restrict__ at_rec, int cap, double h3, double h_kb, int n_orb_pad,
-             double2 *c, double2 *hc) {
+             const uint4 *__restrict__ at_rec, int cap, int nch, double h3, double3 hl,
+             int n_orb_pad, double2 *c, double2 *hc) {
   constexpr int BO = 2;
   __shared__ double red[8 * 2 * BO];
-  const int J = blockIdx.x, blk = blockIdx.y;
-  const int cnt = at_cnt[J];
+  // one CTA per (projector P = J nch + k, block): atom J's entries, channel k
+  const int P = blockIdx.x, blk = blockIdx.y;
+  const int cnt = at_cnt[P / nch];
+  const int l = emd_channel_l(P % nch);
+  const double h_kb = l == 0 ? hl.x : l == 1 ? hl.y : hl.z;
   const double2 *ub = u + (size_t)blk * n3 * BO;
-  const uint4 *rec = at_rec + (size_t)J * cap;
+  const uint4 *rec = at_rec + (size_t)P * cap;
   float2 ah[BO], al[BO];
 #pragma unroll
   for (int j = 0; j < BO; ++j) ah[j] = al[j] = make_float2(0.f, 0.f);
@@ -1664,7 +1674,7 @@ k_project_df(const double2 *__restrict__ u, size_t n3, const int *__restrict__ a
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int j = 0; j < BO; ++j) {
-      const size_t o = (size_t)J * n_orb_pad + (size_t)blk * BO + j;
+      const size_t o = (size_t)P * n_orb_pad + (size_t)blk * BO + j;
       const double re = h3 * acc[2 * j], im = h3 * acc[2 * j + 1];
       c[o] = make_double2(re, im);
       hc[o] = make_double2(h_kb * re, h_kb * im);
@@ -1672,18 +1682,23 @@ k_project_df(const double2 *__restrict__ u, size_t n3, const int *__restrict__ a
   }
 }
 
+// part[(P n_blk + blk) 3 + a]: projector P's share of the nonlocal force of
+// block blk's orbitals on atom P / nch (coef for P's strength: coef3.x for
+// l = 0, .y for l = 1, .z for l = 2)
 __global__ void __launch_bounds__(256)
 k_nl_force_df(const double2 *__restrict__ u, size_t n3, int n_blk,
               const int *__restrict__ at_cnt, const uint4 *__restrict__ at_rec,
-              const float4 *__restrict__ at_w, int cap, const double2 *__restrict__ c,
-              int n_orb_pad, int n_orb, double h3, double coef, double *part) {
+              const float4 *__restrict__ at_w, int cap, int nch, const double2 *__restrict__ c,
+              int n_orb_pad, int n_orb, double h3, double3 coef3, double *part) {
   constexpr int BO = 2, EU = DF_EU / 2;
   __shared__ double red[8 * 6 * BO];
-  const int J = blockIdx.x, blk = blockIdx.y;
-  const int cnt = at_cnt[J];
+  const int P = blockIdx.x, blk = blockIdx.y;
+  const int cnt = at_cnt[P / nch];
+  const int l = emd_channel_l(P % nch);
+  const double coef = l == 0 ? coef3.x : l == 1 ? coef3.y : coef3.z;
   const double2 *ub = u + (size_t)blk * n3 * BO;
-  const uint4 *rec = at_rec + (size_t)J * cap;
-  const float4 *wr = at_w + (size_t)J * cap * 2;
+  const uint4 *rec = at_rec + (size_t)P * cap;
+  const float4 *wr = at_w + (size_t)P * cap * 2;
   float2 ah[3 * BO], al[3 * BO];      // [orbital][axis] complex moments
 #pragma unroll
   for (int k = 0; k < 3 * BO; ++k) ah[k] = al[k] = make_float2(0.f, 0.f);
@@ -1727,14 +1742,14 @@ k_nl_force_df(const double2 *__restrict__ u, size_t n3, int n_blk,
     for (int j = 0; j < BO; ++j) {
       const int A = blk * BO + j;
       if (A >= n_orb) continue;
-      const double2 cj = c[(size_t)J * n_orb_pad + A];
+      const double2 cj = c[(size_t)P * n_orb_pad + A];
       for (int a = 0; a < 3; ++a) {
         const double dr = h3 * acc[6 * j + 2 * a], di = h3 * acc[6 * j + 2 * a + 1];
         f[a] += cj.x * dr + cj.y * di;   // Re(conj(c) dc)
       }
     }
     for (int a = 0; a < 3; ++a)
-      part[((size_t)J * n_blk + blk) * 3 + a] = coef * f[a];
+      part[((size_t)P * n_blk + blk) * 3 + a] = coef * f[a];
   }
 }
 
@@ -1961,13 +1976,13 @@ void stage_df_tt(const OrbLayout &o, const StageArgs &a, size_t smem, cudaStream
   k_stage_df<M, HCS><<<grid, Z::NT, smem, st>>>(
       (const double2 *)a.u_in, (const double2 *)a.psi0, (double2 *)a.u_out,
       (const double *)a.v_eff, a.tab->pt4d, a.tab->pt_J, a.tab->pt_p,
-      (const double2 *)a.hc, o.n, ntx, zc, o.n_orb_pad, o.n_atoms, a.a, a.apply_only, W);
+      (const double2 *)a.hc, o.n, ntx, zc, o.n_orb_pad, o.n_proj, a.a, a.apply_only, W);
 }
 
 template <int M>
 void stage_df_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
   typedef DFTile<M> Z;
-  const int hc_bytes = o.n_atoms * Z::BO * (int)sizeof(float4);
+  const int hc_bytes = o.n_proj * Z::BO * (int)sizeof(float4);   // every projector's h c
   if (hc_bytes <= 32768)
     stage_df_tt<M, true>(o, a, Z::SMEM_FIXED + hc_bytes, st);
   else
@@ -2006,9 +2021,10 @@ void project_t(const OrbLayout &o, const TableSet &t, int n_atoms,
                cudaStream_t st) {
   typedef typename cplx<T>::type V;
   dim3 grid(n_atoms, o.n_blk);
-  if (sizeof(T) == 8 && BO == 2 && t.at_rec)
-    k_project_df<<<grid, 256, 0, st>>>((const double2 *)u, (size_t)o.n3, t.at_cnt, t.at_rec,
-                                       t.cap, h3, h_kb, o.n_orb_pad, c, (double2 *)hc);
+  if (sizeof(T) == 8 && BO == 2 && t.at_rec)   // one CTA per projector
+    k_project_df<<<dim3(n_atoms * o.nch, o.n_blk), 256, 0, st>>>(
+        (const double2 *)u, (size_t)o.n3, t.at_cnt, t.at_rec, t.cap, o.nch, h3,
+        make_double3(h_kb, o.hl[1], o.hl[2]), o.n_orb_pad, c, (double2 *)hc);
   else
     k_project<T, BO><<<grid, 256, 0, st>>>((const V *)u, (size_t)o.n3, t.at_cnt,
                                            t.at_pt, t.at_p, t.cap, h3, h_kb,
@@ -2051,15 +2067,17 @@ void kinetic_t(const OrbLayout &o, const void *u, double *part, int nb,
 
 template <typename T, int BO>
 void nlf_t(const OrbLayout &o, const TableSet &t, int n_atoms, const void *u,
-           const double2 *c, double h3, double coef, double inv_rc2,
+           const double2 *c, double h3, double coef, double coef_unit, double inv_rc2,
            double *part, cudaStream_t st) {
   typedef typename cplx<T>::type V;
   dim3 grid(n_atoms, o.n_blk);
-  if (sizeof(T) == 8 && BO == 2 && t.at_rec)
-    k_nl_force_df<<<grid, 256, 0, st>>>((const double2 *)u, (size_t)o.n3, o.n_blk, t.at_cnt,
-                                        t.at_rec, t.at_w, t.cap, c, o.n_orb_pad, o.n_orb, h3,
-                                        coef, part);
-  else
+  if (sizeof(T) == 8 && BO == 2 && t.at_rec) {
+    // the s channel keeps coef = -2 h_kb occ as given
+    const double3 coef3 = make_double3(coef, coef_unit * o.hl[1], coef_unit * o.hl[2]);
+    k_nl_force_df<<<dim3(n_atoms * o.nch, o.n_blk), 256, 0, st>>>(
+        (const double2 *)u, (size_t)o.n3, o.n_blk, t.at_cnt, t.at_rec, t.at_w, t.cap, o.nch, c,
+        o.n_orb_pad, o.n_orb, h3, coef3, part);
+  } else
     k_nl_force<T, BO><<<grid, 256, 0, st>>>((const V *)u, (size_t)o.n3, o.n_blk,
                                             t.at_cnt, t.at_pt, t.at_p, t.at_d,
                                             t.cap, c, o.n_orb_pad, o.n_orb, h3,
@@ -2159,17 +2177,19 @@ void emd_launch_kinetic_partials(const OrbLayout &o, const void *u,
 
 void emd_launch_nl_force(const OrbLayout &o, const TableSet &t, int n_atoms,
                          const void *u, const double2 *c, double h3,
-                         double coef, double inv_rc2, double *part,
+                         double coef, double coef_unit, double inv_rc2, double *part,
                          double *F_nl, cudaStream_t st) {
   if (n_atoms <= 0) return;
   emd_note_launches(2);
   if (o.prec == EMD_FP64) {
-    EMD_DISPATCH_BO(double, nlf_t, o, t, n_atoms, u, c, h3, coef, inv_rc2, part, st)
+    EMD_DISPATCH_BO(double, nlf_t, o, t, n_atoms, u, c, h3, coef, coef_unit, inv_rc2, part, st)
   } else {
-    EMD_DISPATCH_BO(float, nlf_t, o, t, n_atoms, u, c, h3, coef, inv_rc2, part, st)
+    EMD_DISPATCH_BO(float, nlf_t, o, t, n_atoms, u, c, h3, coef, coef_unit, inv_rc2, part, st)
   }
+  // an atom's partials: its projectors' (channel-major), each over the blocks
+  const int per = (o.prec == EMD_FP64 && o.bo == 2 && t.at_rec) ? o.nch * o.n_blk : o.n_blk;
   const int m = 3 * n_atoms;
-  k_nl_force_sum<<<(m + 127) / 128, 128, 0, st>>>(part, n_atoms, o.n_blk, F_nl);
+  k_nl_force_sum<<<(m + 127) / 128, 128, 0, st>>>(part, n_atoms, per, F_nl);
 }
 
 void emd_launch_pack(const OrbLayout &o, const double2 *canon, void *u,
@@ -2212,10 +2232,10 @@ void emd_launch_unpack_c64(const OrbLayout &o, const void *u, float2 *canon, int
   }
 }
 
-void emd_launch_abs2_sum(const double2 *c, int n, double *out,
+void emd_launch_abs2_sum(const double2 *c, int n, int row, int nch, const double *w, double *out,
                          cudaStream_t st) {
   emd_note_launches(1);
-  k_abs2_sum<<<1, 256, 0, st>>>(c, n, out);
+  k_abs2_sum<<<1, 256, 0, st>>>(c, n, row, nch, make_double3(w[0], w[1], w[2]), out);
 }
 
 void emd_launch_cdot_re_c64(const OrbLayout &o, const void *a, const void *b,

@@ -104,7 +104,7 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
               SpeciesDev sp, float margin, const int *tile_cnt, const int *tile_ent,
               const double *gtab, const int *glo,
               int *pt_cnt, int *pt_J, double *pt_p, float *pt_pf, int2 *pt4, int4 *pt4d,
-              double *g_ion, int *te_off, uint2 *te_pp, float4 *te_q, int *err) {
+              double *g_ion, int *te_off, uint2 *te_pp, float4 *te_q, int kmax, int *err) {
   __shared__ int cand[EMD_TILE_CAND_MAX];
   __shared__ float cfs[EMD_TILE_CAND_MAX][3];
   __shared__ float cfl[F32 ? EMD_TILE_CAND_MAX : 1][3];   // low parts of the centres
@@ -169,26 +169,38 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
   int cnt = 0;
   double gsum = 0.0;
   int te_base = 0;
+  // complex128 with several projectors per atom: channel k >= 1 sums
+  double pch[9];
+  // the entries of atom J at this point: one per projector (channel)
+  auto close_atom = [&](int J, double psum) {
+    for (int k = 0; k < sp.nch; ++k) {
+      if (cnt < kmax) {
+        const double v = k == 0 ? psum : pch[k];
+        pt_J[cnt * n3 + p] = J * sp.nch + k;
+        pt_p[cnt * n3 + p] = v;
+        pt_pf[cnt * n3 + p] = (float)v;
+        ++cnt;
+      } else {
+        atomicOr(err, EMD_ERRBIT_PT);
+      }
+    }
+  };
   for (int r = 0; r < nrun; ++r) {
     double psum = 0.0;
     float psumf = 0.f, pdx = 0.f, pdy = 0.f, pdz = 0.f;
     bool hit = false;
     int J = -1;
+    if (!F32)
+      for (int k = 1; k < sp.nch; ++k) pch[k] = 0.0;
     for (int e = run_start[r]; e < run_start[r + 1]; ++e) {
       const int code = cand[e];
       const int Je = code / 27, img = code % 27;
       if (!F32 && Je != J && hit) {
         // F32 = false with more than EMD_TILE_ATOM_MAX atoms: the last run
         // holds several atoms; close the previous one
-        if (cnt < EMD_PT_KMAX) {
-          pt_J[cnt * n3 + p] = J;
-          pt_p[cnt * n3 + p] = psum;
-          pt_pf[cnt * n3 + p] = (float)psum;
-          ++cnt;
-        } else {
-          atomicOr(err, EMD_ERRBIT_PT);
-        }
+        close_atom(J, psum);
         psum = 0.0;
+        for (int k = 1; k < sp.nch; ++k) pch[k] = 0.0;
         hit = false;
       }
       J = Je;
@@ -198,16 +210,16 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
       if (d2f > rmax2f) continue;
       // decisions: FP32 where it is certain, FP64 in the shells
       bool in_p, in_l;
-      double d2 = 0.0;
+      double d2 = 0.0, dx = 0.0, dy = 0.0, dz = 0.0;
       bool have64 = false;
       if (d2f < rp2f - margin) {
         in_p = true;
       } else if (d2f > rp2f + margin) {
         in_p = false;
       } else {
-        const double dx = emd_disp(x, h, Rw[3 * J + 0], img % 3 - 1, L);
-        const double dy = emd_disp(y, h, Rw[3 * J + 1], (img / 3) % 3 - 1, L);
-        const double dz = emd_disp(z, h, Rw[3 * J + 2], img / 9 - 1, L);
+        dx = emd_disp(x, h, Rw[3 * J + 0], img % 3 - 1, L);
+        dy = emd_disp(y, h, Rw[3 * J + 1], (img / 3) % 3 - 1, L);
+        dz = emd_disp(z, h, Rw[3 * J + 2], img / 9 - 1, L);
         d2 = emd_norm2(dx, dy, dz);
         have64 = true;
         in_p = d2 < rp2;
@@ -218,9 +230,9 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
         in_l = false;
       } else {
         if (!have64) {
-          const double dx = emd_disp(x, h, Rw[3 * J + 0], img % 3 - 1, L);
-          const double dy = emd_disp(y, h, Rw[3 * J + 1], (img / 3) % 3 - 1, L);
-          const double dz = emd_disp(z, h, Rw[3 * J + 2], img / 9 - 1, L);
+          dx = emd_disp(x, h, Rw[3 * J + 0], img % 3 - 1, L);
+          dy = emd_disp(y, h, Rw[3 * J + 1], (img / 3) % 3 - 1, L);
+          dz = emd_disp(z, h, Rw[3 * J + 2], img / 9 - 1, L);
           d2 = emd_norm2(dx, dy, dz);
           have64 = true;
         }
@@ -240,9 +252,9 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
         }
       }
       if (!have64 && ((in_l && !g_tab) || (in_p && !F32))) {
-        const double dx = emd_disp(x, h, Rw[3 * J + 0], img % 3 - 1, L);
-        const double dy = emd_disp(y, h, Rw[3 * J + 1], (img / 3) % 3 - 1, L);
-        const double dz = emd_disp(z, h, Rw[3 * J + 2], img / 9 - 1, L);
+        dx = emd_disp(x, h, Rw[3 * J + 0], img % 3 - 1, L);
+        dy = emd_disp(y, h, Rw[3 * J + 1], (img / 3) % 3 - 1, L);
+        dz = emd_disp(z, h, Rw[3 * J + 2], img / 9 - 1, L);
         d2 = emd_norm2(dx, dy, dz);
       }
       if (in_p) {
@@ -265,17 +277,25 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
           pdy += w * ey;
           pdz += w * ez;
         } else {
-          psum += sp.c_p * exp(-d2 * sp.inv_2rc2);
+          const double ex = exp(-d2 * sp.inv_2rc2);
+          psum += sp.c_p * ex;
+          if (sp.nch > 1) {
+            double pk[9];
+            emd_channel_values(sp, dx, dy, dz, ex, pk, nullptr);
+            for (int k = 1; k < sp.nch; ++k) pch[k] += pk[k];
+          }
         }
         hit = true;
       }
       if (in_l) gsum += g_tab ? g_val : sp.c_g * exp(-d2 * sp.inv_a2);
     }
     if (hit) {
-      if (cnt < EMD_PT_KMAX) {
+      if (!F32) {
+        close_atom(J, psum);
+      } else if (cnt < kmax) {
         pt_J[cnt * n3 + p] = J;
-        pt_p[cnt * n3 + p] = F32 ? (double)psumf : psum;
-        pt_pf[cnt * n3 + p] = F32 ? psumf : (float)psum;
+        pt_p[cnt * n3 + p] = (double)psumf;
+        pt_pf[cnt * n3 + p] = psumf;
         ++cnt;
       } else {
         atomicOr(err, EMD_ERRBIT_PT);
@@ -458,20 +478,32 @@ k_atom_table(int pass, int n, double h, double L, const double *Rw,
         const double dx = emd_disp(ix, h, c[0], ni[0], L);
         const double dy = emd_disp(iy, h, c[1], ni[1], L);
         const double dz = emd_disp(iz, h, c[2], ni[2], L);
-        const double pv = sp.c_p * exp(-emd_norm2(dx, dy, dz) * sp.inv_2rc2);
+        const double ex = exp(-emd_norm2(dx, dy, dz) * sp.inv_2rc2);
+        const double pv = sp.c_p * ex;
         at_p[q] = pv;
         double *dd = at_d + 3 * q;
         dd[0] = dx;
         dd[1] = dy;
         dd[2] = dz;
         if (at_rec) {
-          const float2 ps = emd_df_split(pv);
+          // channel 0 (s): p and dp/dR = p d / r_c^2; channels k >= 1 from
+          // the solid harmonics, in list J nch + k at the same position
+          double pk[9], gk[9][3];
+          pk[0] = pv;
           const double pw = pv * sp.inv_rc2;
-          const float2 wx = emd_df_split(pw * dx), wy = emd_df_split(pw * dy),
-                       wz = emd_df_split(pw * dz);
-          at_rec[q] = make_uint4((unsigned)pidx, __float_as_uint(ps.x), __float_as_uint(ps.y), 0u);
-          at_w[2 * q] = make_float4(wx.x, wx.y, wy.x, wy.y);
-          at_w[2 * q + 1] = make_float4(wz.x, wz.y, 0.f, 0.f);
+          gk[0][0] = pw * dx;
+          gk[0][1] = pw * dy;
+          gk[0][2] = pw * dz;
+          if (sp.nch > 1) emd_channel_values(sp, dx, dy, dz, ex, pk, gk);
+          for (int k = 0; k < sp.nch; ++k) {
+            const size_t qk = ((size_t)J * sp.nch + k) * cap + e;
+            const float2 ps = emd_df_split(pk[k]);
+            const float2 wx = emd_df_split(gk[k][0]), wy = emd_df_split(gk[k][1]),
+                         wz = emd_df_split(gk[k][2]);
+            at_rec[qk] = make_uint4((unsigned)pidx, __float_as_uint(ps.x), __float_as_uint(ps.y), 0u);
+            at_w[2 * qk] = make_float4(wx.x, wx.y, wy.x, wy.y);
+            at_w[2 * qk + 1] = make_float4(wz.x, wz.y, 0.f, 0.f);
+          }
         }
       } else {
         atomicOr(err, EMD_ERRBIT_AT);
@@ -795,13 +827,13 @@ void emd_launch_tables(const GridInfo &g, const SpeciesDev &sp, int n_atoms,
                                                 t.tile_cnt, t.tile_ent, t.gtab, t.glo,
                                                 t.pt_cnt, t.pt_J, t.pt_p, t.pt_pf, t.pt4, t.pt4d,
                                                 t.g_ion, t.te_off, t.te_pp, t.te_q,
-                                                err);
+                                                t.kmax, err);
   else
     k_point_table<false><<<ntiles, 512, 0, st>>>(g.n, g.n3, g.h, g.L, t.Rw, sp, margin_pt,
                                                  t.tile_cnt, t.tile_ent, t.gtab, t.glo,
                                                  t.pt_cnt, t.pt_J, t.pt_p, t.pt_pf, t.pt4, t.pt4d,
                                                  t.g_ion, t.te_off, t.te_pp, t.te_q,
-                                                 err);
+                                                 t.kmax, err);
   if (n_atoms > 0 && !t.te_off) {
     dim3 grid(n_atoms, EMD_SPLIT);
     const float margin = emd_fp32_d2_margin(g.L, sp.r_proj);

@@ -34,7 +34,8 @@ class EmdError(RuntimeError):
 
 class emd_species(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in
-                ("z", "mass", "a_loc", "r_loc", "r_c", "h_kb", "r_proj")]
+                ("z", "mass", "a_loc", "r_loc", "r_c", "h_kb", "r_proj")] + [
+                ("lmax", ctypes.c_int), ("h_l", ctypes.c_double * 2)]
 
 
 class emd_config(ctypes.Structure):
@@ -221,8 +222,9 @@ def emd_get_potentials(h, n: int):
     return dict(zip(("v_loc", "v_h", "v_xc", "g_ion"), out))
 
 
-def emd_get_projections(h, n_atoms: int, n_orb: int) -> np.ndarray:
-    c = np.zeros((n_atoms, n_orb), dtype=np.complex128)
+def emd_get_projections(h, n_atoms: int, n_orb: int, n_ch: int = 1) -> np.ndarray:
+    """Projections [n_atoms * n_ch, n_orb]; n_ch = (lmax + 1)^2 projectors per atom."""
+    c = np.zeros((n_atoms * n_ch, n_orb), dtype=np.complex128)
     _check(load().emd_get_projections(h, c.view(np.float64).ctypes.data_as(_DPTR)))
     return c
 
@@ -302,7 +304,9 @@ def config_for(sysin, precision: int = EMD_FP64, stream: int = 0,
                       n_orb=sysin.n_orb, occ=sysin.occ, precision=precision,
                       n_atoms=sysin.n_atoms,
                       species=emd_species(sp.z, sp.mass, sp.a_loc, sp.r_loc,
-                                          sp.r_c, sp.h_kb, sp.r_proj),
+                                          sp.r_c, sp.h_kb, sp.r_proj,
+                                          int(getattr(sp, "lmax", 0)),
+                                          (ctypes.c_double * 2)(*getattr(sp, "h_l", (0.0, 0.0)))),
                       cuda_stream=stream or None,
                       block_orbitals=block_orbitals)
 
