@@ -90,6 +90,72 @@ k_project_grad(const double2 *__restrict__ x, size_t n3, const int *at_cnt,
   }
 }
 
+// complex128, bo = 2: the same sums (c, h_kb c and the three moments dc) in
+// double-float arithmetic on the FP32 pipes from the pre-split atom records
+// (p and p d / r_c^2 as (hi, lo) pairs, as the forward projections and
+// moments use), two entries of a thread in flight; widened to FP64 once and
+// added by the fixed-tree block sum.
+__global__ void __launch_bounds__(256)
+k_project_grad_df(const double2 *__restrict__ x, size_t n3, const int *__restrict__ at_cnt,
+                  const uint4 *__restrict__ at_rec, const float4 *__restrict__ at_w, int cap,
+                  double h3, double h_kb, int n_orb_pad, double2 *c, double2 *hc, double2 *dc) {
+  constexpr int BO = 2, EU = 2;
+  __shared__ double red[8 * 8 * BO];
+  const int J = blockIdx.x, blk = blockIdx.y;
+  const int cnt = at_cnt[J];
+  const double2 *xb = x + (size_t)blk * n3 * BO;
+  const uint4 *rec = at_rec + (size_t)J * cap;
+  const float4 *wr = at_w + (size_t)J * cap * 2;
+  float2 ah[4 * BO], al[4 * BO];     // [orbital][c, dc_x, dc_y, dc_z]
+#pragma unroll
+  for (int k = 0; k < 4 * BO; ++k) ah[k] = al[k] = make_float2(0.f, 0.f);
+  for (int e0 = threadIdx.x; e0 < cnt; e0 += EU * 256) {
+    uint4 r[EU];
+    float4 w0[EU], w1[EU];
+#pragma unroll
+    for (int v = 0; v < EU; ++v) {        // past the end: point 0, zero weights
+      const int e = e0 + 256 * v;
+      const bool ok = e < cnt;
+      r[v] = ok ? __ldg(rec + e) : make_uint4(0u, 0u, 0u, 0u);
+      w0[v] = ok ? __ldg(wr + 2 * e) : make_float4(0.f, 0.f, 0.f, 0.f);
+      w1[v] = ok ? __ldg(wr + 2 * e + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    double2 xv[EU][BO];
+#pragma unroll
+    for (int v = 0; v < EU; ++v)
+#pragma unroll
+      for (int j = 0; j < BO; ++j) xv[v][j] = xb[(size_t)r[v].x * BO + j];
+#pragma unroll
+    for (int v = 0; v < EU; ++v)
+#pragma unroll
+      for (int j = 0; j < BO; ++j) {
+        const float4 xs = df_split2(xv[v][j]);
+        dfp_add_prod(ah[4 * j + 0], al[4 * j + 0], __uint_as_float(r[v].y),
+                     __uint_as_float(r[v].z), f4hi(xs), f4lo(xs));
+        dfp_add_prod(ah[4 * j + 1], al[4 * j + 1], w0[v].x, w0[v].y, f4hi(xs), f4lo(xs));
+        dfp_add_prod(ah[4 * j + 2], al[4 * j + 2], w0[v].z, w0[v].w, f4hi(xs), f4lo(xs));
+        dfp_add_prod(ah[4 * j + 3], al[4 * j + 3], w1[v].x, w1[v].y, f4hi(xs), f4lo(xs));
+      }
+  }
+  double acc[8 * BO];
+#pragma unroll
+  for (int k = 0; k < 4 * BO; ++k) {
+    acc[2 * k] = __dadd_rn(df_widen(ah[k].x), df_widen(al[k].x));
+    acc[2 * k + 1] = __dadd_rn(df_widen(ah[k].y), df_widen(al[k].y));
+  }
+  emd_block_sum<8 * BO>(acc, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < BO; ++j) {
+      const size_t o = (size_t)J * n_orb_pad + (size_t)blk * BO + j;
+      c[o] = make_double2(h3 * acc[8 * j], h3 * acc[8 * j + 1]);
+      hc[o] = make_double2(h_kb * h3 * acc[8 * j], h_kb * h3 * acc[8 * j + 1]);
+      for (int a = 0; a < 3; ++a)
+        dc[3 * o + a] = make_double2(h3 * acc[8 * j + 2 + 2 * a], h3 * acc[8 * j + 3 + 2 * a]);
+    }
+  }
+}
+
 // gR[J][a] += coef * Im sum_A [conj(dcm) cu + conj(cm) dcu]
 __global__ void k_proj_sens(const double2 *cm, const double2 *dcm,
                             const double2 *cu, const double2 *dcu, int n_atoms,
@@ -191,7 +257,13 @@ void emd_adj_project_grad(const OrbLayout &o, const TableSet &t, int n_atoms,
   dim3 grid(n_atoms, o.n_blk);
   switch (o.bo) {
     case 1: k_project_grad<1><<<grid, 256, 0, st>>>(x, (size_t)o.n3, t.at_cnt, t.at_pt, t.at_p, t.at_d, t.cap, h3, h_kb, inv_rc2, o.n_orb_pad, c, hc, dc); break;
-    case 2: k_project_grad<2><<<grid, 256, 0, st>>>(x, (size_t)o.n3, t.at_cnt, t.at_pt, t.at_p, t.at_d, t.cap, h3, h_kb, inv_rc2, o.n_orb_pad, c, hc, dc); break;
+    case 2:
+      if (t.at_rec)
+        k_project_grad_df<<<grid, 256, 0, st>>>(x, (size_t)o.n3, t.at_cnt, t.at_rec, t.at_w,
+                                                t.cap, h3, h_kb, o.n_orb_pad, c, hc, dc);
+      else
+        k_project_grad<2><<<grid, 256, 0, st>>>(x, (size_t)o.n3, t.at_cnt, t.at_pt, t.at_p, t.at_d, t.cap, h3, h_kb, inv_rc2, o.n_orb_pad, c, hc, dc);
+      break;
     case 4: k_project_grad<4><<<grid, 256, 0, st>>>(x, (size_t)o.n3, t.at_cnt, t.at_pt, t.at_p, t.at_d, t.cap, h3, h_kb, inv_rc2, o.n_orb_pad, c, hc, dc); break;
   }
 }
