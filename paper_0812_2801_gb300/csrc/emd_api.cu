@@ -619,6 +619,9 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
     t.te_pp = nullptr;
     t.te_q = nullptr;
     t.pt4d = nullptr;
+    t.pt_rec = nullptr;
+    if (c.precision == EMD_FP64 && o.bo == 2 && s->sp.nch > 1)
+      TRY(A((void **)&t.pt_rec, n3 * t.kmax * sizeof(int4)));
     if (c.precision == EMD_FP64 && o.bo == 2) TRY(A((void **)&t.pt4d, n3 * 3 * sizeof(int4)));
     if (c.precision == EMD_FP32_ORBITALS) {
       TRY(A((void **)&t.te_off, (size_t)ntiles * (EMD_TILE_ATOM_MAX + 1) * 4));

@@ -102,6 +102,10 @@ struct TableSet {
   // p_2 lo, p_3 hi, p_3 lo) with p in double-float (unused entries 0);
   // NULL for other layouts
   int4 *pt4d;
+  // complex128 with several projectors per atom: every entry as (P, p hi,
+  // p lo, 0), [kmax][n3], for the stage's entries past the first four;
+  // NULL otherwise
+  int4 *pt_rec;
   int *at_cnt;      // [n_atoms] (projector P's list: at_cnt[P / n_ch])
   int *split_cnt;   // [n_atoms][EMD_SPLIT] hits per range (table building)
   int *at_pt;       // [n_atoms][cap] flat grid index

@@ -1414,12 +1414,16 @@ template <int M> struct DFTile {
   static constexpr size_t SMEM_FIXED = 3 * (size_t)RSLOT + 2 * (size_t)DSLOT;
 };
 
-template <int M, bool HCS>
+// MP: several projectors per atom (the pre-split records past the first four
+// are read with four in flight); a separate instantiation keeps the
+// s-projector kernel's registers as they were
+template <int M, bool HCS, bool MP>
 __global__ void __launch_bounds__(512, 1)
 k_stage_df(const double2 *__restrict__ u_in, const double2 *__restrict__ psi0,
            double2 *__restrict__ u_out, const double *__restrict__ v_eff,
            const int4 *__restrict__ pt4d, const int *__restrict__ pt_J,
-           const double *__restrict__ pt_p, const double2 *__restrict__ hc, int n,
+           const double *__restrict__ pt_p, const int4 *__restrict__ pt_rec,
+           const double2 *__restrict__ hc, int n,
            int ntx, int zc, int n_orb_pad, int n_atoms, double a, int apply_only,
            DFWeights W) {
   typedef DFTile<M> Z;
@@ -1586,12 +1590,36 @@ k_stage_df(const double2 *__restrict__ u_in, const double2 *__restrict__ psi0,
       const int cnt = q0.x >> 16;
       if (cnt > 4) {
         const size_t p = (size_t)(z0 + zi - 2 * M) * n2 + pxy;
-        for (int e = 4; e < cnt; ++e) {
-          const int J = pt_J[(size_t)e * n3 + p];
-          const float2 pv = df_split(pt_p[(size_t)e * n3 + p]);
-          const float4 h4 = HCS ? *reinterpret_cast<const float4 *>(hcj + J * (BO * 16))
-                                : df_split2(hcg[(size_t)J * n_orb_pad]);
-          dfp_add_prod(hh, hl, pv.x, pv.y, f4hi(h4), f4lo(h4));
+        if (MP) {
+          // several projectors per atom: pre-split 16-byte records, four in
+          // flight, summed into four independent pairs (combined in a fixed
+          // order) so that the TwoSum chains overlap
+          float2 xh[4], xl[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) xh[v] = xl[v] = make_float2(0.f, 0.f);
+          for (int e = 4; e < cnt; e += 4) {
+            int4 q[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              q[v] = e + v < cnt ? __ldg(pt_rec + (size_t)(e + v) * n3 + p) : make_int4(0, 0, 0, 0);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              const float4 h4 = HCS ? *reinterpret_cast<const float4 *>(hcj + q[v].x * (BO * 16))
+                                    : df_split2(hcg[(size_t)q[v].x * n_orb_pad]);
+              dfp_add_prod(xh[v], xl[v], __int_as_float(q[v].y), __int_as_float(q[v].z),
+                           f4hi(h4), f4lo(h4));
+            }
+          }
+#pragma unroll
+          for (int v = 0; v < 4; ++v) dfp_add(hh, hl, xh[v], xl[v]);
+        } else {
+          for (int e = 4; e < cnt; ++e) {
+            const int J = pt_J[(size_t)e * n3 + p];
+            const float2 pv = df_split(pt_p[(size_t)e * n3 + p]);
+            const float4 h4 = HCS ? *reinterpret_cast<const float4 *>(hcj + J * (BO * 16))
+                                  : df_split2(hcg[(size_t)J * n_orb_pad]);
+            dfp_add_prod(hh, hl, pv.x, pv.y, f4hi(h4), f4lo(h4));
+          }
         }
       }
       const double Hr = __dadd_rn(df_widen(hh.x), df_widen(hl.x));
@@ -1954,12 +1982,12 @@ void stage_z_m(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
   }
 }
 
-template <int M, bool HCS>
+template <int M, bool HCS, bool MP>
 void stage_df_tt(const OrbLayout &o, const StageArgs &a, size_t smem, cudaStream_t st) {
   typedef DFTile<M> Z;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(k_stage_df<M, HCS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_stage_df<M, HCS, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(Z::SMEM_FIXED + 32768));
     attr_done = true;
   }
@@ -1973,9 +2001,9 @@ void stage_df_tt(const OrbLayout &o, const StageArgs &a, size_t smem, cudaStream
   W.dvs = -2.0 * o.h * o.h * o.den;
   W.dv0 = 3.0 * o.num[0];
   dim3 grid(ntx * nty, (o.n + zc - 1) / zc, o.n_blk);
-  k_stage_df<M, HCS><<<grid, Z::NT, smem, st>>>(
+  k_stage_df<M, HCS, MP><<<grid, Z::NT, smem, st>>>(
       (const double2 *)a.u_in, (const double2 *)a.psi0, (double2 *)a.u_out,
-      (const double *)a.v_eff, a.tab->pt4d, a.tab->pt_J, a.tab->pt_p,
+      (const double *)a.v_eff, a.tab->pt4d, a.tab->pt_J, a.tab->pt_p, a.tab->pt_rec,
       (const double2 *)a.hc, o.n, ntx, zc, o.n_orb_pad, o.n_proj, a.a, a.apply_only, W);
 }
 
@@ -1983,10 +2011,14 @@ template <int M>
 void stage_df_t(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {
   typedef DFTile<M> Z;
   const int hc_bytes = o.n_proj * Z::BO * (int)sizeof(float4);   // every projector's h c
-  if (hc_bytes <= 32768)
-    stage_df_tt<M, true>(o, a, Z::SMEM_FIXED + hc_bytes, st);
-  else
-    stage_df_tt<M, false>(o, a, Z::SMEM_FIXED, st);
+  const bool mp = a.tab->pt_rec != nullptr;
+  if (hc_bytes <= 32768) {
+    if (mp) stage_df_tt<M, true, true>(o, a, Z::SMEM_FIXED + hc_bytes, st);
+    else stage_df_tt<M, true, false>(o, a, Z::SMEM_FIXED + hc_bytes, st);
+  } else {
+    if (mp) stage_df_tt<M, false, true>(o, a, Z::SMEM_FIXED, st);
+    else stage_df_tt<M, false, false>(o, a, Z::SMEM_FIXED, st);
+  }
 }
 
 inline void stage_df_m(const OrbLayout &o, const StageArgs &a, cudaStream_t st) {

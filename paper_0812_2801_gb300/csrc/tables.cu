@@ -104,7 +104,8 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
               SpeciesDev sp, float margin, const int *tile_cnt, const int *tile_ent,
               const double *gtab, const int *glo,
               int *pt_cnt, int *pt_J, double *pt_p, float *pt_pf, int2 *pt4, int4 *pt4d,
-              double *g_ion, int *te_off, uint2 *te_pp, float4 *te_q, int kmax, int *err) {
+              double *g_ion, int *te_off, uint2 *te_pp, float4 *te_q, int kmax, int4 *pt_rec,
+              int *err) {
   __shared__ int cand[EMD_TILE_CAND_MAX];
   __shared__ float cfs[EMD_TILE_CAND_MAX][3];
   __shared__ float cfl[F32 ? EMD_TILE_CAND_MAX : 1][3];   // low parts of the centres
@@ -179,6 +180,11 @@ k_point_table(int n, int n3, double h, double L, const double *Rw,
         pt_J[cnt * n3 + p] = J * sp.nch + k;
         pt_p[cnt * n3 + p] = v;
         pt_pf[cnt * n3 + p] = (float)v;
+        if (pt_rec) {
+          const float2 vs = emd_df_split(v);
+          pt_rec[(size_t)cnt * n3 + p] =
+              make_int4(J * sp.nch + k, __float_as_int(vs.x), __float_as_int(vs.y), 0);
+        }
         ++cnt;
       } else {
         atomicOr(err, EMD_ERRBIT_PT);
@@ -827,13 +833,13 @@ void emd_launch_tables(const GridInfo &g, const SpeciesDev &sp, int n_atoms,
                                                 t.tile_cnt, t.tile_ent, t.gtab, t.glo,
                                                 t.pt_cnt, t.pt_J, t.pt_p, t.pt_pf, t.pt4, t.pt4d,
                                                 t.g_ion, t.te_off, t.te_pp, t.te_q,
-                                                t.kmax, err);
+                                                t.kmax, nullptr, err);
   else
     k_point_table<false><<<ntiles, 512, 0, st>>>(g.n, g.n3, g.h, g.L, t.Rw, sp, margin_pt,
                                                  t.tile_cnt, t.tile_ent, t.gtab, t.glo,
                                                  t.pt_cnt, t.pt_J, t.pt_p, t.pt_pf, t.pt4, t.pt4d,
                                                  t.g_ion, t.te_off, t.te_pp, t.te_q,
-                                                 t.kmax, err);
+                                                 t.kmax, t.pt_rec, err);
   if (n_atoms > 0 && !t.te_off) {
     dim3 grid(n_atoms, EMD_SPLIT);
     const float margin = emd_fp32_d2_margin(g.L, sp.r_proj);
