@@ -81,3 +81,32 @@ def test_binding_declares_argument_types(lib):
         if args.strip() in ("", "void"):
             continue
         assert getattr(lib, name).argtypes is not None, name
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of emd_species, emd_config, emd_energy and
+    emd_gs_info have the C compiler's size and field offsets."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"emd_species": emd.emd_species, "emd_config": emd.emd_config,
+               "emd_energy": emd.emd_energy, "emd_gs_info": emd.emd_gs_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "emd.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f in cls._fields_:
+            lines.append(f'  printf("{name}.{f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], check=True,
+                                                         capture_output=True, text=True).stdout.split("\n") if l)
+    for name, cls in structs.items():
+        assert int(out[name]) == ctypes.sizeof(cls), name
+        for f in cls._fields_:
+            assert int(out[f"{name}.{f[0]}"]) == getattr(cls, f[0]).offset, (name, f[0])
