@@ -1718,7 +1718,7 @@ k_nl_force_df(const double2 *__restrict__ u, size_t n3, int n_blk,
               const int *__restrict__ at_cnt, const uint4 *__restrict__ at_rec,
               const float4 *__restrict__ at_w, int cap, int nch, const double2 *__restrict__ c,
               int n_orb_pad, int n_orb, double h3, double3 coef3, double *part) {
-  constexpr int BO = 2, EU = DF_EU / 2;
+  constexpr int BO = 2, EU = DF_EU;
   __shared__ double red[8 * 6 * BO];
   const int P = blockIdx.x, blk = blockIdx.y;
   const int cnt = at_cnt[P / nch];
