@@ -366,9 +366,12 @@ int emd_get_dipole(emd_system *s, double *D);
  * gap to the first unoccupied Ritz value (the subspace carries
  * max(4, n_orb/10) buffer states above the occupied ones); rho,
  * v_Hxc and F are recomputed from the new orbitals by the next call that
- * reads them (as after emd_set_orbitals).  The subspace products use cuBLAS
- * (in the orbital precision) and the n_orb x n_orb eigenproblem cuSOLVER (in
- * FP64).  Errors: EMD_EINVAL, EMD_ESTATE (ions or orbitals not set),
+ * reads them (as after emd_set_orbitals).  The subspace products X^H X,
+ * X^H H X and X V are the library's own kernels (FP64 sums, in a fixed
+ * order); the m x m generalized eigenproblem is solved on the host
+ * (Cholesky of the overlap, cyclic Jacobi rotations), m = n_orb + the
+ * buffer states; no vendor library is called.
+ * Errors: EMD_EINVAL, EMD_ESTATE (ions or orbitals not set),
  * EMD_ENOTCONV (tolerance not reached; the orbitals are the last iterate),
  * EMD_ECUDA (including a subspace that lost rank). */
 typedef struct {

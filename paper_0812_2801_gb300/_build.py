@@ -64,7 +64,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         run([nvcc()] + ARCH + ["-shared", "-o", LIB] + objs +
-            ["-lcudart", "-lcublas", "-lcusolver"])
+            ["-lcudart"])
     return LIB
 
 

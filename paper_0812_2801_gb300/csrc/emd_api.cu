@@ -16,6 +16,7 @@
 // read-out and the ground-state solver (driver; element-wise kernels in
 // groundstate.cu).
 #include <algorithm>
+#include <complex>
 #include <atomic>
 #include <cstdarg>
 #include <cmath>
@@ -25,8 +26,6 @@
 #include <string>
 #include <utility>
 #include <vector>
-#include <cublas_v2.h>
-#include <cusolverDn.h>
 #include "emd_internal.cuh"
 
 namespace {
@@ -2034,14 +2033,8 @@ struct GroundStateWork {
   double2 *c = nullptr;                    // projections of the subspace
   void *hc = nullptr;
   double2 *part = nullptr;                 // per-tile projection partials
-  cublasHandle_t blas = nullptr;
-  cusolverDnHandle_t solver = nullptr;
-  void *S = nullptr, *Hs = nullptr, *V = nullptr;   // m x m, orbital precision
-  double2 *Sz = nullptr, *Hz = nullptr;             // m x m, FP64
-  double *w = nullptr;                              // Ritz values
-  double2 *work = nullptr;
-  int lwork = 0;
-  int *dinfo = nullptr;
+  double2 *Sz = nullptr, *Hz = nullptr;             // m x m, FP64 (Hz: then V)
+  double2 *gpart = nullptr;                         // subspace-product partials
   double *rho_in = nullptr, *rho_out = nullptr;
   double *hr[kHist] = {}, *hf[kHist] = {};          // rho_in and F = rho_out - rho_in
   std::vector<void *> mem;
@@ -2051,8 +2044,6 @@ namespace {
 
 void gs_release(GroundStateWork *g) {
   if (!g) return;
-  if (g->blas) cublasDestroy(g->blas);
-  if (g->solver) cusolverDnDestroy(g->solver);
   for (void *p : g->mem) cudaFree(p);
   delete g;
 }
@@ -2083,28 +2074,19 @@ int gs_setup(emd_system *s) {
     g->mem.push_back(*p);
     return true;
   };
-  bool ok = cublasCreate(&g->blas) == CUBLAS_STATUS_SUCCESS &&
-            cusolverDnCreate(&g->solver) == CUSOLVER_STATUS_SUCCESS;
-  ok = ok && A(&g->A, set_bytes) && A(&g->B, set_bytes) && A(&g->C, set_bytes) &&
+  bool ok = A(&g->A, set_bytes) && A(&g->B, set_bytes) && A(&g->C, set_bytes) &&
        A((void **)&g->c, na * g->og.n_orb_pad * sizeof(double2)) &&
        A(&g->hc, na * g->og.n_orb_pad * esz) &&
        A((void **)&g->part, ntiles * EMD_TILE_ATOM_MAX * g->og.n_orb_pad * sizeof(double2)) &&
-       A(&g->S, (size_t)m * m * esz) && A(&g->Hs, (size_t)m * m * esz) &&
-       A(&g->V, (size_t)m * m * esz) && A((void **)&g->Sz, (size_t)m * m * 16) &&
-       A((void **)&g->Hz, (size_t)m * m * 16) && A((void **)&g->w, (size_t)m * 8) &&
-       A((void **)&g->dinfo, sizeof(int)) && A((void **)&g->rho_in, n3 * 8) &&
+       A((void **)&g->Sz, (size_t)m * m * 16) && A((void **)&g->Hz, (size_t)m * m * 16) &&
+       A((void **)&g->gpart, emd_gram_scratch((int)n3, m) * sizeof(double2)) &&
+       A((void **)&g->rho_in, n3 * 8) &&
        A((void **)&g->rho_out, n3 * 8);
   for (int k = 0; ok && k < GroundStateWork::kHist; ++k)
     ok = A((void **)&g->hr[k], n3 * 8) && A((void **)&g->hf[k], n3 * 8);
-  if (ok)
-    ok = cusolverDnZhegvd_bufferSize(g->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
-                                     CUBLAS_FILL_MODE_LOWER, m, (cuDoubleComplex *)g->Hz, m,
-                                     (cuDoubleComplex *)g->Sz, m, g->w,
-                                     &g->lwork) == CUSOLVER_STATUS_SUCCESS;
-  ok = ok && A((void **)&g->work, (size_t)std::max(1, g->lwork) * 16);
   if (!ok) {
     gs_release(g);
-    return fail(EMD_ENOMEM, "ground-state workspace: allocation or library set-up failed");
+    return fail(EMD_ENOMEM, "ground-state workspace: allocation failed");
   }
   s->gsw = g;
   return EMD_OK;
@@ -2177,6 +2159,112 @@ int gs_filter(emd_system *s, int m, double a, double b, double a0) {
   return launch_check("ground state Chebyshev filter");
 }
 
+// The m x m generalized Hermitian eigenproblem H v = lambda S v of the
+// Rayleigh-Ritz step, on the host (column-major): the Cholesky factor S = L
+// L^H, A = L^-1 H L^-H, cyclic Jacobi rotations A <- U^H A U (each a phase
+// that makes A_pq real times a real plane rotation that zeroes it) until
+// the off-diagonal part is below 1e-15 of the largest diagonal entry, then
+// v = L^-H w.  Returns the eigenvalues ascending with their S-orthonormal
+// vectors; false if S is not positive definite.
+bool hermitian_generalized_eig(int m, const std::vector<std::complex<double>> &H,
+                               const std::vector<std::complex<double>> &S,
+                               std::vector<double> &w,
+                               std::vector<std::complex<double>> &V) {
+  typedef std::complex<double> cd;
+  auto at = [m](std::vector<cd> &M, int i, int j) -> cd & { return M[(size_t)j * m + i]; };
+  std::vector<cd> L((size_t)m * m, 0.0), Sc(S), Hc(H);
+  for (int j = 0; j < m; ++j) {                 // Cholesky, lower
+    double d = at(Sc, j, j).real();
+    for (int k = 0; k < j; ++k) d -= std::norm(at(L, j, k));
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    at(L, j, j) = ljj;
+    for (int i = j + 1; i < m; ++i) {
+      cd v = at(Sc, i, j);
+      for (int k = 0; k < j; ++k) v -= at(L, i, k) * std::conj(at(L, j, k));
+      at(L, i, j) = v / ljj;
+    }
+  }
+  // Y = L^-1 H (forward substitution per column), then A = L^-1 Y^H (= (Y L^-H)^H)
+  std::vector<cd> Y((size_t)m * m), A((size_t)m * m);
+  auto lsolve = [&](std::vector<cd> &B, std::vector<cd> &X) {
+    for (int c = 0; c < m; ++c)
+      for (int i = 0; i < m; ++i) {
+        cd v = at(B, i, c);
+        for (int k = 0; k < i; ++k) v -= at(L, i, k) * at(X, k, c);
+        at(X, i, c) = v / at(L, i, i);
+      }
+  };
+  lsolve(Hc, Y);
+  std::vector<cd> Yh((size_t)m * m);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) at(Yh, i, j) = std::conj(at(Y, j, i));
+  lsolve(Yh, A);
+  for (int i = 0; i < m; ++i) {                 // A is Hermitian up to rounding
+    at(A, i, i) = at(A, i, i).real();
+    for (int j = i + 1; j < m; ++j) {
+      const cd v = 0.5 * (at(A, i, j) + std::conj(at(A, j, i)));
+      at(A, i, j) = v;
+      at(A, j, i) = std::conj(v);
+    }
+  }
+  std::vector<cd> W((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) at(W, i, i) = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, dmax = 0.0;
+    for (int j = 0; j < m; ++j) {
+      dmax = std::max(dmax, std::abs(at(A, j, j).real()));
+      for (int i = 0; i < j; ++i) off = std::max(off, std::abs(at(A, i, j)));
+    }
+    if (off <= 1e-15 * std::max(dmax, 1e-300)) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const cd apq = at(A, p, q);
+        const double r = std::abs(apq);
+        if (r == 0.0) continue;
+        const cd u = apq / r;                   // A_pq = r u
+        const double tau = (at(A, q, q).real() - at(A, p, p).real()) / (2.0 * r);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (std::abs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
+        // U on (p, q) = [[c, sn], [-sn conj(u), c conj(u)]]
+        const cd upp = c, upq = sn, uqp = -sn * std::conj(u), uqq = c * std::conj(u);
+        for (int k = 0; k < m; ++k) {           // A <- A U, W <- W U
+          const cd ap = at(A, k, p), aq = at(A, k, q);
+          at(A, k, p) = ap * upp + aq * uqp;
+          at(A, k, q) = ap * upq + aq * uqq;
+          const cd wp = at(W, k, p), wq = at(W, k, q);
+          at(W, k, p) = wp * upp + wq * uqp;
+          at(W, k, q) = wp * upq + wq * uqq;
+        }
+        for (int k = 0; k < m; ++k) {           // A <- U^H A
+          const cd bp = at(A, p, k), bq = at(A, q, k);
+          at(A, p, k) = std::conj(upp) * bp + std::conj(uqp) * bq;
+          at(A, q, k) = std::conj(upq) * bp + std::conj(uqq) * bq;
+        }
+        at(A, p, q) = at(A, q, p) = 0.0;
+        at(A, p, p) = at(A, p, p).real();
+        at(A, q, q) = at(A, q, q).real();
+      }
+  }
+  std::vector<int> ord(m);
+  for (int i = 0; i < m; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+    return at(A, a, a).real() < at(A, b, b).real();
+  });
+  w.resize(m);
+  V.assign((size_t)m * m, 0.0);
+  for (int c = 0; c < m; ++c) {
+    const int k = ord[c];
+    w[c] = at(A, k, k).real();
+    for (int i = m - 1; i >= 0; --i) {          // v = L^-H w_k (back substitution)
+      cd v = at(W, i, k);
+      for (int j = i + 1; j < m; ++j) v -= std::conj(at(L, j, i)) * at(V, j, c);
+      at(V, i, c) = v / at(L, i, i);
+    }
+  }
+  return true;
+}
+
 // A <- Rayleigh-Ritz vectors of span(A) (h^3-orthonormal, ascending Ritz
 // values into eps); on return B holds them canonically (column-major
 // n3 x m), so the occupied ones are its first n_occ columns.
@@ -2187,60 +2275,22 @@ int gs_rayleigh_ritz(emd_system *s, std::vector<double> &eps) {
   const int n3 = s->g.n3;
   const double h3 = s->g.h * s->g.h * s->g.h;
   const bool f64 = s->o.prec == EMD_FP64;
-  if (cublasSetStream(g->blas, s->st) != CUBLAS_STATUS_SUCCESS ||
-      cusolverDnSetStream(g->solver, s->st) != CUSOLVER_STATUS_SUCCESS)
-    return fail(EMD_ECUDA, "cannot bind the subspace libraries to the stream");
   gs_apply(s, g->A, g->B);
   gs_unpack(og, g->A, g->C, m, s->st);      // X (canonical) in C
   gs_unpack(og, g->B, g->A, m, s->st);      // H X (canonical) in A
-  bool ok;
-  if (f64) {
-    const cuDoubleComplex al = {h3, 0.0}, be = {0.0, 0.0};
-    const cuDoubleComplex *X = (const cuDoubleComplex *)g->C;
-    ok = cublasZgemm(g->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, m, n3, &al, X, n3, X, n3, &be,
-                     (cuDoubleComplex *)g->Sz, m) == CUBLAS_STATUS_SUCCESS &&
-         cublasZgemm(g->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, m, n3, &al, X, n3,
-                     (const cuDoubleComplex *)g->A, n3, &be, (cuDoubleComplex *)g->Hz,
-                     m) == CUBLAS_STATUS_SUCCESS;
-  } else {
-    const cuComplex al = {(float)h3, 0.f}, be = {0.f, 0.f};
-    const cuComplex *X = (const cuComplex *)g->C;
-    ok = cublasCgemm(g->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, m, n3, &al, X, n3, X, n3, &be,
-                     (cuComplex *)g->S, m) == CUBLAS_STATUS_SUCCESS &&
-         cublasCgemm(g->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, m, n3, &al, X, n3,
-                     (const cuComplex *)g->A, n3, &be, (cuComplex *)g->Hs,
-                     m) == CUBLAS_STATUS_SUCCESS;
-    emd_launch_widen((size_t)m * m, (const float2 *)g->S, g->Sz, s->st);
-    emd_launch_widen((size_t)m * m, (const float2 *)g->Hs, g->Hz, s->st);
-  }
-  if (!ok) return fail(EMD_ECUDA, "subspace product (cuBLAS) failed");
-  if (cusolverDnZhegvd(g->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
-                       CUBLAS_FILL_MODE_LOWER, m, (cuDoubleComplex *)g->Hz, m,
-                       (cuDoubleComplex *)g->Sz, m, g->w, (cuDoubleComplex *)g->work,
-                       g->lwork, g->dinfo) != CUSOLVER_STATUS_SUCCESS)
-    return fail(EMD_ECUDA, "subspace eigenproblem (cuSOLVER) failed");
-  int info = 0;
-  eps.resize(m);
-  CK(cudaMemcpyAsync(&info, g->dinfo, sizeof(int), cudaMemcpyDeviceToHost, s->st));
-  CK(cudaMemcpyAsync(eps.data(), g->w, (size_t)m * 8, cudaMemcpyDeviceToHost, s->st));
+  const int prec = f64 ? EMD_FP64 : EMD_FP32_ORBITALS;
+  emd_launch_gram(prec, g->C, g->C, n3, m, h3, g->gpart, g->Sz, s->st);
+  emd_launch_gram(prec, g->C, g->A, n3, m, h3, g->gpart, g->Hz, s->st);
+  std::vector<std::complex<double>> Sh((size_t)m * m), Hh((size_t)m * m), Vh;
+  CK(cudaMemcpyAsync(Sh.data(), g->Sz, (size_t)m * m * 16, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemcpyAsync(Hh.data(), g->Hz, (size_t)m * m * 16, cudaMemcpyDeviceToHost, s->st));
   CK(cudaStreamSynchronize(s->st));
-  if (info != 0)
-    return fail(EMD_ECUDA, "subspace eigenproblem: info %d (the filtered set lost rank)",
-                info);
-  // X V (V = eigenvectors, in Hz) into B (canonical), packed into A
-  if (f64) {
-    const cuDoubleComplex one = {1.0, 0.0}, zero = {0.0, 0.0};
-    ok = cublasZgemm(g->blas, CUBLAS_OP_N, CUBLAS_OP_N, n3, m, m, &one,
-                     (const cuDoubleComplex *)g->C, n3, (const cuDoubleComplex *)g->Hz, m,
-                     &zero, (cuDoubleComplex *)g->B, n3) == CUBLAS_STATUS_SUCCESS;
-  } else {
-    const cuComplex one = {1.f, 0.f}, zero = {0.f, 0.f};
-    emd_launch_narrow((size_t)m * m, g->Hz, (float2 *)g->V, s->st);
-    ok = cublasCgemm(g->blas, CUBLAS_OP_N, CUBLAS_OP_N, n3, m, m, &one,
-                     (const cuComplex *)g->C, n3, (const cuComplex *)g->V, m, &zero,
-                     (cuComplex *)g->B, n3) == CUBLAS_STATUS_SUCCESS;
-  }
-  if (!ok) return fail(EMD_ECUDA, "subspace rotation (cuBLAS) failed");
+  if (!hermitian_generalized_eig(m, Hh, Sh, eps, Vh))
+    return fail(EMD_ECUDA, "subspace eigenproblem: the overlap matrix is not positive "
+                           "definite (the filtered set lost rank)");
+  // X V (V = eigenvectors, ascending Ritz values) into B (canonical), packed into A
+  CK(cudaMemcpyAsync(g->Hz, Vh.data(), (size_t)m * m * 16, cudaMemcpyHostToDevice, s->st));
+  emd_launch_rotate(prec, g->C, g->Hz, n3, m, g->B, s->st);
   gs_pack(og, g->B, g->A, m, s->st);
   return launch_check("ground state Rayleigh-Ritz");
 }

@@ -343,6 +343,16 @@ void emd_launch_comb(int n3, const EmdComb &cb, double *out, cudaStream_t st);
 void emd_launch_absdiff_partials(int n3, const double *a, const double *b, double *part,
                                  int nblocks, cudaStream_t st);
 void emd_launch_widen(size_t n, const float2 *a, double2 *b, cudaStream_t st);
+// Rayleigh-Ritz products over canonical column-major sets (column i at
+// X + i n3; complex128 for EMD_FP64, complex64 otherwise): G = scale X^H Y
+// (m x m, column-major FP64, summed in FP64 in a fixed order; part holds
+// emd_gram_scratch(n3, m) double2), and B = X V (V column-major FP64)
+int emd_gram_chunks(int n3);
+size_t emd_gram_scratch(int n3, int m);
+void emd_launch_gram(int prec, const void *X, const void *Y, int n3, int m, double scale,
+                     double2 *part, double2 *G, cudaStream_t st);
+void emd_launch_rotate(int prec, const void *X, const double2 *V, int n3, int m, void *B,
+                       cudaStream_t st);
 void emd_launch_narrow(size_t n, const double2 *a, float2 *b, cudaStream_t st);
 // columns c0 .. c1-1 of a canonical (n3 x m, column-major) orbital array
 // filled with uniform values in [-1, 1) (counter hash of seed and index)
