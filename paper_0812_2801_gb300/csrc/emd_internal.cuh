@@ -342,7 +342,6 @@ void emd_launch_comb(int n3, const EmdComb &cb, double *out, cudaStream_t st);
 // part[b] = block sums of |a - b|
 void emd_launch_absdiff_partials(int n3, const double *a, const double *b, double *part,
                                  int nblocks, cudaStream_t st);
-void emd_launch_widen(size_t n, const float2 *a, double2 *b, cudaStream_t st);
 // Rayleigh-Ritz products over canonical column-major sets (column i at
 // X + i n3; complex128 for EMD_FP64, complex64 otherwise): G = scale X^H Y
 // (m x m, column-major FP64, summed in FP64 in a fixed order; part holds
@@ -353,7 +352,6 @@ void emd_launch_gram(int prec, const void *X, const void *Y, int n3, int m, doub
                      double2 *part, double2 *G, cudaStream_t st);
 void emd_launch_rotate(int prec, const void *X, const double2 *V, int n3, int m, void *B,
                        cudaStream_t st);
-void emd_launch_narrow(size_t n, const double2 *a, float2 *b, cudaStream_t st);
 // columns c0 .. c1-1 of a canonical (n3 x m, column-major) orbital array
 // filled with uniform values in [-1, 1) (counter hash of seed and index)
 void emd_launch_fill_random(int prec, void *canon, size_t n3, int c0, int c1, unsigned seed,

@@ -50,16 +50,6 @@ k_absdiff(int n, const double *__restrict__ a, const double *__restrict__ b,
   if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
 }
 
-__global__ void k_widen(size_t n, const float2 *__restrict__ a, double2 *__restrict__ b) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = make_double2(a[i].x, a[i].y);
-}
-
-__global__ void k_narrow(size_t n, const double2 *__restrict__ a, float2 *__restrict__ b) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
-}
-
 // columns c0 .. c1-1 of a canonical (column-major n3 x m) set: uniform
 // values in [-1, 1) from a counter hash of (seed, element index)
 template <typename V>
@@ -233,16 +223,6 @@ void emd_launch_absdiff_partials(int n3, const double *a, const double *b, doubl
                                  int nblocks, cudaStream_t st) {
   emd_note_launches(1);
   k_absdiff<<<nblocks, 256, 0, st>>>(n3, a, b, part);
-}
-
-void emd_launch_widen(size_t n, const float2 *a, double2 *b, cudaStream_t st) {
-  emd_note_launches(1);
-  k_widen<<<blocks(n), 256, 0, st>>>(n, a, b);
-}
-
-void emd_launch_narrow(size_t n, const double2 *a, float2 *b, cudaStream_t st) {
-  emd_note_launches(1);
-  k_narrow<<<blocks(n), 256, 0, st>>>(n, a, b);
 }
 
 void emd_launch_fill_random(int prec, void *canon, size_t n3, int c0, int c1, unsigned seed,
