@@ -110,3 +110,15 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(out[name]) == ctypes.sizeof(cls), name
         for f in cls._fields_:
             assert int(out[f"{name}.{f[0]}"]) == getattr(cls, f[0]).offset, (name, f[0])
+
+
+@pytest.mark.parametrize("lmax,prec,bo", [(3, 0, 0), (-1, 0, 0), (1, 1, 0), (2, 0, 4), (1, 0, 1)])
+def test_projector_channels_rejected_before_device_use(lib, lmax, prec, bo):
+    """lmax outside 0..2, or several projectors per atom outside the FP64 form
+    with block width 2 (the double-float kernels that carry them)."""
+    s = inputs.small_system(n=16, h=0.35, n_atoms=2, seed=1)
+    cfg = emd.config_for(s, precision=prec, block_orbitals=bo)
+    cfg.species.lmax = lmax
+    with pytest.raises(emd.EmdError) as ei:
+        emd.emd_init_system(cfg)
+    assert ei.value.code == emd.EMD_EINVAL
