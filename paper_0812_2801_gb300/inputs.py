@@ -347,6 +347,22 @@ def small_system(n: int = 16, h: float = 0.3, fd_order: int = 4,
     return sysin
 
 
+def with_extra_states(sysin: SystemInput, n_extra: int, seed: int = 17) -> SystemInput:
+    """``sysin`` with n_extra more orbitals: smooth random functions (complex
+    normal noise keeping the Fourier modes |m_a| <= 2 on each axis),
+    orthonormalised after the existing ones.  For a smeared ground state,
+    whose partially occupied states sit above the n_orb filled ones."""
+    n = sysin.n
+    rng = np.random.default_rng(seed)
+    d = rng.normal(size=(n_extra, n, n, n)) + 1j * rng.normal(size=(n_extra, n, n, n))
+    m = np.abs(np.fft.fftfreq(n, d=1.0 / n))
+    low = (m[:, None, None] <= 2) & (m[None, :, None] <= 2) & (m[None, None, :] <= 2)
+    d = np.fft.ifftn(np.fft.fftn(d, axes=(1, 2, 3)) * low[None], axes=(1, 2, 3))
+    psi = orthonormalise(np.concatenate([sysin.psi, d]), sysin.h)
+    return dataclasses.replace(sysin, name=f"{sysin.name}+{n_extra}",
+                               psi=np.ascontiguousarray(psi))
+
+
 WORKLOADS = {
     "tiny": tiny_fp64,
     "precision": precision_c96,
