@@ -201,6 +201,24 @@ int emd_set_orbitals_c64(emd_system *s, const float *psi);
  * canonical [n_orb][N][N][N], host).  EMD_FP64 systems round to float32. */
 int emd_get_orbitals_c64(emd_system *s, float *psi);
 
+/* Occupations f[n_orb] (host): the density is rho = sum_A f_A |phi_A|^2
+ * (eq. density with a weight per orbital; f_A = occ for every orbital
+ * after emd_init_system and after emd_ground_state, the closed-shell
+ * case).  Each f_A must lie in (0, occ]; values below 1e-30 occ are raised
+ * to it.  The weights enter the energies and forces with the density (each
+ * term is quadratic in an orbital with its weight f_A) and stay fixed while
+ * the orbitals evolve (the propagation is linear in each orbital).
+ * Storage: the device holds u_A = sqrt(f_A / occ) phi_A, so the kernels
+ * work unchanged with the single weight occ; emd_set_orbitals*,
+ * emd_get_state, emd_get_orbitals_c64 and emd_get_projections take and
+ * return phi_A (the weights applied on the way in and removed on the way
+ * out).  Set before or after the orbitals; if orbitals are set, rho,
+ * v_Hxc and F are recomputed by the next call that reads them.  A
+ * smeared ground state (emd_ground_state_smeared) sets them.  Not in the
+ * paper, whose systems are closed-shell.  Errors: EMD_EINVAL. */
+int emd_set_occupations(emd_system *s, const double *f);
+int emd_get_occupations(emd_system *s, double *f);
+
 /* Advance n_steps MD steps of length dt with the electronic mass-like
  * parameter mu (mu = 1: plain Ehrenfest).  field: NULL, or n_steps
  * amplitudes e_n (host) of a uniform field along z in the length gauge,
@@ -362,9 +380,10 @@ int emd_get_dipole(emd_system *s, double *D);
  * orthonormal set of atom-centred functions will do).  On return the
  * orbitals are the last Ritz vectors in ascending order, eigenvalues (if not
  * NULL, host, n_orb doubles) their Ritz values, info (if not NULL) the
- * iteration count, final residual, occ * sum of the Ritz values and the
- * gap to the first unoccupied Ritz value (the subspace carries
- * max(4, n_orb/10) buffer states above the occupied ones); rho,
+ * iteration count, final residual, occ * sum of the Ritz values, the gap
+ * to the first unoccupied Ritz value (the subspace carries max(4,
+ * n_orb/10) buffer states above the occupied ones), the middle of that gap
+ * and zero entropy; the occupations are reset to occ; rho,
  * v_Hxc and F are recomputed from the new orbitals by the next call that
  * reads them (as after emd_set_orbitals).  The subspace products X^H X,
  * X^H H X and X V are the library's own kernels (FP64 sums, in a fixed
@@ -377,13 +396,41 @@ int emd_get_dipole(emd_system *s, double *D);
 typedef struct {
   int iterations;
   double residual;       /* h^3 sum |rho_out - rho_in| / n_electrons */
-  double band_energy;    /* occ * sum of the Ritz values              */
-  double gap;            /* lowest unoccupied minus highest occupied
-                            Ritz value (from the buffer states); the
-                            integer occupations need it > 0          */
+  double band_energy;    /* sum_A f_A eps_A over the n_orb states      */
+  double gap;            /* first buffer-state Ritz value minus the
+                            n_orb-th one; integer occupations need
+                            it > 0                                    */
+  double fermi_level;    /* mu_F of the Fermi-Dirac occupations; with
+                            kT = 0 the middle of that gap             */
+  double entropy;        /* S = -sum_A occ [g ln g + (1-g) ln(1-g)],
+                            g = f_A / occ (0 with kT = 0); the Mermin
+                            free energy is E_KS - kT S               */
 } emd_gs_info;
 int emd_ground_state(emd_system *s, int max_scf, double tol, int degree,
                      double mix, double *eigenvalues, emd_gs_info *info);
+
+/* The same with fractional occupations, for cells with a small or no gap
+ * (the paper's systems are gapped and it uses none; a reading).  With
+ * kT > 0 the n_orb states of the system carry Fermi-Dirac occupations
+ *   f_A = occ / (1 + exp((eps_A - mu_F) / kT)),  sum_A f_A = n_electrons,
+ * mu_F found by bisection each iteration from the n_orb lowest Ritz values
+ * (0 < n_electrons < occ n_orb: give the system more orbitals than
+ * n_electrons / occ), rho_out = sum_A f_A |phi_A|^2, and the fixed point is
+ * the stationary point of the Mermin free energy E_KS - kT S.  kT = 0 is
+ * emd_ground_state (n_electrons ignored).  kerker_q0 > 0 preconditions
+ * the mixing step: the Anderson-combined residual R(G) is multiplied by
+ * |G|^2 / (|G|^2 + q0^2) (R(0) unchanged; an FFT pass like the Hartree
+ * solve), which damps the long-wavelength charge sloshing of metallic
+ * cells; 0 mixes unpreconditioned.  Neither kT's search nor the
+ * preconditioner moves the fixed point.  On return the occupations are
+ * the system's (emd_set_occupations), occupations (if not NULL, host,
+ * n_orb doubles) a copy of them, and the starting density is that of the
+ * current orbitals and occupations scaled to n_electrons.  Errors as for
+ * emd_ground_state. */
+int emd_ground_state_smeared(emd_system *s, int max_scf, double tol, int degree,
+                             double mix, double kT, double n_electrons,
+                             double kerker_q0, double *eigenvalues,
+                             double *occupations, emd_gs_info *info);
 
 /* Release all device memory and the handle.  NULL is accepted. */
 void emd_destroy(emd_system *s);

@@ -149,6 +149,15 @@ struct emd_system {
   double *scal = nullptr;
   int *err = nullptr;
   int ions_set = 0, orbs_set = 0;
+  // occupations f_A (host).  The device holds the orbitals as
+  // u_A = sqrt(f_A / occ) phi_A, so that occ sum_A |u_A|^2 = sum_A f_A
+  // |phi_A|^2 and every energy and force term, quadratic in each orbital,
+  // carries the weight f_A; the propagation is linear in each orbital and
+  // keeps its weight.  occ_w holds those weights, occ_winv their inverses;
+  // f_uniform: every f_A = occ (weights 1, nothing scaled).
+  std::vector<double> f;
+  int f_uniform = 1;
+  double *occ_w = nullptr, *occ_winv = nullptr;
   // set by emd_set_ions / emd_set_orbitals*: rho, v_Hxc (history restarted),
   // projections and F(0) are recomputed by the next call that reads them
   int needs_restart = 0;
@@ -194,6 +203,34 @@ int launch_check(const char *what) {
     return fail(EMD_ECUDA, "%s: kernel launch failed: %s", what,
                 cudaGetErrorString(e));
   return EMD_OK;
+}
+
+// Occupations f (n_orb values in (0, occ]) into the system: values below
+// 1e-30 occ are raised to it, so that every weight sqrt(f / occ) is a
+// normal FP32 number; the orbitals on the device are not touched.
+int set_occupation_state(emd_system *s, const double *f) {
+  const double occ = s->cfg.occ;
+  const int n = s->o.n_orb;
+  std::vector<double> w(n), wi(n);
+  bool uniform = true;
+  for (int i = 0; i < n; ++i) {
+    const double fi = std::max(f[i], 1e-30 * occ);
+    s->f[i] = fi;
+    uniform = uniform && fi == occ;
+    w[i] = std::sqrt(fi / occ);
+    wi[i] = 1.0 / w[i];
+  }
+  s->f_uniform = uniform;
+  CK(cudaMemcpyAsync(s->occ_w, w.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(s->occ_winv, wi.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return EMD_OK;
+}
+
+double occupation_sum(const emd_system *s) {
+  double t = 0.0;
+  for (double fi : s->f) t += fi;
+  return t;
 }
 
 int read_err_flag(emd_system *s) {
@@ -669,6 +706,9 @@ int emd_init_system(const emd_config *cfg, emd_system **out) {
   TRY(A((void **)&s->partials, (size_t)s->n_partials * 8));
   TRY(A((void **)&s->scal, 16 * 8));
   TRY(A((void **)&s->err, sizeof(int)));
+  TRY(A((void **)&s->occ_w, (size_t)o.n_orb_pad * 8));
+  TRY(A((void **)&s->occ_winv, (size_t)o.n_orb_pad * 8));
+  s->f.assign(o.n_orb, c.occ);
 #undef TRY
   cudaError_t e = cudaMemsetAsync(s->err, 0, sizeof(int), s->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->V, 0, na * 3 * 8, s->st);
@@ -727,14 +767,19 @@ static int upload_orbitals(emd_system *s, const double *psi, int n_vec,
   return launch_check("upload_orbitals");
 }
 
+// winv (device, one factor per orbital, or NULL): each orbital is scaled by
+// it on the way out (the system's orbitals have their occupation weights
+// removed this way)
 static int download_orbitals(emd_system *s, const void *src, int n_vec,
-                             double *psi) {
+                             double *psi, const double *winv = nullptr) {
   const size_t n3 = s->g.n3;
   for (int b = 0; b * s->o.bo < n_vec; ++b) {
     const int nv = std::min(s->o.bo, n_vec - b * s->o.bo);
     const char *d = (const char *)src + (size_t)b * n3 * s->o.bo *
                                             (s->o.prec == EMD_FP64 ? 16 : 8);
     emd_launch_unpack(s->o, d, s->stage_buf, nv, s->st);
+    if (winv)
+      emd_launch_scale_canon(false, s->stage_buf, n3, nv, winv + (size_t)b * s->o.bo, s->st);
     CK(cudaMemcpyAsync(psi + 2 * (size_t)b * s->o.bo * n3, s->stage_buf,
                        (size_t)nv * n3 * 16, cudaMemcpyDeviceToHost, s->st));
   }
@@ -784,6 +829,7 @@ int emd_set_orbitals_c64(emd_system *s, const float *psi) {
   CK(cudaMemsetAsync(s->psi, 0, s->orb_bytes, s->st));
   int r = upload_orbitals_c64(s, psi, s->psi);
   if (r) return r;
+  if (!s->f_uniform) emd_launch_scale_orbitals(s->o, s->psi, s->o.n_orb, s->occ_w, s->st);
   s->orbs_set = 1;
   s->c_valid = 0;
   if (s->ions_set) s->needs_restart = 1;
@@ -808,6 +854,8 @@ int emd_get_orbitals_c64(emd_system *s, float *psi) {
     const char *d = (const char *)s->psi + (size_t)b * n3 * s->o.bo *
                                                (s->o.prec == EMD_FP64 ? 16 : 8);
     emd_launch_unpack_c64(s->o, d, half[k], nv, s->st);
+    if (!s->f_uniform)
+      emd_launch_scale_canon(true, half[k], n3, nv, s->occ_winv + (size_t)b * s->o.bo, s->st);
     CK(cudaEventRecord(s->cev[1 + k], s->st));
     CK(cudaStreamWaitEvent(s->cst, s->cev[1 + k], 0));
     CK(cudaMemcpyAsync(psi + 2 * (size_t)b * s->o.bo * n3, half[k],
@@ -825,10 +873,40 @@ int emd_set_orbitals(emd_system *s, const double *psi) {
   CK(cudaMemsetAsync(s->psi, 0, s->orb_bytes, s->st));
   int r = upload_orbitals(s, psi, s->o.n_orb, s->psi);
   if (r) return r;
+  if (!s->f_uniform) emd_launch_scale_orbitals(s->o, s->psi, s->o.n_orb, s->occ_w, s->st);
   s->orbs_set = 1;
   s->c_valid = 0;
   if (s->ions_set) s->needs_restart = 1;
   CK(cudaStreamSynchronize(s->st));
+  return EMD_OK;
+}
+
+int emd_set_occupations(emd_system *s, const double *f) {
+  g_err.clear();
+  if (!s || !f) return fail(EMD_EINVAL, "NULL argument");
+  for (int i = 0; i < s->o.n_orb; ++i)
+    if (!(f[i] > 0.0 && f[i] <= s->cfg.occ))
+      return fail(EMD_EINVAL, "occupation %d = %g outside (0, occ = %g]", i, f[i], s->cfg.occ);
+  // orbitals already on the device: u_A <- sqrt(f_new / f_old) u_A in two
+  // scalings (remove the old weight, apply the new one)
+  const int had = s->orbs_set && !s->f_uniform;
+  if (had) emd_launch_scale_orbitals(s->o, s->psi, s->o.n_orb, s->occ_winv, s->st);
+  int r = set_occupation_state(s, f);
+  if (r) return r;
+  if (s->orbs_set && !s->f_uniform)
+    emd_launch_scale_orbitals(s->o, s->psi, s->o.n_orb, s->occ_w, s->st);
+  if (s->orbs_set) {
+    s->c_valid = 0;
+    if (s->ions_set) s->needs_restart = 1;
+  }
+  CK(cudaStreamSynchronize(s->st));
+  return launch_check("emd_set_occupations");
+}
+
+int emd_get_occupations(emd_system *s, double *f) {
+  g_err.clear();
+  if (!s || !f) return fail(EMD_EINVAL, "NULL argument");
+  std::copy(s->f.begin(), s->f.end(), f);
   return EMD_OK;
 }
 
@@ -1914,10 +1992,10 @@ int emd_get_energy(emd_system *s, emd_energy *out) {
   out->kin_ion = 0.5 * s->sp.mass * t;
   out->ks = out->kin_e + out->nl + out->es + out->xc;
   out->total = out->ks + out->kin_ion;
-  if (!std::isfinite(out->total) ||
-      std::fabs(out->n_elec - occ * s->o.n_orb) > 1e-3 * occ * s->o.n_orb)
+  const double n_expect = occupation_sum(s);
+  if (!std::isfinite(out->total) || std::fabs(out->n_elec - n_expect) > 1e-3 * n_expect)
     return fail(EMD_EUNSTABLE, "density normalisation lost: h^3 sum rho = %g, "
-                "expected %g", out->n_elec, occ * s->o.n_orb);
+                "expected %g", out->n_elec, n_expect);
   return EMD_OK;
 }
 
@@ -1936,7 +2014,7 @@ int emd_get_state(emd_system *s, double *R, double *V, double *psi, double *rho)
   if (rho)
     CK(cudaMemcpyAsync(rho, s->rho, s->g.n3 * 8, cudaMemcpyDeviceToHost, s->st));
   if (psi) {
-    r = download_orbitals(s, s->psi, s->o.n_orb, psi);
+    r = download_orbitals(s, s->psi, s->o.n_orb, psi, s->f_uniform ? nullptr : s->occ_winv);
     if (r) return r;
   }
   CK(cudaStreamSynchronize(s->st));
@@ -1972,6 +2050,13 @@ int emd_get_projections(emd_system *s, double *c) {
     CK(cudaMemcpyAsync(c + 2 * (size_t)P * s->o.n_orb, s->c + (size_t)P * s->o.n_orb_pad,
                        (size_t)s->o.n_orb * 16, cudaMemcpyDeviceToHost, s->st));
   CK(cudaStreamSynchronize(s->st));
+  if (!s->f_uniform)                        // projections of phi_A, not of u_A
+    for (int P = 0; P < s->o.n_proj; ++P)
+      for (int i = 0; i < s->o.n_orb; ++i) {
+        const double w = std::sqrt(s->f[i] / s->cfg.occ);
+        c[2 * ((size_t)P * s->o.n_orb + i)] /= w;
+        c[2 * ((size_t)P * s->o.n_orb + i) + 1] /= w;
+      }
   return read_err_flag(s);
 }
 
@@ -2036,6 +2121,7 @@ struct GroundStateWork {
   double2 *Sz = nullptr, *Hz = nullptr;             // m x m, FP64 (Hz: then V)
   double2 *gpart = nullptr;                         // subspace-product partials
   double *rho_in = nullptr, *rho_out = nullptr;
+  double *wd = nullptr;                             // occupation weights sqrt(f / occ)
   double *hr[kHist] = {}, *hf[kHist] = {};          // rho_in and F = rho_out - rho_in
   std::vector<void *> mem;
 };
@@ -2081,7 +2167,7 @@ int gs_setup(emd_system *s) {
        A((void **)&g->Sz, (size_t)m * m * 16) && A((void **)&g->Hz, (size_t)m * m * 16) &&
        A((void **)&g->gpart, emd_gram_scratch((int)n3, m) * sizeof(double2)) &&
        A((void **)&g->rho_in, n3 * 8) &&
-       A((void **)&g->rho_out, n3 * 8);
+       A((void **)&g->rho_out, n3 * 8) && A((void **)&g->wd, (size_t)m * 8);
   for (int k = 0; ok && k < GroundStateWork::kHist; ++k)
     ok = A((void **)&g->hr[k], n3 * 8) && A((void **)&g->hf[k], n3 * 8);
   if (!ok) {
@@ -2296,15 +2382,61 @@ int gs_rayleigh_ritz(emd_system *s, std::vector<double> &eps) {
 }
 
 // density of the occupied Ritz vectors (the first n_occ columns of the
-// canonical set in B), packed into C with the occupied blocks only
-void gs_density(emd_system *s, double *rho) {
+// canonical set in B), packed into C with the occupied blocks only; with
+// weights w (device, sqrt(f_A / occ)) rho = sum_A f_A |phi_A|^2, else
+// occ sum_A |phi_A|^2
+void gs_density(emd_system *s, double *rho, const double *w) {
   GroundStateWork *g = s->gsw;
   OrbLayout oo = g->og;
   oo.n_orb = g->n_occ;
   oo.n_blk = (g->n_occ + oo.bo - 1) / oo.bo;
   oo.n_orb_pad = oo.n_blk * oo.bo;
   gs_pack(oo, g->B, g->C, g->n_occ, s->st);
+  if (w) emd_launch_scale_orbitals(oo, g->C, g->n_occ, w, s->st);
   emd_launch_density(oo, g->C, s->cfg.occ, rho, s->st);
+}
+
+// Fermi-Dirac occupations of the n lowest Ritz values, f_i = occ / (1 +
+// exp((eps_i - mu) / kT)), with mu bisected (sum f is increasing in mu)
+// until sum f = n_e; returns mu.  Needs 0 < n_e < occ n.
+double gs_fermi_dirac(const std::vector<double> &eps, int n, double n_e, double occ,
+                      double kT, std::vector<double> &f) {
+  double lo = eps[0], hi = eps[0];
+  for (int i = 0; i < n; ++i) {
+    lo = std::min(lo, eps[i]);
+    hi = std::max(hi, eps[i]);
+  }
+  lo -= 50.0 * kT + 1.0;                    // sum f ~ 0 here
+  hi += 50.0 * kT + 1.0;                    // sum f ~ occ n here
+  f.assign(n, 0.0);
+  auto fill = [&](double mu) {
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) {
+      f[i] = occ / (1.0 + std::exp((eps[i] - mu) / kT));
+      t += f[i];
+    }
+    return t;
+  };
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (fill(mid) < n_e) lo = mid;
+    else hi = mid;
+  }
+  const double mu = 0.5 * (lo + hi);
+  fill(mu);
+  return mu;
+}
+
+// S = -sum_i occ [g ln g + (1 - g) ln(1 - g)], g = 1 / (1 + e^x) and
+// 1 - g = 1 / (1 + e^-x), x = (eps_i - mu) / kT (0 ln 0 = 0)
+double gs_entropy(const std::vector<double> &eps, int n, double mu, double occ, double kT) {
+  auto xlx = [](double v) { return v > 0.0 ? v * std::log(v) : 0.0; };
+  double t = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double x = (eps[i] - mu) / kT;
+    t += xlx(1.0 / (1.0 + std::exp(x))) + xlx(1.0 / (1.0 + std::exp(-x)));
+  }
+  return -occ * t;
 }
 
 // Anderson mixing: with F_i = rho_out_i - rho_in_i over the stored
@@ -2358,37 +2490,59 @@ void gs_anderson_coefficients(const double (&B)[GroundStateWork::kHist][GroundSt
 
 extern "C" {
 
-int emd_ground_state(emd_system *s, int max_scf, double tol, int degree, double mix,
-                     double *eigenvalues, emd_gs_info *info) {
+int emd_ground_state_smeared(emd_system *s, int max_scf, double tol, int degree, double mix,
+                             double kT, double n_electrons, double kerker_q0,
+                             double *eigenvalues, double *occupations, emd_gs_info *info) {
   g_err.clear();
-  if (s && s->sp.nch > 1)
-    return fail(EMD_EINVAL, "the ground-state solver covers the s-projector only (species lmax = 0)");
   if (!s) return fail(EMD_EINVAL, "NULL system");
+  if (s->sp.nch > 1)
+    return fail(EMD_EINVAL, "the ground-state solver covers the s-projector only (species lmax = 0)");
   if (!s->ions_set || !s->orbs_set) return fail(EMD_ESTATE, "set ions and orbitals first");
   if (max_scf < 1 || !(tol > 0.0) || degree < 1 || degree > 64 || !(mix > 0.0) || mix > 1.0)
     return fail(EMD_EINVAL, "need max_scf >= 1, tol > 0, 1 <= degree <= 64, 0 < mix <= 1");
+  const double occ = s->cfg.occ;
+  if (!(kT >= 0.0) || !std::isfinite(kT) || !(kerker_q0 >= 0.0) || !std::isfinite(kerker_q0))
+    return fail(EMD_EINVAL, "need kT >= 0 and kerker_q0 >= 0 (finite)");
+  if (kT > 0.0 && !(n_electrons > 0.0 && n_electrons < occ * s->o.n_orb))
+    return fail(EMD_EINVAL, "with kT > 0 need 0 < n_electrons < occ n_orb = %g",
+                occ * s->o.n_orb);
   int r = gs_setup(s);
   if (r) return r;
   GroundStateWork *g = s->gsw;
   const int n_occ = g->n_occ, m = g->og.n_orb;
   const int n3 = s->g.n3;
   const double h3 = s->g.h * s->g.h * s->g.h;
-  const double n_e = s->cfg.occ * n_occ;
+  const bool smear = kT > 0.0;
+  const double n_e = smear ? n_electrons : occ * n_occ;
   const int nb = std::min(s->n_partials, 1024);
   constexpr int K = GroundStateWork::kHist;
   s->c_valid = 0;
   s->needs_restart = 1;                     // whatever happens, derived state is stale
-  // starting subspace: the current orbitals and random buffer states
+  // starting subspace: the current orbitals (occupation weights removed) and
+  // random buffer states; starting density: theirs, scaled to n_e electrons
   gs_unpack(s->o, s->psi, g->B, n_occ, s->st);
+  if (!s->f_uniform)
+    emd_launch_scale_canon(s->o.prec != EMD_FP64, g->B, (size_t)n3, n_occ, s->occ_winv, s->st);
   emd_launch_fill_random(s->o.prec, g->B, (size_t)n3, n_occ, m, 0x5eedu, s->st);
   gs_pack(g->og, g->B, g->A, m, s->st);
-  emd_launch_density(s->o, s->psi, s->cfg.occ, g->rho_in, s->st);
+  emd_launch_density(s->o, s->psi, occ, g->rho_in, s->st);
+  const double n_now = occupation_sum(s);
+  if (n_now != n_e) {
+    EmdComb sc{};
+    sc.p[0] = g->rho_in;
+    sc.w[0] = n_e / n_now;
+    sc.m = 1;
+    emd_launch_comb(n3, sc, g->rho_out, s->st);
+    std::swap(g->rho_in, g->rho_out);
+  }
   gs_potential(s, g->rho_in);
   std::vector<double> eps;
   r = gs_rayleigh_ritz(s, eps);
   if (r) return r;
   double B[K][K] = {};
   std::vector<int> act;
+  std::vector<double> f(n_occ, occ), wh(n_occ, 1.0);
+  double mu_f = 0.0;
   double res = 0.0;
   int it = 0;
   bool converged = false;
@@ -2404,7 +2558,12 @@ int emd_ground_state(emd_system *s, int max_scf, double tol, int degree, double 
     if (r) return r;
     r = gs_rayleigh_ritz(s, eps);
     if (r) return r;
-    gs_density(s, g->rho_out);
+    if (smear) {
+      mu_f = gs_fermi_dirac(eps, n_occ, n_e, occ, kT, f);
+      for (int i = 0; i < n_occ; ++i) wh[i] = std::sqrt(f[i] / occ);
+      CK(cudaMemcpyAsync(g->wd, wh.data(), (size_t)n_occ * 8, cudaMemcpyHostToDevice, s->st));
+    }
+    gs_density(s, g->rho_out, smear ? g->wd : nullptr);
     emd_launch_absdiff_partials(n3, g->rho_out, g->rho_in, s->partials, nb, s->st);
     emd_launch_sum(s->partials, nb, s->scal + 8, s->st);
     double l1 = 0.0;
@@ -2416,16 +2575,16 @@ int emd_ground_state(emd_system *s, int max_scf, double tol, int degree, double 
       converged = true;
       break;
     }
-    // store (rho_in, F) in the oldest slot and mix
+    // store (rho_in, F) in the oldest slot
     const int k = (it - 1) % K;
     CK(cudaMemcpyAsync(g->hr[k], g->rho_in, (size_t)n3 * 8, cudaMemcpyDeviceToDevice, s->st));
-    EmdComb f{};
-    f.p[0] = g->rho_out;
-    f.w[0] = 1.0;
-    f.p[1] = g->rho_in;
-    f.w[1] = -1.0;
-    f.m = 2;
-    emd_launch_comb(n3, f, g->hf[k], s->st);
+    EmdComb fd{};
+    fd.p[0] = g->rho_out;
+    fd.w[0] = 1.0;
+    fd.p[1] = g->rho_in;
+    fd.w[1] = -1.0;
+    fd.m = 2;
+    emd_launch_comb(n3, fd, g->hf[k], s->st);
     act.erase(std::remove(act.begin(), act.end(), k), act.end());
     act.push_back(k);
     for (size_t j = 0; j < act.size(); ++j) {
@@ -2439,35 +2598,59 @@ int emd_ground_state(emd_system *s, int max_scf, double tol, int degree, double 
     for (size_t j = 0; j < act.size(); ++j) B[k][act[j]] = B[act[j]][k] = dots[j];
     std::vector<double> c;
     gs_anderson_coefficients(B, act, k, c);
+    // rho_in <- sum_j c_j rho_in_j + mix K[sum_j c_j F_j] (K: Kerker's
+    // factor, or 1), the combined residual formed in rho_out
+    EmdComb cf{};
+    for (size_t j = 0; j < act.size(); ++j) {
+      cf.p[cf.m] = g->hf[act[j]];
+      cf.w[cf.m++] = c[j];
+    }
+    emd_launch_comb(n3, cf, g->rho_out, s->st);
+    if (kerker_q0 > 0.0)
+      emd_launch_kerker(s->g, kerker_q0, g->rho_out, g->rho_out, s->fft_a, s->fft_b, s->st);
     EmdComb cb{};
-    cb.m = 0;
     for (size_t j = 0; j < act.size(); ++j) {
       cb.p[cb.m] = g->hr[act[j]];
       cb.w[cb.m++] = c[j];
-      cb.p[cb.m] = g->hf[act[j]];
-      cb.w[cb.m++] = c[j] * mix;
     }
+    cb.p[cb.m] = g->rho_out;
+    cb.w[cb.m++] = mix;
     emd_launch_comb(n3, cb, g->rho_in, s->st);
     gs_potential(s, g->rho_in);
   }
-  // the occupied Ritz vectors become the system's orbitals
+  // the occupied Ritz vectors become the system's orbitals, with their
+  // occupations (the last iteration's)
   gs_pack(s->o, g->B, s->psi, n_occ, s->st);
+  r = launch_check("emd_ground_state");
+  if (r) return r;
+  r = set_occupation_state(s, f.data());
+  if (r) return r;
+  if (!s->f_uniform) emd_launch_scale_orbitals(s->o, s->psi, n_occ, s->occ_w, s->st);
   r = launch_check("emd_ground_state");
   if (r) return r;
   CK(cudaStreamSynchronize(s->st));
   if (eigenvalues) std::copy(eps.begin(), eps.begin() + n_occ, eigenvalues);
+  if (occupations) std::copy(s->f.begin(), s->f.end(), occupations);
   if (info) {
     info->iterations = converged ? it : max_scf;
     info->residual = res;
     double sum = 0.0;
-    for (int i = 0; i < n_occ; ++i) sum += eps[i];
-    info->band_energy = s->cfg.occ * sum;
+    for (int i = 0; i < n_occ; ++i) sum += f[i] * eps[i];
+    info->band_energy = sum;
     info->gap = eps[n_occ] - eps[n_occ - 1];
+    info->fermi_level = smear ? mu_f : 0.5 * (eps[n_occ - 1] + eps[n_occ]);
+    info->entropy = smear ? gs_entropy(eps, n_occ, mu_f, occ, kT) : 0.0;
   }
   if (!converged)
     return fail(EMD_ENOTCONV, "ground state: residual %.3e after %d iterations (tol %.3e)",
                 res, max_scf, tol);
   return EMD_OK;
+}
+
+int emd_ground_state(emd_system *s, int max_scf, double tol, int degree, double mix,
+                     double *eigenvalues, emd_gs_info *info) {
+  return emd_ground_state_smeared(s, max_scf, tol, degree, mix, 0.0, 0.0, 0.0, eigenvalues,
+                                  nullptr, info);
 }
 
 int emd_get_dipole(emd_system *s, double *D) {

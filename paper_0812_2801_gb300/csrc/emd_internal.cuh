@@ -311,6 +311,10 @@ void emd_fft_plan_check(int n, int *ok);   // host-only factor check
 int emd_fft_prepare(int n);                 // twiddle tables on the device
 void emd_launch_poisson(const GridInfo &g, const double *charge, double *v,
                         double2 *work_a, double2 *work_b, cudaStream_t st);
+// out = the inverse transform of K(G) r(G), Kerker's K = |G|^2 / (|G|^2 +
+// q0^2) for G != 0 and K(0) = 1; out may alias r
+void emd_launch_kerker(const GridInfo &g, double q0, const double *r, double *out,
+                       double2 *work_a, double2 *work_b, cudaStream_t st);
 void emd_launch_lda(int n3, const double *rho, const double *v_h,
                     double *eps_xc, double *v_xc, double *vhxc,
                     cudaStream_t st);
@@ -404,6 +408,13 @@ void emd_launch_nl_force(const OrbLayout &o, const TableSet &t, int n_atoms,
                          const void *u, const double2 *c, double h3,
                          double coef, double coef_unit, double inv_rc2, double *part,
                          double *F_nl, cudaStream_t st);
+// groundstate.cu, per-orbital weights: u_A <- w_A u_A for the orbitals A < n_orb of a
+// packed set (layout o), and for the n_vec columns of a canonical set
+// (complex64 when c64, else complex128)
+void emd_launch_scale_orbitals(const OrbLayout &o, void *u, int n_orb, const double *w,
+                               cudaStream_t st);
+void emd_launch_scale_canon(bool c64, void *c, size_t n3, int n_vec, const double *w,
+                            cudaStream_t st);
 void emd_launch_pack(const OrbLayout &o, const double2 *canon, void *u,
                      int n_vec, cudaStream_t st);
 void emd_launch_unpack(const OrbLayout &o, const void *u, double2 *canon,

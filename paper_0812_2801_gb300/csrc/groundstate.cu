@@ -74,6 +74,36 @@ __global__ void k_fill_random(V *x, size_t n3, int c0, int c1, unsigned seed) {
 
 inline unsigned blocks(size_t n) { return (unsigned)((n + 255) / 256); }
 
+// ---- per-orbital weights ----------------------------------------------------
+// u_A <- w_A u_A for the orbitals A < n_orb of a packed set (element i of
+// [n_blk][n3][bo] belongs to orbital (i / (bo n3)) bo + i % bo); the padding
+// orbitals are left alone.  The product is formed in FP64.
+template <typename V>
+__global__ void k_scale_packed(V *u, size_t n3, int bo, int n_orb, size_t tot,
+                               const double *__restrict__ w) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= tot) return;
+  const int A = (int)(i / ((size_t)bo * n3)) * bo + (int)(i % (size_t)bo);
+  if (A >= n_orb) return;
+  const double f = w[A];
+  V v = u[i];
+  v.x = (double)v.x * f;
+  v.y = (double)v.y * f;
+  u[i] = v;
+}
+
+// c_A <- w_A c_A over the n_vec columns of a canonical set (column A at c + A n3)
+template <typename V>
+__global__ void k_scale_canon(V *c, size_t n3, size_t tot, const double *__restrict__ w) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= tot) return;
+  const double f = w[i / n3];
+  V v = c[i];
+  v.x = (double)v.x * f;
+  v.y = (double)v.y * f;
+  c[i] = v;
+}
+
 // ---- subspace products ----------------------------------------------------
 // X, Y: canonical column-major sets, column i at X + i n3 (complex128, or
 // complex64 read into FP64 sums).  G = h^3 X^H Y, m x m, column-major FP64.
@@ -262,4 +292,27 @@ void emd_launch_rotate(int prec, const void *X, const double2 *V, int n3, int m,
     k_rotate<double2><<<grid, 256, 0, st>>>((const double2 *)X, V, n3, m, (double2 *)B);
   else
     k_rotate<float2><<<grid, 256, 0, st>>>((const float2 *)X, V, n3, m, (float2 *)B);
+}
+
+void emd_launch_scale_orbitals(const OrbLayout &o, void *u, int n_orb, const double *w,
+                               cudaStream_t st) {
+  emd_note_launches(1);
+  const size_t tot = (size_t)((n_orb + o.bo - 1) / o.bo) * o.n3 * o.bo;
+  if (o.prec == EMD_FP64)
+    k_scale_packed<double2><<<blocks(tot), 256, 0, st>>>((double2 *)u, (size_t)o.n3, o.bo,
+                                                          n_orb, tot, w);
+  else
+    k_scale_packed<float2><<<blocks(tot), 256, 0, st>>>((float2 *)u, (size_t)o.n3, o.bo,
+                                                         n_orb, tot, w);
+}
+
+void emd_launch_scale_canon(bool c64, void *c, size_t n3, int n_vec, const double *w,
+                            cudaStream_t st) {
+  if (n_vec <= 0) return;
+  emd_note_launches(1);
+  const size_t tot = n3 * (size_t)n_vec;
+  if (c64)
+    k_scale_canon<float2><<<blocks(tot), 256, 0, st>>>((float2 *)c, n3, tot, w);
+  else
+    k_scale_canon<double2><<<blocks(tot), 256, 0, st>>>((double2 *)c, n3, tot, w);
 }

@@ -335,11 +335,20 @@ k_fft_pass_r(const void *in, void *out, FftPlan pl, const double2 *tab,
   }
 }
 
-// [kz][ky][kx] (kx in 0..m) -> v(G) = c inv_s[s] n(G) written to
+// The spectral factor of the integer s = mx^2 + my^2 + mz^2 (|G|^2 = (2 pi /
+// L)^2 s): the Poisson kernel c inv_s[s] when kappa < 0; otherwise Kerker's
+// c s / (s + kappa), kappa = (q0 L / 2 pi)^2, with c at s = 0
+__device__ __forceinline__ double spectral_factor(int s, double c, double kappa,
+                                                  const double *__restrict__ inv_s) {
+  if (kappa < 0.0) return c * inv_s[s];
+  return s == 0 ? c : c * (double)s / ((double)s + kappa);
+}
+
+// [kz][ky][kx] (kx in 0..m) -> v(G) = factor(s) n(G) written to
 // [kx][ky][kz], through 32 x 32 shared-memory tiles of each (kz, kx) plane
 __global__ void __launch_bounds__(256)
 k_poisson_transpose(const double2 *__restrict__ a, double2 *__restrict__ b, int n, int nh,
-                    double c, const double *__restrict__ inv_s) {
+                    double c, double kappa, const double *__restrict__ inv_s) {
   __shared__ double2 tile[32][33];
   const int ky = blockIdx.z;
   const int kx0 = blockIdx.x * 32, kz0 = blockIdx.y * 32;
@@ -349,7 +358,7 @@ k_poisson_transpose(const double2 *__restrict__ a, double2 *__restrict__ b, int 
     if (kz < n && kx < nh) {
       const int mz = 2 * kz < n ? kz : kz - n;
       const int mx = kx;   // kx <= n / 2 (the Nyquist plane has |mx| = n / 2 either way)
-      const double f = c * inv_s[mx * mx + my * my + mz * mz];
+      const double f = spectral_factor(mx * mx + my * my + mz * mz, c, kappa, inv_s);
       const double2 v = a[((size_t)kz * n + ky) * nh + kx];
       tile[r][threadIdx.x] = make_double2(f * v.x, f * v.y);
     }
@@ -365,7 +374,7 @@ k_poisson_transpose(const double2 *__restrict__ a, double2 *__restrict__ b, int 
 // unnormalised inverse transform.  |G|^2 = (2 pi / L)^2 s with the integer
 // s = mx^2 + my^2 + mz^2, and inv_s[s] = 1 / s (inv_s[0] = 0) is a table per
 // grid size, so v(G) = c inv_s[s] n(G), c = 4 pi / ((2 pi / L)^2 N^3).
-__global__ void k_poisson_kernel(double2 *a, int n, double c, const double *inv_s) {
+__global__ void k_poisson_kernel(double2 *a, int n, double c, double kappa, const double *inv_s) {
   const size_t n3 = (size_t)n * n * n;
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n3) return;
@@ -373,7 +382,7 @@ __global__ void k_poisson_kernel(double2 *a, int n, double c, const double *inv_
   const int mx = 2 * kx < n ? kx : kx - n;
   const int my = 2 * ky < n ? ky : ky - n;
   const int mz = 2 * kz < n ? kz : kz - n;
-  const double f = c * inv_s[mx * mx + my * my + mz * mz];
+  const double f = spectral_factor(mx * mx + my * my + mz * mz, c, kappa, inv_s);
   double2 v = a[i];
   v.x *= f;
   v.y *= f;
@@ -567,11 +576,14 @@ int emd_fft_prepare(int n) {
   return 0;
 }
 
-void emd_launch_poisson(const GridInfo &g, const double *charge, double *v,
-                        double2 *wa, double2 *wb, cudaStream_t st) {
+namespace {
+
+// v = the inverse transform of factor(s) times the transform of the real grid
+// `charge` (spectral_factor; cpois includes the 1/N^3 of the inverse);
+// `charge` is read by the first pass only, so v may alias it
+void spectral_multiply(const GridInfo &g, const double *charge, double *v, double2 *wa,
+                       double2 *wb, double cpois, double kappa, cudaStream_t st) {
   const PlanCache *pc = get_plan(g.n);
-  const double gq = 2.0 * M_PI / g.L;
-  const double cpois = 4.0 * M_PI / (gq * gq) / (double)g.n3;
   const int n = g.n;
   if (n % 2 == 0) {
     // real data: half-length transforms along x, half spectrum in kx
@@ -587,7 +599,7 @@ void emd_launch_poisson(const GridInfo &g, const double *charge, double *v,
     k_fft_pass_r<0><<<bh, 256, smf, st>>>(wa, wb, pf, pc->tab, nullptr, nh, n, -1);
     k_fft_pass_r<0><<<bh, 256, smf, st>>>(wb, wa, pf, pc->tab, nullptr, n, nh, -1);
     k_poisson_transpose<<<dim3((nh + 31) / 32, (n + 31) / 32, n), dim3(32, 8), 0, st>>>(
-        wa, wb, n, nh, cpois, pc->inv_s);
+        wa, wb, n, nh, cpois, kappa, pc->inv_s);
     k_fft_pass_r<0><<<bh, 256, smf, st>>>(wb, wa, pf, pc->tab, nullptr, nh, n, +1);
     k_fft_pass_r<0><<<bh, 256, smf, st>>>(wa, wb, pf, pc->tab, nullptr, n, nh, +1);
     k_fft_pass_r<2><<<bx, 256, smm, st>>>(wb, v, pm, ph->tab, pc->rtw, n, n, +1);
@@ -600,10 +612,24 @@ void emd_launch_poisson(const GridInfo &g, const double *charge, double *v,
   k_fft_pass<true, false><<<blocks, 256, smem, st>>>(charge, wa, p, pc->tab, -1, 1.0);
   k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wa, wb, p, pc->tab, -1, 1.0);
   k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wb, wa, p, pc->tab, -1, 1.0);
-  k_poisson_kernel<<<(g.n3 + 255) / 256, 256, 0, st>>>(wa, g.n, cpois, pc->inv_s);
+  k_poisson_kernel<<<(g.n3 + 255) / 256, 256, 0, st>>>(wa, g.n, cpois, kappa, pc->inv_s);
   k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wa, wb, p, pc->tab, +1, 1.0);
   k_fft_pass<false, false><<<blocks, 256, smem, st>>>(wb, wa, p, pc->tab, +1, 1.0);
   k_fft_pass<false, true><<<blocks, 256, smem, st>>>(wa, v, p, pc->tab, +1, 1.0);
+}
+
+}  // namespace
+
+void emd_launch_poisson(const GridInfo &g, const double *charge, double *v,
+                        double2 *wa, double2 *wb, cudaStream_t st) {
+  const double gq = 2.0 * M_PI / g.L;
+  spectral_multiply(g, charge, v, wa, wb, 4.0 * M_PI / (gq * gq) / (double)g.n3, -1.0, st);
+}
+
+void emd_launch_kerker(const GridInfo &g, double q0, const double *r, double *out,
+                       double2 *wa, double2 *wb, cudaStream_t st) {
+  const double k = q0 * g.L / (2.0 * M_PI);
+  spectral_multiply(g, r, out, wa, wb, 1.0 / (double)g.n3, k * k, st);
 }
 
 void emd_launch_lda(int n3, const double *rho, const double *v_h,

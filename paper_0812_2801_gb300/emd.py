@@ -57,7 +57,11 @@ class emd_energy(ctypes.Structure):
 
 class emd_gs_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("residual", ctypes.c_double),
-                ("band_energy", ctypes.c_double), ("gap", ctypes.c_double)]
+                ("band_energy", ctypes.c_double), ("gap", ctypes.c_double),
+                ("fermi_level", ctypes.c_double), ("entropy", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lib = None
@@ -103,6 +107,13 @@ def load() -> ctypes.CDLL:
     lib.emd_get_dipole.restype = ctypes.c_int
     lib.emd_ground_state.argtypes = [vp, ip, dp, ip, dp, _DPTR, ctypes.POINTER(emd_gs_info)]
     lib.emd_ground_state.restype = ctypes.c_int
+    lib.emd_ground_state_smeared.argtypes = [vp, ip, dp, ip, dp, dp, dp, dp, _DPTR, _DPTR,
+                                             ctypes.POINTER(emd_gs_info)]
+    lib.emd_ground_state_smeared.restype = ctypes.c_int
+    lib.emd_set_occupations.argtypes = [vp, _DPTR]
+    lib.emd_set_occupations.restype = ctypes.c_int
+    lib.emd_get_occupations.argtypes = [vp, _DPTR]
+    lib.emd_get_occupations.restype = ctypes.c_int
     lib.emd_destroy.argtypes = [vp]
     lib.emd_destroy.restype = None
     lib.emd_last_error.restype = ctypes.c_char_p
@@ -200,8 +211,31 @@ def emd_ground_state(h, n_orb: int, max_scf: int = 200, tol: float = 1e-10,
     w = np.zeros(n_orb)
     info = emd_gs_info()
     _check(load().emd_ground_state(h, max_scf, tol, degree, mix, _dptr(w), ctypes.byref(info)))
-    return w, {"iterations": info.iterations, "residual": info.residual,
-               "band_energy": info.band_energy, "gap": info.gap}
+    return w, info.as_dict()
+
+
+def emd_ground_state_smeared(h, n_orb: int, kT: float, n_electrons: float,
+                             kerker_q0: float = 0.0, max_scf: int = 200,
+                             tol: float = 1e-10, degree: int = 16, mix: float = 0.5):
+    """Ground state with Fermi-Dirac occupations (see include/emd.h).
+    Returns (eigenvalues [n_orb], occupations [n_orb], info dict)."""
+    w = np.zeros(n_orb)
+    f = np.zeros(n_orb)
+    info = emd_gs_info()
+    _check(load().emd_ground_state_smeared(h, max_scf, tol, degree, mix, kT, n_electrons,
+                                           kerker_q0, _dptr(w), _dptr(f), ctypes.byref(info)))
+    return w, f, info.as_dict()
+
+
+def emd_set_occupations(h, f: np.ndarray) -> None:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _check(load().emd_set_occupations(h, _dptr(f)))
+
+
+def emd_get_occupations(h, n_orb: int) -> np.ndarray:
+    f = np.zeros(n_orb)
+    _check(load().emd_get_occupations(h, _dptr(f)))
+    return f
 
 
 def emd_get_state(h, n_atoms: int, n_orb: int, n: int, want_psi=True, want_rho=True):
