@@ -369,6 +369,27 @@ class System:
         s = self.sysin
         return emd_get_state(self.handle, s.n_atoms, s.n_orb, s.n, want_psi, want_rho)
 
+    def occupations(self):
+        return emd_get_occupations(self.handle, self.sysin.n_orb)
+
+    def set_occupations(self, f):
+        emd_set_occupations(self.handle, f)
+
+    def ground_state(self, kT: float = 0.0, n_electrons: Optional[float] = None,
+                     kerker_q0: float = 0.0, **kw):
+        """Ground state at the current ions: integer occupations (kT = 0) or
+        Fermi-Dirac ones holding n_electrons (default: the valence charge
+        Z n_atoms).
+        Returns (eigenvalues, occupations, info)."""
+        s = self.sysin
+        if kT <= 0.0:
+            w, info = emd_ground_state(self.handle, s.n_orb, **kw)
+            return w, self.occupations(), info
+        if n_electrons is None:
+            n_electrons = s.species.z * s.n_atoms
+        return emd_ground_state_smeared(self.handle, s.n_orb, kT, n_electrons,
+                                        kerker_q0=kerker_q0, **kw)
+
     def close(self):
         emd_destroy(self.handle)
         self.handle = None
