@@ -388,7 +388,8 @@ int emd_get_dipole(emd_system *s, double *D);
  * reads them (as after emd_set_orbitals).  The subspace products X^H X,
  * X^H H X and X V are the library's own kernels (FP64 sums, in a fixed
  * order); the m x m generalized eigenproblem is solved on the host
- * (Cholesky of the overlap, cyclic Jacobi rotations), m = n_orb + the
+ * (Cholesky of the overlap, Householder reduction to a real tridiagonal,
+ * implicit QR with Wilkinson shifts), m = n_orb + the
  * buffer states; no vendor library is called.
  * Errors: EMD_EINVAL, EMD_ESTATE (ions or orbitals not set),
  * EMD_ENOTCONV (tolerance not reached; the orbitals are the last iterate),

@@ -42,7 +42,8 @@ def _stale(obj: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "emd_internal.cuh"), os.path.join(INCLUDE, "emd.h")]
+    headers = [os.path.join(CSRC, "emd_internal.cuh"), os.path.join(CSRC, "gs_host.h"),
+               os.path.join(INCLUDE, "emd.h")]
     jobs = []
     objs = []
     for src in SOURCES:

@@ -27,6 +27,7 @@
 #include <utility>
 #include <vector>
 #include "emd_internal.cuh"
+#include "gs_host.h"
 
 namespace {
 
@@ -2245,111 +2246,6 @@ int gs_filter(emd_system *s, int m, double a, double b, double a0) {
   return launch_check("ground state Chebyshev filter");
 }
 
-// The m x m generalized Hermitian eigenproblem H v = lambda S v of the
-// Rayleigh-Ritz step, on the host (column-major): the Cholesky factor S = L
-// L^H, A = L^-1 H L^-H, cyclic Jacobi rotations A <- U^H A U (each a phase
-// that makes A_pq real times a real plane rotation that zeroes it) until
-// the off-diagonal part is below 1e-15 of the largest diagonal entry, then
-// v = L^-H w.  Returns the eigenvalues ascending with their S-orthonormal
-// vectors; false if S is not positive definite.
-bool hermitian_generalized_eig(int m, const std::vector<std::complex<double>> &H,
-                               const std::vector<std::complex<double>> &S,
-                               std::vector<double> &w,
-                               std::vector<std::complex<double>> &V) {
-  typedef std::complex<double> cd;
-  auto at = [m](std::vector<cd> &M, int i, int j) -> cd & { return M[(size_t)j * m + i]; };
-  std::vector<cd> L((size_t)m * m, 0.0), Sc(S), Hc(H);
-  for (int j = 0; j < m; ++j) {                 // Cholesky, lower
-    double d = at(Sc, j, j).real();
-    for (int k = 0; k < j; ++k) d -= std::norm(at(L, j, k));
-    if (!(d > 0.0)) return false;
-    const double ljj = std::sqrt(d);
-    at(L, j, j) = ljj;
-    for (int i = j + 1; i < m; ++i) {
-      cd v = at(Sc, i, j);
-      for (int k = 0; k < j; ++k) v -= at(L, i, k) * std::conj(at(L, j, k));
-      at(L, i, j) = v / ljj;
-    }
-  }
-  // Y = L^-1 H (forward substitution per column), then A = L^-1 Y^H (= (Y L^-H)^H)
-  std::vector<cd> Y((size_t)m * m), A((size_t)m * m);
-  auto lsolve = [&](std::vector<cd> &B, std::vector<cd> &X) {
-    for (int c = 0; c < m; ++c)
-      for (int i = 0; i < m; ++i) {
-        cd v = at(B, i, c);
-        for (int k = 0; k < i; ++k) v -= at(L, i, k) * at(X, k, c);
-        at(X, i, c) = v / at(L, i, i);
-      }
-  };
-  lsolve(Hc, Y);
-  std::vector<cd> Yh((size_t)m * m);
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < m; ++j) at(Yh, i, j) = std::conj(at(Y, j, i));
-  lsolve(Yh, A);
-  for (int i = 0; i < m; ++i) {                 // A is Hermitian up to rounding
-    at(A, i, i) = at(A, i, i).real();
-    for (int j = i + 1; j < m; ++j) {
-      const cd v = 0.5 * (at(A, i, j) + std::conj(at(A, j, i)));
-      at(A, i, j) = v;
-      at(A, j, i) = std::conj(v);
-    }
-  }
-  std::vector<cd> W((size_t)m * m, 0.0);
-  for (int i = 0; i < m; ++i) at(W, i, i) = 1.0;
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0, dmax = 0.0;
-    for (int j = 0; j < m; ++j) {
-      dmax = std::max(dmax, std::abs(at(A, j, j).real()));
-      for (int i = 0; i < j; ++i) off = std::max(off, std::abs(at(A, i, j)));
-    }
-    if (off <= 1e-15 * std::max(dmax, 1e-300)) break;
-    for (int p = 0; p < m - 1; ++p)
-      for (int q = p + 1; q < m; ++q) {
-        const cd apq = at(A, p, q);
-        const double r = std::abs(apq);
-        if (r == 0.0) continue;
-        const cd u = apq / r;                   // A_pq = r u
-        const double tau = (at(A, q, q).real() - at(A, p, p).real()) / (2.0 * r);
-        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (std::abs(tau) + std::sqrt(1.0 + tau * tau));
-        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
-        // U on (p, q) = [[c, sn], [-sn conj(u), c conj(u)]]
-        const cd upp = c, upq = sn, uqp = -sn * std::conj(u), uqq = c * std::conj(u);
-        for (int k = 0; k < m; ++k) {           // A <- A U, W <- W U
-          const cd ap = at(A, k, p), aq = at(A, k, q);
-          at(A, k, p) = ap * upp + aq * uqp;
-          at(A, k, q) = ap * upq + aq * uqq;
-          const cd wp = at(W, k, p), wq = at(W, k, q);
-          at(W, k, p) = wp * upp + wq * uqp;
-          at(W, k, q) = wp * upq + wq * uqq;
-        }
-        for (int k = 0; k < m; ++k) {           // A <- U^H A
-          const cd bp = at(A, p, k), bq = at(A, q, k);
-          at(A, p, k) = std::conj(upp) * bp + std::conj(uqp) * bq;
-          at(A, q, k) = std::conj(upq) * bp + std::conj(uqq) * bq;
-        }
-        at(A, p, q) = at(A, q, p) = 0.0;
-        at(A, p, p) = at(A, p, p).real();
-        at(A, q, q) = at(A, q, q).real();
-      }
-  }
-  std::vector<int> ord(m);
-  for (int i = 0; i < m; ++i) ord[i] = i;
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
-    return at(A, a, a).real() < at(A, b, b).real();
-  });
-  w.resize(m);
-  V.assign((size_t)m * m, 0.0);
-  for (int c = 0; c < m; ++c) {
-    const int k = ord[c];
-    w[c] = at(A, k, k).real();
-    for (int i = m - 1; i >= 0; --i) {          // v = L^-H w_k (back substitution)
-      cd v = at(W, i, k);
-      for (int j = i + 1; j < m; ++j) v -= std::conj(at(L, j, i)) * at(V, j, c);
-      at(V, i, c) = v / at(L, i, i);
-    }
-  }
-  return true;
-}
 
 // A <- Rayleigh-Ritz vectors of span(A) (h^3-orthonormal, ascending Ritz
 // values into eps); on return B holds them canonically (column-major
@@ -2371,9 +2267,10 @@ int gs_rayleigh_ritz(emd_system *s, std::vector<double> &eps) {
   CK(cudaMemcpyAsync(Sh.data(), g->Sz, (size_t)m * m * 16, cudaMemcpyDeviceToHost, s->st));
   CK(cudaMemcpyAsync(Hh.data(), g->Hz, (size_t)m * m * 16, cudaMemcpyDeviceToHost, s->st));
   CK(cudaStreamSynchronize(s->st));
-  if (!hermitian_generalized_eig(m, Hh, Sh, eps, Vh))
+  if (!emd_host::hermitian_generalized_eig(m, Hh, Sh, eps, Vh))
     return fail(EMD_ECUDA, "subspace eigenproblem: the overlap matrix is not positive "
-                           "definite (the filtered set lost rank)");
+                           "definite (the filtered set lost rank), or its QR iteration "
+                           "did not converge");
   // X V (V = eigenvectors, ascending Ritz values) into B (canonical), packed into A
   CK(cudaMemcpyAsync(g->Hz, Vh.data(), (size_t)m * m * 16, cudaMemcpyHostToDevice, s->st));
   emd_launch_rotate(prec, g->C, g->Hz, n3, m, g->B, s->st);
@@ -2396,95 +2293,8 @@ void gs_density(emd_system *s, double *rho, const double *w) {
   emd_launch_density(oo, g->C, s->cfg.occ, rho, s->st);
 }
 
-// Fermi-Dirac occupations of the n lowest Ritz values, f_i = occ / (1 +
-// exp((eps_i - mu) / kT)), with mu bisected (sum f is increasing in mu)
-// until sum f = n_e; returns mu.  Needs 0 < n_e < occ n.
-double gs_fermi_dirac(const std::vector<double> &eps, int n, double n_e, double occ,
-                      double kT, std::vector<double> &f) {
-  double lo = eps[0], hi = eps[0];
-  for (int i = 0; i < n; ++i) {
-    lo = std::min(lo, eps[i]);
-    hi = std::max(hi, eps[i]);
-  }
-  lo -= 50.0 * kT + 1.0;                    // sum f ~ 0 here
-  hi += 50.0 * kT + 1.0;                    // sum f ~ occ n here
-  f.assign(n, 0.0);
-  auto fill = [&](double mu) {
-    double t = 0.0;
-    for (int i = 0; i < n; ++i) {
-      f[i] = occ / (1.0 + std::exp((eps[i] - mu) / kT));
-      t += f[i];
-    }
-    return t;
-  };
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (fill(mid) < n_e) lo = mid;
-    else hi = mid;
-  }
-  const double mu = 0.5 * (lo + hi);
-  fill(mu);
-  return mu;
-}
 
-// S = -sum_i occ [g ln g + (1 - g) ln(1 - g)], g = 1 / (1 + e^x) and
-// 1 - g = 1 / (1 + e^-x), x = (eps_i - mu) / kT (0 ln 0 = 0)
-double gs_entropy(const std::vector<double> &eps, int n, double mu, double occ, double kT) {
-  auto xlx = [](double v) { return v > 0.0 ? v * std::log(v) : 0.0; };
-  double t = 0.0;
-  for (int i = 0; i < n; ++i) {
-    const double x = (eps[i] - mu) / kT;
-    t += xlx(1.0 / (1.0 + std::exp(x))) + xlx(1.0 / (1.0 + std::exp(-x)));
-  }
-  return -occ * t;
-}
 
-// Anderson mixing: with F_i = rho_out_i - rho_in_i over the stored
-// iterations, c minimises |sum c_i F_i| subject to sum c_i = 1, and
-// rho_in <- sum c_i (rho_in_i + mix F_i).  B holds <F_i, F_j>.
-void gs_anderson_coefficients(const double (&B)[GroundStateWork::kHist][GroundStateWork::kHist],
-                              const std::vector<int> &act, int newest, std::vector<double> &c) {
-  const int m = (int)act.size();
-  std::vector<double> M(m * m), x(m, 1.0);
-  double dmax = 0.0;
-  for (int i = 0; i < m; ++i) dmax = std::max(dmax, B[act[i]][act[i]]);
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < m; ++j)
-      M[i * m + j] = B[act[i]][act[j]] + (i == j ? 1e-12 * dmax : 0.0);
-  bool ok = dmax > 0.0;
-  for (int k = 0; ok && k < m; ++k) {       // Gaussian elimination, partial pivoting
-    int p = k;
-    for (int i = k + 1; i < m; ++i)
-      if (std::fabs(M[i * m + k]) > std::fabs(M[p * m + k])) p = i;
-    if (!(std::fabs(M[p * m + k]) > 0.0)) {
-      ok = false;
-      break;
-    }
-    if (p != k) {
-      for (int j = 0; j < m; ++j) std::swap(M[k * m + j], M[p * m + j]);
-      std::swap(x[k], x[p]);
-    }
-    for (int i = k + 1; i < m; ++i) {
-      const double f = M[i * m + k] / M[k * m + k];
-      for (int j = k; j < m; ++j) M[i * m + j] -= f * M[k * m + j];
-      x[i] -= f * x[k];
-    }
-  }
-  for (int k = m - 1; ok && k >= 0; --k) {
-    double v = x[k];
-    for (int j = k + 1; j < m; ++j) v -= M[k * m + j] * x[j];
-    x[k] = v / M[k * m + k];
-  }
-  double sum = 0.0;
-  for (int i = 0; ok && i < m; ++i) sum += x[i];
-  ok = ok && std::isfinite(sum) && std::fabs(sum) > 0.0;
-  c.assign(m, 0.0);
-  if (!ok) {                                // plain mixing with the newest pair
-    for (int i = 0; i < m; ++i) c[i] = act[i] == newest ? 1.0 : 0.0;
-    return;
-  }
-  for (int i = 0; i < m; ++i) c[i] = x[i] / sum;
-}
 
 }  // namespace
 
@@ -2559,7 +2369,7 @@ int emd_ground_state_smeared(emd_system *s, int max_scf, double tol, int degree,
     r = gs_rayleigh_ritz(s, eps);
     if (r) return r;
     if (smear) {
-      mu_f = gs_fermi_dirac(eps, n_occ, n_e, occ, kT, f);
+      mu_f = emd_host::fermi_dirac(eps, n_occ, n_e, occ, kT, f);
       for (int i = 0; i < n_occ; ++i) wh[i] = std::sqrt(f[i] / occ);
       CK(cudaMemcpyAsync(g->wd, wh.data(), (size_t)n_occ * 8, cudaMemcpyHostToDevice, s->st));
     }
@@ -2597,7 +2407,7 @@ int emd_ground_state_smeared(emd_system *s, int max_scf, double tol, int degree,
     CK(cudaStreamSynchronize(s->st));
     for (size_t j = 0; j < act.size(); ++j) B[k][act[j]] = B[act[j]][k] = dots[j];
     std::vector<double> c;
-    gs_anderson_coefficients(B, act, k, c);
+    emd_host::anderson_coefficients(K, &B[0][0], act, k, c);
     // rho_in <- sum_j c_j rho_in_j + mix K[sum_j c_j F_j] (K: Kerker's
     // factor, or 1), the combined residual formed in rho_out
     EmdComb cf{};
@@ -2639,7 +2449,7 @@ int emd_ground_state_smeared(emd_system *s, int max_scf, double tol, int degree,
     info->band_energy = sum;
     info->gap = eps[n_occ] - eps[n_occ - 1];
     info->fermi_level = smear ? mu_f : 0.5 * (eps[n_occ - 1] + eps[n_occ]);
-    info->entropy = smear ? gs_entropy(eps, n_occ, mu_f, occ, kT) : 0.0;
+    info->entropy = smear ? emd_host::smearing_entropy(eps, n_occ, mu_f, occ, kT) : 0.0;
   }
   if (!converged)
     return fail(EMD_ENOTCONV, "ground state: residual %.3e after %d iterations (tol %.3e)",
