@@ -122,3 +122,13 @@ def test_projector_channels_rejected_before_device_use(lib, lmax, prec, bo):
     with pytest.raises(emd.EmdError) as ei:
         emd.emd_init_system(cfg)
     assert ei.value.code == emd.EMD_EINVAL
+
+
+def test_occupation_and_smeared_entry_points_reject_null(lib):
+    import ctypes
+    f = (ctypes.c_double * 4)(2.0, 2.0, 1.0, 1.0)
+    assert lib.emd_set_occupations(None, f) == emd.EMD_EINVAL
+    assert lib.emd_get_occupations(None, f) == emd.EMD_EINVAL
+    assert lib.emd_ground_state_smeared(None, 10, 1e-8, 8, 0.5, 0.01, 6.0, 0.8,
+                                        None, None, None) == emd.EMD_EINVAL
+    assert "NULL" in lib.emd_last_error().decode()
