@@ -238,3 +238,18 @@ def test_small_smearing_reduces_to_integer_ground_state(system, gs):
     assert np.max(np.abs(sm.rho - gs.rho)) < 1e-8 * np.max(gs.rho)
     e_int = O.energies(gs.state)["ks"]
     assert abs(sm.free_energy - e_int) < 1e-9 * abs(e_int)
+
+
+def test_kerker_factor_on_plane_waves():
+    """Kerker's preconditioner multiplies a plane wave of wave vector G by
+    |G|^2 / (|G|^2 + q0^2) and leaves a constant alone."""
+    n, h, q0 = 12, 0.4, 0.7
+    L = n * h
+    x = np.arange(n) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    m = (1, 2, 3)
+    k = 2 * np.pi * np.array(m) / L
+    wave = np.cos(k[0] * X + k[1] * Y + k[2] * Z)
+    g2 = float(k @ k)
+    out = G.kerker(wave + 0.25, h, q0)
+    assert np.max(np.abs(out - (g2 / (g2 + q0 * q0) * wave + 0.25))) < 1e-13
